@@ -1,0 +1,93 @@
+"""Edge-preserving regularizer R, its gradient and its Huber-curvature SQS diagonal.
+
+ORACLE -- test infrastructure only.
+
+R(x) = sum_i beta_i sum_n kappa_n kappa_{n+s_i} phi([C_i x]_n)      (Sec. III, Eq. (def_reg))
+
+with [C_i x]_n = x_n - x_{n+s_i}, counted for pairs whose both pixels lie in
+the image, kappa = 1, and beta_i = beta / ||s_i|| (axis neighbours beta,
+diagonal neighbours beta/sqrt(2)).  In 2-D the four directions
+(1,0), (0,1), (1,1), (1,-1) cover all 8 neighbours.
+
+The SQS diagonal uses Huber's curvature omega(t) = phi'(t)/t (Sec. III-A: the
+iteration-dependent curvature used "for faster convergence"):
+
+D_R(x) = |C|' diag(beta_i omega([C_i x]_n)) |C| 1, i.e. each pair adds
+2 beta_i omega(t) to both of its pixels (|C_i| 1 = 2).
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+DIRECTIONS_2D = ((1, 0), (0, 1), (1, 1), (1, -1))  # (step in ix, step in iy)
+
+
+def potential(kind: str, delta: float):
+    """(phi, phi', omega = phi'(t)/t) for the hyperbola, Fair or quadratic potential."""
+    if kind == "hyperbola":  # delta^2 (sqrt(1 + (t/delta)^2) - 1)
+        phi = lambda t: delta * delta * (np.sqrt(1.0 + (t / delta) ** 2) - 1.0)  # noqa: E731
+        dphi = lambda t: t / np.sqrt(1.0 + (t / delta) ** 2)  # noqa: E731
+        omega = lambda t: 1.0 / np.sqrt(1.0 + (t / delta) ** 2)  # noqa: E731
+    elif kind == "fair":  # delta^2 (|t/delta| - log(1 + |t/delta|)), Sec. IV-A
+        phi = lambda t: delta * delta * (np.abs(t / delta) - np.log1p(np.abs(t / delta)))  # noqa: E731
+        dphi = lambda t: t / (1.0 + np.abs(t) / delta)  # noqa: E731
+        omega = lambda t: 1.0 / (1.0 + np.abs(t) / delta)  # noqa: E731
+    elif kind == "quadratic":  # t^2 / 2
+        phi = lambda t: 0.5 * t * t  # noqa: E731
+        dphi = lambda t: np.asarray(t, dtype=np.float64) * 1.0  # noqa: E731
+        omega = lambda t: np.ones_like(np.asarray(t, dtype=np.float64))  # noqa: E731
+    else:
+        raise ValueError(kind)
+    return phi, dphi, omega
+
+
+def direction_weights(beta: float, dirs=DIRECTIONS_2D):
+    return [beta / math.sqrt(sum(c * c for c in d)) for d in dirs]
+
+
+def _pair_slices(shape, d):
+    """Slices (a, b) so that x[a] and x[b] are the pixel pairs n, n + s (both in the image)."""
+    ny, nx = shape
+    sx, sy = d
+
+    def one(step, n):
+        return (slice(0, n - step), slice(step, n)) if step >= 0 else (slice(-step, n), slice(0, n + step))
+
+    ax, bx = one(sx, nx)
+    ay, by = one(sy, ny)
+    return (ay, ax), (by, bx)
+
+
+def value(x: np.ndarray, beta: float, delta: float, kind: str) -> float:
+    phi, _, _ = potential(kind, delta)
+    tot = 0.0
+    for d, bi in zip(DIRECTIONS_2D, direction_weights(beta)):
+        a, b = _pair_slices(x.shape, d)
+        tot += bi * float(np.sum(phi(x[a] - x[b])))
+    return tot
+
+
+def gradient(x: np.ndarray, beta: float, delta: float, kind: str) -> np.ndarray:
+    _, dphi, _ = potential(kind, delta)
+    g = np.zeros_like(x, dtype=np.float64)
+    for d, bi in zip(DIRECTIONS_2D, direction_weights(beta)):
+        a, b = _pair_slices(x.shape, d)
+        f = bi * dphi(x[a] - x[b])
+        g[a] += f
+        g[b] -= f
+    return g
+
+
+def curvature(x: np.ndarray, beta: float, delta: float, kind: str) -> np.ndarray:
+    """Huber-curvature SQS diagonal D_R(x)."""
+    _, _, omega = potential(kind, delta)
+    D = np.zeros_like(x, dtype=np.float64)
+    for d, bi in zip(DIRECTIONS_2D, direction_weights(beta)):
+        a, b = _pair_slices(x.shape, d)
+        c = 2.0 * bi * omega(x[a] - x[b])
+        D[a] += c
+        D[b] += c
+    return D

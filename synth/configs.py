@@ -1,0 +1,114 @@
+"""Scan geometries and workload descriptions.
+
+Geometry convention (2-D fan beam, equiangular "arc" detector):
+
+* Image: ``nx x ny`` pixels of size ``dx x dy`` (mm); pixel (ix, iy) has its
+  centre at ``x = (ix - (nx-1)/2 + offset_x) dx``, ``y = (iy - (ny-1)/2 +
+  offset_y) dy``.  Arrays are stored ``[iy][ix]`` (x fastest).
+* View v has angle ``beta_v = orbit_start + v * orbit / na``.  The central ray
+  points from the source towards the isocentre along ``e = (cos b, sin b)``; the
+  source sits at ``-dso * e``.
+* Detector bin s has fan angle ``gamma_s = (s - (ns-1)/2 + offset_s) * dgamma``
+  with ``dgamma = ds / dsd`` (``ds`` is the arc length of a cell at ``dsd``).
+  A point P has fan angle ``atan2((P - S).e_perp, (P - S).e)`` with
+  ``e_perp = (-sin b, cos b)``.
+* Sinograms are stored view-major ``[view][bin]`` (bin fastest).
+
+The numbers of the two 2-D workloads follow the paper's GE LightSpeed-type
+fan geometry (Sec. IV-A: 888 channels, 984 views per turn, 0.9776 mm pixels,
+source-to-isocentre 541 mm, source-to-detector 949 mm).
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+
+MU_WATER_PER_MM = 0.02  # 1 HU = MU_WATER_PER_MM / 1000 per mm ("modified HU", air = 0)
+
+
+@dataclasses.dataclass(frozen=True)
+class FanArcGeometry:
+    nx: int
+    ny: int
+    dx: float
+    dy: float
+    ns: int
+    ds: float
+    na: int
+    dso: float
+    dsd: float
+    offset_x: float = 0.0
+    offset_y: float = 0.0
+    offset_s: float = 0.0
+    orbit_deg: float = 360.0
+    orbit_start_deg: float = 0.0
+
+    @property
+    def dgamma(self) -> float:
+        return self.ds / self.dsd
+
+    def betas(self):
+        import numpy as np
+
+        v = np.arange(self.na, dtype=np.float64)
+        return np.deg2rad(self.orbit_start_deg + v * self.orbit_deg / self.na)
+
+    def gammas(self):
+        import numpy as np
+
+        s = np.arange(self.ns, dtype=np.float64)
+        return (s - (self.ns - 1) / 2.0 + self.offset_s) * self.dgamma
+
+    def fov_radius(self) -> float:
+        """Radius of the disk seen by every view: min(image half-width, dso*sin(half fan))."""
+        half_fan = max(abs(self.gammas()[0]), abs(self.gammas()[-1])) + 0.5 * self.dgamma
+        r_fan = self.dso * math.sin(half_fan)
+        r_img = min(self.nx * self.dx, self.ny * self.dy) / 2.0
+        return min(r_fan, r_img)
+
+    def with_(self, **kw) -> "FanArcGeometry":
+        return dataclasses.replace(self, **kw)
+
+
+@dataclasses.dataclass(frozen=True)
+class ScanConfig:
+    name: str
+    geom: FanArcGeometry
+    phantom: str  # "random10" | "anthro"
+    i0: float
+    sigma_e: float
+    beta: float
+    delta_hu: float
+    potential: str
+    M: int
+    alpha: float
+    n_iter: int
+    seed: int = 0
+
+    @property
+    def delta(self) -> float:
+        """Potential parameter delta in 1/mm."""
+        return self.delta_hu * MU_WATER_PER_MM / 1000.0
+
+
+def fan2d_128(seed: int = 0) -> ScanConfig:
+    """128x128, 1 mm pixels, 256 bins x 1.0 mm, 180 views, M=10, alpha=1.999, 20 iterations."""
+    g = FanArcGeometry(nx=128, ny=128, dx=1.0, dy=1.0, ns=256, ds=1.0, na=180, dso=541.0, dsd=949.0)
+    return ScanConfig(
+        name="fan2d_128", geom=g, phantom="random10", i0=1e5, sigma_e=5.0,
+        beta=2.0 ** 10, delta_hu=10.0, potential="hyperbola", M=10, alpha=1.999, n_iter=20, seed=seed,
+    )
+
+
+def fan2d_512(seed: int = 0) -> ScanConfig:
+    """512x512, 0.98 mm pixels, 888 bins x 1.0239 mm, 984 views, M=41, alpha=1.999, 30 iterations."""
+    g = FanArcGeometry(nx=512, ny=512, dx=0.98, dy=0.98, ns=888, ds=1.0239, na=984, dso=541.0, dsd=949.0)
+    return ScanConfig(
+        name="fan2d_512", geom=g, phantom="anthro", i0=1e5, sigma_e=5.0,
+        beta=2.0 ** 10, delta_hu=10.0, potential="hyperbola", M=41, alpha=1.999, n_iter=30, seed=seed,
+    )
+
+
+def config_by_name(name: str, seed: int = 0) -> ScanConfig:
+    return {"fan2d_128": fan2d_128, "fan2d_512": fan2d_512}[name](seed)
