@@ -1,0 +1,175 @@
+/*
+ * ct.h -- C ABI of the GB300 (sm_103a) relaxed OS-LALM CT reconstruction library.
+ *
+ * The library solves the penalized weighted least-squares CT problem of
+ * Nien & Fessler, "Relaxed Linearized Algorithms for Faster X-Ray CT Image
+ * Reconstruction" (Sec. III, Eq. (ct_problem)):
+ *
+ *     x_hat = argmin_{x in Omega} 1/2 ||y - A x||_W^2 + R(x)
+ *
+ * with A a separable-footprint (SF) fan-beam projector, W = diag(w) the
+ * statistical weights, R the edge-preserving regularizer of Eq. (def_reg)
+ * and Omega = {x >= 0}, using the proposed relaxed OS-LALM of Algorithm 1
+ * (or the simple relaxation of Algorithm 2) with the continuation sequence
+ * of Eq. (dec_rho).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Images are float32 [ny][nx] (x fastest); sinograms are float32
+ *   [view][bin] (bin fastest), view-major.  Pixel (ix, iy) is centred at
+ *   ((ix - (nx-1)/2 + offset_x) dx, (iy - (ny-1)/2 + offset_y) dy) mm.
+ *   View v has angle beta_v = orbit_start + v * orbit / na; the source sits
+ *   at -dso (cos beta, sin beta); bin s is centred at fan angle
+ *   (s - (ns-1)/2 + offset_s) ds / dsd (equiangular arc detector, ds is the
+ *   cell's arc length at dsd).
+ * - Array arguments named x, y, w, d_l, x_inout, x_ref are DEVICE pointers to
+ *   caller-owned memory; they must be 4-byte aligned and must not alias
+ *   each other unless stated.  `views` lists are HOST arrays.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  ct_forward, ct_back, ct_sqs_diag and ct_reg_gradient are
+ *   asynchronous on it; ct_relaxed_oslalm_solve synchronises it before
+ *   filling the report.
+ * - Every entry point validates its arguments on the host and returns a
+ *   status without launching anything when they are invalid;
+ *   ct_last_error() then returns a message (thread-local, valid until the
+ *   next call on the same thread).
+ * - The library allocates device memory only for the workspace owned by a
+ *   ct_geom (geometry tables at creation, solver state at the first solve);
+ *   ct_geom_destroy frees it.  Calls that use one ct_geom must not run
+ *   concurrently on different streams.
+ */
+#ifndef CT_H
+#define CT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CT_OK = 0,
+    CT_EINVAL = 1,   /* invalid argument (sizes, pointers, parameters) */
+    CT_ENOMEM = 2,   /* device allocation failed */
+    CT_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+    CT_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+    CT_ENOTSUP = 5   /* geometry kind or option not supported */
+} ct_status;
+
+enum { CT_FAN_ARC_2D = 1 };
+
+typedef struct ct_geom ct_geom; /* opaque; owns device geometry tables and workspace */
+
+/* Scan geometry (plain data, copied by ct_geom_create).  Lengths in mm,
+ * angles in degrees.  For CT_FAN_ARC_2D the fields nz, dz, offset_z, nt, dt,
+ * offset_t and pitch are ignored. */
+typedef struct {
+    int kind;
+    int nx, ny, nz;
+    double dx, dy, dz;
+    double offset_x, offset_y, offset_z; /* in pixels */
+    int ns, nt, na;
+    double ds, dt;
+    double offset_s, offset_t; /* in detector cells */
+    double dso, dsd;           /* source-to-isocentre, source-to-detector */
+    double orbit_deg, orbit_start_deg;
+    double pitch;
+} ct_geom_desc;
+
+/* Create the device-side description of a scan geometry (Sec. III: A is the
+ * forward projection matrix of the scan).  Checks that every pixel lies in
+ * front of the source (image inside the circle of radius 0.95 dso) and
+ * precomputes per-view and per-(view, 16x16 pixel tile) FP64-derived tables
+ * in device memory.  On success *out owns that memory; release it with
+ * ct_geom_destroy.  Errors: CT_EINVAL (bad sizes), CT_ENOTSUP (kind),
+ * CT_ENOMEM, CT_ECUDA. */
+ct_status ct_geom_create(const ct_geom_desc *desc, ct_geom **out);
+
+/* Free a geometry and all device memory it owns (NULL is a no-op).  Call it
+ * only once no work using it is pending on any stream. */
+void ct_geom_destroy(ct_geom *g);
+
+/* Forward projection y = A_V x (Sec. III, Eq. (ct_problem); SF footprints,
+ * ray-driven).  x: device [ny][nx]; y: device [nviews][ns], row k is view
+ * views[k].  views: host array of nviews indices in [0, na), or NULL for all
+ * na views in order (then nviews must be na).  1 <= nviews <= na.  Output
+ * rows are overwritten.  Errors: CT_EINVAL, CT_ECUDA. */
+ct_status ct_forward(const ct_geom *g, const float *x, float *y, const int *views, int nviews, void *stream);
+
+/* Back-projection x = scale * A_V' y (+ x if accumulate != 0), with the same
+ * a_ij as ct_forward (voxel-driven, no atomics).  y: device [nviews][ns];
+ * x: device [ny][nx]; views as for ct_forward.  Errors: CT_EINVAL, CT_ECUDA. */
+ct_status ct_back(const ct_geom *g, const float *y, float *x, const int *views, int nviews, float scale,
+                  int accumulate, void *stream);
+
+/* SQS majorizer of the data term, D_L = diag(A' W A 1) over all views
+ * (Sec. III-A: the diagonal majorizing matrix of A'WA).  w: device [na][ns]
+ * weights; d_l: device [ny][nx] output.  Uses the geometry's sinogram
+ * workspace.  Errors: CT_EINVAL, CT_ENOMEM, CT_ECUDA. */
+ct_status ct_sqs_diag(const ct_geom *g, const float *w, float *d_l, void *stream);
+
+enum { CT_POT_HYPERBOLA = 0, CT_POT_FAIR = 1, CT_POT_QUADRATIC = 2 };
+enum { CT_ALG_PROPOSED = 0, CT_ALG_SIMPLE = 1 };
+
+/* Gradient and Huber-curvature SQS diagonal of the regularizer
+ * R(x) = sum_i beta_i sum_n phi([C_i x]_n) (Eq. (def_reg)) over the 8
+ * neighbours in 2-D, beta_i = beta / ||s_i||, kappa = 1.  potential:
+ * CT_POT_*, delta > 0 its scale (same units as x).  grad, curv: device
+ * [ny][nx] outputs (curv may be NULL).  Errors: CT_EINVAL, CT_ECUDA. */
+ct_status ct_reg_gradient(const ct_geom *g, const float *x, float beta, float delta, int potential, float *grad,
+                          float *curv, void *stream);
+
+/* Parameters of ct_relaxed_oslalm_solve. */
+typedef struct {
+    int M;              /* number of ordered subsets, 1 <= M <= na (interleaved: v mod M) */
+    int n_iter;         /* outer iterations (each visits all M subsets) */
+    float alpha;        /* relaxation, 1 <= alpha < 2 (Algorithm 1: 1.999 in the paper) */
+    float beta;         /* regularization parameter (>= 0) */
+    float delta;        /* potential scale (> 0 unless potential is quadratic) */
+    int potential;      /* CT_POT_* */
+    int algorithm;      /* CT_ALG_PROPOSED (Algorithm 1) or CT_ALG_SIMPLE (Algorithm 2) */
+    int nonneg;         /* 1: Omega = {x >= 0}; 0: unconstrained */
+    int continuation;   /* 1: rho_k(alpha) of Eq. (dec_rho), k = subiterations; 0: rho = rho_fixed */
+    float rho_fixed;    /* used when continuation == 0 (> 0) */
+    const float *x_ref; /* optional device [ny][nx] reference (x*) for the RMSD trace, or NULL */
+    float hu_per_unit;  /* HU per unit of x, for RMSD reporting */
+    float fov_radius;   /* RMSD mask radius in mm; <= 0 selects the scan's full field of view */
+    float stop_rmsd_hu; /* > 0: stop after the first iteration with RMSD <= this (needs x_ref) */
+} ct_solve_params;
+
+/* Report filled by ct_relaxed_oslalm_solve.  The two array pointers are
+ * optional caller-owned HOST arrays of at least n_iter entries. */
+typedef struct {
+    int iters_done;
+    double seconds;         /* device time of the whole solve (D_L, initialisation, iterations) */
+    double seconds_to_tol;  /* device time until the first iteration with RMSD <= stop tolerance
+                               (or <= 1 HU when stop_rmsd_hu <= 0); negative if never reached */
+    float rmsd_hu_last;     /* RMSD of the last iterate, or -1 without x_ref */
+    float *rmsd_trace_hu;   /* optional out: RMSD after each iteration */
+    double *iter_seconds;   /* optional out: device time from the solve's start to the end of each iteration */
+} ct_solve_report;
+
+/* Relaxed OS-LALM (Algorithm 1, or Algorithm 2 when algorithm ==
+ * CT_ALG_SIMPLE) for Eq. (ct_problem) with W = diag(w):
+ *   D_L = diag(A'WA1); rho = 1; zeta = g = M grad L_M(x); h = D_L x - zeta;
+ *   per subiteration (subset m): s = rho (D_L x - h) + (1 - rho) g;
+ *   x+ = [x - (rho D_L + D_R)^{-1}(s + grad R(x))]_Omega (D_R: Huber curvature);
+ *   zeta = M grad L_m(x+); g+ = rho/(rho+1)(alpha zeta + (1-alpha) g) + g/(rho+1);
+ *   h+ = alpha (D_L x+ - zeta) + (1-alpha) h; rho <- rho_{k}(alpha).
+ * y, w: device [na][ns] sinogram and weights (w >= 0).  x_inout: device
+ * [ny][nx], the initial image on entry and the result on return.  The solve
+ * runs on `stream` as CUDA-graph replays of one outer iteration and
+ * synchronises the stream before returning.  Errors: CT_EINVAL, CT_ENOMEM,
+ * CT_ECUDA. */
+ct_status ct_relaxed_oslalm_solve(const ct_geom *g, const float *y, const float *w, const ct_solve_params *p,
+                                  float *x_inout, ct_solve_report *report, void *stream);
+
+/* Message describing the last failure on this thread ("" if none). */
+const char *ct_last_error(void);
+
+/* Library version (major * 100 + minor). */
+int ct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CT_H */

@@ -1,0 +1,203 @@
+// Internal declarations of the CT library: geometry object, device footprint
+// arithmetic shared by the forward and back projectors, kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/ct.h"
+
+namespace ct {
+
+constexpr int kTile = 16;            // pixels per side of an anchor tile
+constexpr float kTileHalf = 7.5f;    // offset of a tile's centre from its first pixel, in pixels
+
+// Fan-beam geometry as the kernels see it (passed by value).
+struct FanDev {
+    int nx, ny, ns, na;
+    int ntx, nty;             // anchor tiles along x and y
+    float dx, dy, hx, hy;     // pixel size and half size (mm)
+    float inv_dx, inv_dy;
+    float inv_dg;             // detector cells per radian (dsd / ds)
+    float dgamma;             // cell width in radians
+    float gamma0;             // fan angle of cell 0's centre (rad)
+    float dso;
+    float x_edge0, y_edge0;   // x of the left edge of column 0, y of the lower edge of row 0 (mm)
+    float cxo, cyo;           // (nx-1)/2 - offset_x, (ny-1)/2 - offset_y (pixel index of the origin)
+    const float4 *anchor;     // [na][ntx*nty]: view-frame (t_par, t_perp) of the tile centre,
+                              // and its detector coordinate u = gamma/dgamma + (ns-1)/2 - offset_s
+                              // split into hi + lo floats (FP64-derived)
+    const float2 *view_cs;    // [na]: (cos beta, sin beta)
+    const float *view_beta;   // [na]: beta in [0, 2 pi)
+};
+
+// Solver state shared by the kernels of one subiteration (device pointers).
+struct SolveDev {
+    float *x;        // canonical image x (caller's x_inout)
+    float *x_new;    // x+ written by the update kernel
+    float *g, *h;    // split-variable and dual recursions (Algorithm 2 keeps zeta in h)
+    const float *d_l;
+    float *resid;    // subset residual slab [views of subset][ns]
+    const float *rho_tab;  // rho for subiteration t (0-based)
+    int *counter;    // [0]: subiterations done; [1]: block-completion counter of the back-projector
+    float alpha, M_scale;
+    int algorithm;   // CT_ALG_*
+    int nonneg;
+};
+
+}  // namespace ct
+
+// The opaque handle of the C ABI.
+struct ct_geom {
+    ct_geom_desc desc;
+    ct::FanDev fan;
+    float4 *d_anchor = nullptr;
+    float2 *d_view_cs = nullptr;
+    float *d_view_beta = nullptr;
+    int *d_views_all = nullptr;   // identity list [0, na)
+    int *d_views_stage = nullptr; // caller view lists are staged here [na]
+    float *d_sino_ws = nullptr;   // [na][ns] sinogram workspace (D_L)
+    // solver workspace (allocated at the first solve)
+    size_t solve_bytes = 0;
+    void *d_solve = nullptr;
+    double fov_radius = 0.0;
+    int device = 0;
+};
+
+namespace ct {
+
+void set_error(const char *fmt, ...);
+ct_status cuda_fail(cudaError_t e, const char *what);
+
+#define CT_CUDA_TRY(expr, what)                                  \
+    do {                                                         \
+        cudaError_t _e = (expr);                                 \
+        if (_e != cudaSuccess) return ::ct::cuda_fail(_e, what); \
+    } while (0)
+
+// ---------------------------------------------------------------- device arithmetic
+
+// arctan by its Gregory (Taylor) series, for |z| <= 0.25 (truncation < |z|^15/15).
+__device__ __forceinline__ float atan_series(float z)
+{
+    const float z2 = z * z;
+    float p = fmaf(z2, -1.0f / 13.0f, 1.0f / 11.0f);
+    p = fmaf(z2, p, -1.0f / 9.0f);
+    p = fmaf(z2, p, 1.0f / 7.0f);
+    p = fmaf(z2, p, -1.0f / 5.0f);
+    p = fmaf(z2, p, 1.0f / 3.0f);
+    return fmaf(-z * z2, p, z);
+}
+
+// arctan for the pixel-corner offsets, |z| <= 0.02 (truncation < |z|^7/7 < 2e-13).
+__device__ __forceinline__ float atan_tiny(float z)
+{
+    const float z2 = z * z;
+    return fmaf(z * z2, fmaf(z2, 0.2f, -1.0f / 3.0f), z);
+}
+
+// Separable footprint of one pixel in one view: a unit-height trapezoid with
+// sorted vertices t0..t3 in detector-cell units relative to cell n (cell s
+// covers [s - n - 1/2, s - n + 1/2]), times the amplitude amp (chord through
+// the pixel along the ray through its centre).
+struct Footprint {
+    float t0, t1, t2, t3;
+    float amp;
+    float i2w1, i2w3;  // 1/(2 (t1 - t0)) and 1/(2 (t3 - t2)), 0 for a vertical edge
+    int n;
+};
+
+// cb, sb: view direction; A: the pixel's tile anchor for this view; (ox, oy):
+// pixel centre minus tile centre (mm, image axes).
+__device__ __forceinline__ Footprint sf_footprint(const FanDev &G, float cb, float sb, float4 A, float ox, float oy)
+{
+    // pixel centre relative to the anchor, in the view frame (small vector: accurate in FP32)
+    const float dpar = fmaf(ox, cb, oy * sb);
+    const float dperp = fmaf(oy, cb, -ox * sb);
+    const float cpar = A.x + dpar;
+    const float cperp = A.y + dperp;
+    // fan angle of the centre relative to the anchor's: atan(cross(A, c) / dot(A, c))
+    const float crs = fmaf(A.x, dperp, -A.y * dpar);
+    const float dt = fmaf(A.x, cpar, A.y * cperp);
+    const float du = atan_series(crs / dt) * G.inv_dg;
+    const float nf = floorf(A.z + du);
+    const float f = (A.z - nf) + (A.w + du);  // centre's detector coordinate relative to cell nf
+    // corners: angle relative to the centre, atan(cross(c, o) / (|c|^2 + c.o))
+    const float r2 = fmaf(cpar, cpar, cperp * cperp);
+    const float ir2 = 1.0f / r2;
+    const float xpar = G.hx * cb, xperp = -G.hx * sb;  // +half pixel along x, view frame
+    const float ypar = G.hy * sb, yperp = G.hy * cb;   // +half pixel along y
+    const float cx = fmaf(cpar, xperp, -cperp * xpar), cy = fmaf(cpar, yperp, -cperp * ypar);
+    const float ex = fmaf(cpar, xpar, cperp * xperp) * ir2, ey = fmaf(cpar, ypar, cperp * yperp) * ir2;
+    float t[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const float sx = (k & 1) ? 1.0f : -1.0f;
+        const float sy = (k & 2) ? 1.0f : -1.0f;
+        const float e = fmaf(sx, ex, sy * ey);                 // (c.o)/|c|^2, |e| < 0.01
+        const float inv = fmaf(e, e - 1.0f, 1.0f);              // 1/(1+e) to O(e^3)
+        const float z = fmaf(sx, cx, sy * cy) * ir2 * fmaf(-e * e, e, inv);
+        t[k] = fmaf(atan_tiny(z), G.inv_dg, f);
+    }
+    // sort the four vertices
+    float a0 = fminf(t[0], t[1]), a1 = fmaxf(t[0], t[1]);
+    float b0 = fminf(t[2], t[3]), b1 = fmaxf(t[2], t[3]);
+    Footprint F;
+    F.t0 = fminf(a0, b0);
+    F.t3 = fmaxf(a1, b1);
+    const float m0 = fmaxf(a0, b0), m1 = fminf(a1, b1);
+    F.t1 = fminf(m0, m1);
+    F.t2 = fmaxf(m0, m1);
+    const float w1 = F.t1 - F.t0, w3 = F.t3 - F.t2;
+    F.i2w1 = w1 > 0.0f ? 0.5f / w1 : 0.0f;
+    F.i2w3 = w3 > 0.0f ? 0.5f / w3 : 0.0f;
+    // amplitude: chord through the pixel along the centre ray = |c| / max(|c_x|/dx, |c_y|/dy)
+    const float imx = fabsf(fmaf(cpar, cb, -cperp * sb)) * G.inv_dx;
+    const float imy = fabsf(fmaf(cpar, sb, cperp * cb)) * G.inv_dy;
+    F.amp = sqrtf(r2) / fmaxf(imx, imy);
+    F.n = (int)nf;
+    return F;
+}
+
+// Integral of the unit trapezoid over (-inf, u].
+__device__ __forceinline__ float trap_cdf(const Footprint &F, float u)
+{
+    const float a = fminf(fmaxf(u - F.t0, 0.0f), F.t1 - F.t0);     // rising edge
+    const float b = fminf(fmaxf(F.t3 - u, 0.0f), F.t3 - F.t2);     // falling edge still ahead
+    const float flat = fminf(fmaxf(u - F.t1, 0.0f), F.t2 - F.t1);
+    const float w3 = F.t3 - F.t2;
+    const float fall = (u > F.t2) ? fmaf(-b * b, F.i2w3, 0.5f * w3) : 0.0f;
+    return fmaf(a * a, F.i2w1, flat) + fall;
+}
+
+// Footprint of pixel (ix, iy) in view v (loads the tile anchor).
+__device__ __forceinline__ Footprint pixel_footprint(const FanDev &G, int v, float cb, float sb, int ix, int iy)
+{
+    const int tx = ix / kTile, ty = iy / kTile;
+    const float4 A = __ldg(&G.anchor[(size_t)v * (G.ntx * G.nty) + ty * G.ntx + tx]);
+    const float ox = ((float)(ix - tx * kTile) - kTileHalf) * G.dx;
+    const float oy = ((float)(iy - ty * kTile) - kTileHalf) * G.dy;
+    return sf_footprint(G, cb, sb, A, ox, oy);
+}
+
+// ---------------------------------------------------------------- launchers (projectors.cu)
+
+enum FpMode { FP_PLAIN = 0, FP_RESID = 1, FP_ONES_W = 2 };
+enum BpMode { BP_PLAIN = 0, BP_SOLVE_INIT = 1, BP_SOLVE_UPDATE = 2 };
+
+// out rows follow `views` (device list of nviews view indices).
+cudaError_t launch_fp(const FanDev &G, int mode, const float *x, const int *views, int nviews, float *out,
+                      const float *y, const float *w, cudaStream_t st);
+cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *views, int nviews, float *x,
+                      float scale, int accumulate, const SolveDev *S, cudaStream_t st);
+cudaError_t launch_reg_gradient(const FanDev &G, const float *x, float beta, float delta, int potential,
+                                float *grad, float *curv, cudaStream_t st);
+cudaError_t launch_reg_update(const FanDev &G, const SolveDev &S, float beta, float delta, int potential,
+                              cudaStream_t st);
+
+ct_status validate_views(const ct_geom *g, const int *views, int nviews);
+ct_status stage_views(const ct_geom *g, const int *views, int nviews, const int **dev_views, cudaStream_t st);
+
+}  // namespace ct

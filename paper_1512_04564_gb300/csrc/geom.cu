@@ -1,0 +1,201 @@
+// Geometry object of the C ABI: validation, FP64-derived device tables, error state.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ct_internal.cuh"
+
+namespace ct {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+ct_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? CT_ENOMEM : CT_ECUDA;
+}
+
+ct_status validate_views(const ct_geom *g, const int *views, int nviews)
+{
+    if (nviews < 1 || nviews > g->fan.na) {
+        set_error("nviews=%d must be in [1, na=%d]", nviews, g->fan.na);
+        return CT_EINVAL;
+    }
+    if (!views) {
+        if (nviews != g->fan.na) {
+            set_error("views == NULL selects all %d views, but nviews=%d", g->fan.na, nviews);
+            return CT_EINVAL;
+        }
+        return CT_OK;
+    }
+    for (int k = 0; k < nviews; k++) {
+        if (views[k] < 0 || views[k] >= g->fan.na) {
+            set_error("views[%d]=%d outside [0, %d)", k, views[k], g->fan.na);
+            return CT_EINVAL;
+        }
+    }
+    return CT_OK;
+}
+
+ct_status stage_views(const ct_geom *g, const int *views, int nviews, const int **dev_views, cudaStream_t st)
+{
+    if (!views) {
+        *dev_views = g->d_views_all;
+        return CT_OK;
+    }
+    CT_CUDA_TRY(cudaMemcpyAsync(g->d_views_stage, views, sizeof(int) * nviews, cudaMemcpyHostToDevice, st),
+                "staging view list");
+    *dev_views = g->d_views_stage;
+    return CT_OK;
+}
+
+}  // namespace ct
+
+using namespace ct;
+
+static void free_geom(ct_geom *g)
+{
+    if (!g) return;
+    cudaFree(g->d_anchor);
+    cudaFree(g->d_view_cs);
+    cudaFree(g->d_view_beta);
+    cudaFree(g->d_views_all);
+    cudaFree(g->d_views_stage);
+    cudaFree(g->d_sino_ws);
+    cudaFree(g->d_solve);
+    delete g;
+}
+
+extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
+{
+    if (!d || !out) { set_error("ct_geom_create: null argument"); return CT_EINVAL; }
+    *out = nullptr;
+    if (d->kind != CT_FAN_ARC_2D) {
+        set_error("geometry kind %d is not supported (CT_FAN_ARC_2D=%d)", d->kind, CT_FAN_ARC_2D);
+        return CT_ENOTSUP;
+    }
+    if (d->nx < 1 || d->ny < 1 || d->ns < 1 || d->na < 1 || d->nx > 65536 || d->ny > 65536 || d->ns > (1 << 20) ||
+        d->na > (1 << 20)) {
+        set_error("bad sizes nx=%d ny=%d ns=%d na=%d", d->nx, d->ny, d->ns, d->na);
+        return CT_EINVAL;
+    }
+    if (!(d->dx > 0) || !(d->dy > 0) || !(d->ds > 0) || !(d->dso > 0) || !(d->dsd > 0) || !std::isfinite(d->orbit_deg) ||
+        !std::isfinite(d->orbit_start_deg) || !std::isfinite(d->offset_x) || !std::isfinite(d->offset_y) ||
+        !std::isfinite(d->offset_s)) {
+        set_error("bad geometry lengths/angles");
+        return CT_EINVAL;
+    }
+    // image extent: farthest pixel corner from the isocentre
+    const double cxo = (d->nx - 1) / 2.0 - d->offset_x, cyo = (d->ny - 1) / 2.0 - d->offset_y;
+    double r_img = 0.0;
+    for (int cx = 0; cx < 2; cx++)
+        for (int cy = 0; cy < 2; cy++) {
+            const double X = ((cx ? d->nx - 0.5 : -0.5) - cxo) * d->dx;
+            const double Y = ((cy ? d->ny - 0.5 : -0.5) - cyo) * d->dy;
+            r_img = std::fmax(r_img, std::hypot(X, Y));
+        }
+    const double pmax = std::fmax(d->dx, d->dy);
+    // The footprint arithmetic expands small angles in series; it needs every pixel
+    // at least 50 pixel widths in front of the source.
+    if (d->dso - r_img < 50.0 * pmax) {
+        set_error("image reaches within %.3g mm of the source (needs >= 50 pixels = %.3g mm)", d->dso - r_img,
+                  50.0 * pmax);
+        return CT_EINVAL;
+    }
+    const double dg = d->ds / d->dsd;
+    const double half_fan = (d->ns / 2.0 + std::fabs(d->offset_s)) * dg;
+    if (half_fan >= 1.4) {
+        set_error("fan half-angle %.3g rad is too wide", half_fan);
+        return CT_EINVAL;
+    }
+
+    ct_geom *g = new ct_geom();
+    g->desc = *d;
+    cudaGetDevice(&g->device);
+    FanDev &F = g->fan;
+    F.nx = d->nx; F.ny = d->ny; F.ns = d->ns; F.na = d->na;
+    F.ntx = (d->nx + kTile - 1) / kTile;
+    F.nty = (d->ny + kTile - 1) / kTile;
+    F.dx = (float)d->dx; F.dy = (float)d->dy;
+    F.hx = (float)(0.5 * d->dx); F.hy = (float)(0.5 * d->dy);
+    F.inv_dx = (float)(1.0 / d->dx); F.inv_dy = (float)(1.0 / d->dy);
+    F.inv_dg = (float)(1.0 / dg);
+    F.dgamma = (float)dg;
+    F.gamma0 = (float)((-(d->ns - 1) / 2.0 + d->offset_s) * dg);
+    F.dso = (float)d->dso;
+    F.x_edge0 = (float)((-0.5 - cxo) * d->dx);
+    F.y_edge0 = (float)((-0.5 - cyo) * d->dy);
+    F.cxo = (float)cxo; F.cyo = (float)cyo;
+
+    const int na = d->na, ntiles = F.ntx * F.nty;
+    std::vector<float2> cs(na);
+    std::vector<float> bet(na);
+    std::vector<float4> anc((size_t)na * ntiles);
+    const double c0 = (d->ns - 1) / 2.0 - d->offset_s;
+    for (int v = 0; v < na; v++) {
+        double deg = std::fmod(d->orbit_start_deg + (double)v * d->orbit_deg / na, 360.0);
+        if (deg < 0) deg += 360.0;
+        const double b = deg * M_PI / 180.0;
+        const double cb = std::cos(b), sb = std::sin(b);
+        cs[v] = make_float2((float)cb, (float)sb);
+        bet[v] = (float)b;
+        for (int ty = 0; ty < F.nty; ty++)
+            for (int tx = 0; tx < F.ntx; tx++) {
+                const double X = (tx * kTile + (double)kTileHalf - cxo) * d->dx;
+                const double Y = (ty * kTile + (double)kTileHalf - cyo) * d->dy;
+                const double tpar = d->dso + X * cb + Y * sb;
+                const double tperp = -X * sb + Y * cb;
+                const double u = std::atan2(tperp, tpar) / dg + c0;
+                const float uhi = (float)u;
+                anc[(size_t)v * ntiles + ty * F.ntx + tx] =
+                    make_float4((float)tpar, (float)tperp, uhi, (float)(u - (double)uhi));
+            }
+    }
+    std::vector<int> ident(na);
+    for (int v = 0; v < na; v++) ident[v] = v;
+
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_anchor, sizeof(float4) * anc.size());
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_view_cs, sizeof(float2) * na);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_view_beta, sizeof(float) * na);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_views_all, sizeof(int) * na);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_views_stage, sizeof(int) * na);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_sino_ws, sizeof(float) * (size_t)na * d->ns);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_anchor, anc.data(), sizeof(float4) * anc.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_view_cs, cs.data(), sizeof(float2) * na, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_view_beta, bet.data(), sizeof(float) * na, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_views_all, ident.data(), sizeof(int) * na, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        ct_status st = cuda_fail(e, "ct_geom_create");
+        free_geom(g);
+        return st;
+    }
+    F.anchor = g->d_anchor;
+    F.view_cs = g->d_view_cs;
+    F.view_beta = g->d_view_beta;
+    const double r_fan = d->dso * std::sin(std::fmin(half_fan, M_PI / 2));
+    g->fov_radius = std::fmin(r_fan, 0.5 * std::fmin(d->nx * d->dx, d->ny * d->dy));
+    *out = g;
+    return CT_OK;
+}
+
+extern "C" void ct_geom_destroy(ct_geom *g) { free_geom(g); }
+
+extern "C" const char *ct_last_error(void) { return ct::g_last_error.c_str(); }
+
+extern "C" int ct_version(void) { return 100; }

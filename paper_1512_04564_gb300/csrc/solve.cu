@@ -1,0 +1,291 @@
+// Relaxed OS-LALM driver (Algorithm 1 / Algorithm 2, Sec. III-A) on one GPU.
+//
+// Setup (once per solve): D_L = diag(A'WA1) over all views; zeta = g =
+// M grad L_M(x) from the last subset; h = D_L x - zeta.  One outer iteration
+// (M subiterations of: regularizer + x-update, subset forward projection
+// with the weighted residual, subset back-projection with the g/h update)
+// plus the RMSD-to-reference reduction is captured once as a CUDA graph and
+// replayed n_iter times.  rho for subiteration t is read on the device from
+// a table of the continuation sequence (Eq. (dec_rho)) indexed by a device
+// counter that the back-projector's last block advances, so every replay
+// sees the right rho without host involvement.
+//
+// Subsets are interleaved (S_m = {v : v mod M = m}) and visited m = 0..M-1.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ct_internal.cuh"
+
+namespace ct {
+namespace {
+
+constexpr int kRmsdBlocks = 152;
+
+__global__ void __launch_bounds__(256) rmsd_kernel(FanDev G, const float *__restrict__ x, const float *__restrict__ xr,
+                                                   float r2max, double *__restrict__ partial, int *__restrict__ counter,
+                                                   float *__restrict__ trace, int M, float hu)
+{
+    __shared__ double ss[256];
+    __shared__ double sc[256];
+    double s = 0.0, c = 0.0;
+    const long n = (long)G.nx * G.ny;
+    for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
+        const int ix = (int)(j % G.nx), iy = (int)(j / G.nx);
+        const float X = ((float)ix - G.cxo) * G.dx, Y = ((float)iy - G.cyo) * G.dy;
+        if (fmaf(X, X, Y * Y) <= r2max) {
+            const double d = (double)x[j] - (double)xr[j];
+            s += d * d;
+            c += 1.0;
+        }
+    }
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+            sc[threadIdx.x] += sc[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = ss[0];
+        partial[2 * blockIdx.x + 1] = sc[0];
+        __threadfence();
+        const int done = atomicAdd(&counter[2], 1);
+        if (done == (int)gridDim.x - 1) {
+            __threadfence();
+            double S = 0.0, C = 0.0;
+            for (int b = 0; b < (int)gridDim.x; b++) {
+                S += __ldcg(&partial[2 * b]);
+                C += __ldcg(&partial[2 * b + 1]);
+            }
+            const int it = __ldcg(&counter[0]) / M - 1;
+            trace[it] = C > 0 ? (float)(sqrt(S / C) * hu) : 0.0f;
+            counter[2] = 0;
+        }
+    }
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Workspace {
+    float *x_new, *g, *h, *d_l, *resid, *rho_tab, *trace;
+    int *perm, *counter;
+    double *partial;
+};
+
+ct_status ensure_workspace(ct_geom *g, int max_sub, int T, int n_iter, Workspace &W)
+{
+    const size_t npix = (size_t)g->fan.nx * g->fan.ny;
+    size_t off[10], sz = 0;
+    const size_t sizes[10] = {npix * 4, npix * 4, npix * 4, npix * 4, (size_t)max_sub * g->fan.ns * 4,
+                              (size_t)T * 4, (size_t)(n_iter > 0 ? n_iter : 1) * 4, (size_t)g->fan.na * 4, 16 * 4,
+                              (size_t)kRmsdBlocks * 2 * 8};
+    for (int i = 0; i < 10; i++) {
+        off[i] = sz;
+        sz += align_up(sizes[i]);
+    }
+    if (sz > g->solve_bytes) {
+        cudaFree(g->d_solve);
+        g->d_solve = nullptr;
+        g->solve_bytes = 0;
+        CT_CUDA_TRY(cudaMalloc(&g->d_solve, sz), "allocating solver workspace");
+        g->solve_bytes = sz;
+    }
+    char *b = (char *)g->d_solve;
+    W.x_new = (float *)(b + off[0]);
+    W.g = (float *)(b + off[1]);
+    W.h = (float *)(b + off[2]);
+    W.d_l = (float *)(b + off[3]);
+    W.resid = (float *)(b + off[4]);
+    W.rho_tab = (float *)(b + off[5]);
+    W.trace = (float *)(b + off[6]);
+    W.perm = (int *)(b + off[7]);
+    W.counter = (int *)(b + off[8]);
+    W.partial = (double *)(b + off[9]);
+    return CT_OK;
+}
+
+double rho_continuation(long k, double alpha)
+{
+    if (k == 0) return 1.0;
+    const double q = M_PI / (alpha * (double)(k + 1));
+    return q * std::sqrt(1.0 - 0.25 * q * q);
+}
+
+struct Events {
+    std::vector<cudaEvent_t> ev;
+    ~Events()
+    {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace
+}  // namespace ct
+
+using namespace ct;
+
+extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, const float *w,
+                                             const ct_solve_params *p, float *x, ct_solve_report *rep, void *stream)
+{
+    ct_geom *g = const_cast<ct_geom *>(gc);
+    if (!g || !y || !w || !p || !x) { set_error("ct_relaxed_oslalm_solve: null argument"); return CT_EINVAL; }
+    const int na = g->fan.na;
+    if (p->M < 1 || p->M > na) { set_error("M=%d must be in [1, na=%d]", p->M, na); return CT_EINVAL; }
+    if (p->n_iter < 0 || p->n_iter > 1000000) { set_error("n_iter=%d out of range", p->n_iter); return CT_EINVAL; }
+    if (!(p->alpha >= 1.0f && p->alpha < 2.0f)) { set_error("alpha=%g must be in [1, 2)", p->alpha); return CT_EINVAL; }
+    if (!(p->beta >= 0.0f)) { set_error("beta must be >= 0"); return CT_EINVAL; }
+    if (p->potential < CT_POT_HYPERBOLA || p->potential > CT_POT_QUADRATIC) {
+        set_error("unknown potential %d", p->potential);
+        return CT_EINVAL;
+    }
+    if (p->potential != CT_POT_QUADRATIC && !(p->delta > 0.0f)) { set_error("delta must be > 0"); return CT_EINVAL; }
+    if (p->algorithm != CT_ALG_PROPOSED && p->algorithm != CT_ALG_SIMPLE) {
+        set_error("unknown algorithm %d", p->algorithm);
+        return CT_EINVAL;
+    }
+    if (!p->continuation && !(p->rho_fixed > 0.0f)) { set_error("rho_fixed must be > 0"); return CT_EINVAL; }
+    if (p->stop_rmsd_hu > 0.0f && !p->x_ref) { set_error("stop_rmsd_hu needs x_ref"); return CT_EINVAL; }
+    if ((long)p->n_iter * p->M > 200000000L) { set_error("n_iter * M too large"); return CT_EINVAL; }
+
+    const int M = p->M;
+    // interleaved subsets, stored contiguously: perm = [S_0 | S_1 | ... | S_{M-1}]
+    std::vector<int> perm;
+    std::vector<int> off(M + 1, 0), cnt(M, 0);
+    perm.reserve(na);
+    for (int m = 0; m < M; m++) {
+        off[m] = (int)perm.size();
+        for (int v = m; v < na; v += M) perm.push_back(v);
+        cnt[m] = (int)perm.size() - off[m];
+    }
+    off[M] = na;
+    int max_sub = 0;
+    for (int m = 0; m < M; m++) max_sub = cnt[m] > max_sub ? cnt[m] : max_sub;
+    const long T = (long)p->n_iter * M;
+    std::vector<float> rho((size_t)(T > 0 ? T : 1));
+    for (long t = 0; t < T; t++)
+        rho[t] = (float)(p->continuation ? rho_continuation(t, p->alpha) : (double)p->rho_fixed);
+
+    Workspace W;
+    ct_status st = ensure_workspace(g, max_sub, (int)(T > 0 ? T : 1), p->n_iter, W);
+    if (st != CT_OK) return st;
+
+    cudaStream_t user = (cudaStream_t)stream, ws = nullptr;
+    CT_CUDA_TRY(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking), "creating solver stream");
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamDestroy(s); }
+    } sguard{ws};
+    Events E;
+    const int nev = 3 + p->n_iter;
+    E.ev.resize(nev, nullptr);
+    for (int i = 0; i < nev; i++) CT_CUDA_TRY(cudaEventCreate(&E.ev[i]), "creating events");
+    cudaEvent_t ev_in = E.ev[0], ev_start = E.ev[1], ev_end = E.ev[2];
+
+    CT_CUDA_TRY(cudaEventRecord(ev_in, user), "ordering after caller's stream");
+    CT_CUDA_TRY(cudaStreamWaitEvent(ws, ev_in, 0), "ordering after caller's stream");
+    CT_CUDA_TRY(cudaMemcpyAsync(W.perm, perm.data(), sizeof(int) * na, cudaMemcpyHostToDevice, ws), "upload subsets");
+    CT_CUDA_TRY(cudaMemcpyAsync(W.rho_tab, rho.data(), sizeof(float) * rho.size(), cudaMemcpyHostToDevice, ws),
+                "upload rho");
+    CT_CUDA_TRY(cudaMemsetAsync(W.counter, 0, 16 * sizeof(int), ws), "reset counters");
+
+    SolveDev S;
+    S.x = x;
+    S.x_new = W.x_new;
+    S.g = W.g;
+    S.h = W.h;
+    S.d_l = W.d_l;
+    S.resid = W.resid;
+    S.rho_tab = W.rho_tab;
+    S.counter = W.counter;
+    S.alpha = p->alpha;
+    S.M_scale = (float)M;
+    S.algorithm = p->algorithm;
+    S.nonneg = p->nonneg;
+    const FanDev &G = g->fan;
+    const double R = p->fov_radius > 0.0f ? (double)p->fov_radius : g->fov_radius;
+    const float r2max = (float)(R * R);
+
+    // capture one outer iteration
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (p->n_iter > 0) {
+        CT_CUDA_TRY(cudaStreamBeginCapture(ws, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t e = cudaSuccess;
+        for (int m = 0; m < M && e == cudaSuccess; m++) {
+            e = launch_reg_update(G, S, p->beta, p->delta, p->potential, ws);
+            if (e == cudaSuccess)
+                e = launch_fp(G, FP_RESID, W.x_new, W.perm + off[m], cnt[m], W.resid, y, w, ws);
+            if (e == cudaSuccess) e = launch_bp(G, BP_SOLVE_UPDATE, W.resid, W.perm + off[m], cnt[m], nullptr, 1.0f, 0, &S, ws);
+        }
+        if (e == cudaSuccess && p->x_ref) {
+            rmsd_kernel<<<kRmsdBlocks, 256, 0, ws>>>(G, x, p->x_ref, r2max, W.partial, W.counter, W.trace, M,
+                                                     p->hu_per_unit);
+            e = cudaGetLastError();
+        }
+        cudaError_t e2 = cudaStreamEndCapture(ws, &graph);
+        if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e, "capturing iteration"); }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "instantiating iteration graph");
+        e = cudaGraphUpload(exec, ws);
+        if (e != cudaSuccess) { cudaGraphExecDestroy(exec); return cuda_fail(e, "uploading graph"); }
+    }
+    struct ExecGuard {
+        cudaGraphExec_t e;
+        ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
+    } eguard{exec};
+
+    CT_CUDA_TRY(cudaEventRecord(ev_start, ws), "event");
+    // D_L = diag(A' W A 1) over all views
+    CT_CUDA_TRY(launch_fp(G, FP_ONES_W, nullptr, g->d_views_all, na, g->d_sino_ws, nullptr, w, ws), "D_L forward");
+    CT_CUDA_TRY(launch_bp(G, BP_PLAIN, g->d_sino_ws, g->d_views_all, na, W.d_l, 1.0f, 0, nullptr, ws), "D_L back");
+    // rho = 1, zeta = g = M grad L_M(x), h = D_L x - zeta  (last subset)
+    CT_CUDA_TRY(launch_fp(G, FP_RESID, x, W.perm + off[M - 1], cnt[M - 1], W.resid, y, w, ws), "init forward");
+    CT_CUDA_TRY(launch_bp(G, BP_SOLVE_INIT, W.resid, W.perm + off[M - 1], cnt[M - 1], nullptr, 1.0f, 0, &S, ws),
+                "init back");
+
+    const float tol = p->stop_rmsd_hu > 0.0f ? p->stop_rmsd_hu : 1.0f;
+    int done = 0;
+    for (int it = 0; it < p->n_iter; it++) {
+        CT_CUDA_TRY(cudaGraphLaunch(exec, ws), "graph launch");
+        CT_CUDA_TRY(cudaEventRecord(E.ev[3 + it], ws), "event");
+        done = it + 1;
+        if (p->stop_rmsd_hu > 0.0f) {
+            float r = 0.0f;
+            CT_CUDA_TRY(cudaMemcpyAsync(&r, W.trace + it, sizeof(float), cudaMemcpyDeviceToHost, ws), "read rmsd");
+            CT_CUDA_TRY(cudaStreamSynchronize(ws), "sync");
+            if (r <= tol) break;
+        }
+    }
+    CT_CUDA_TRY(cudaEventRecord(ev_end, ws), "event");
+    CT_CUDA_TRY(cudaEventRecord(ev_in, ws), "event");
+    CT_CUDA_TRY(cudaStreamWaitEvent(user, ev_in, 0), "ordering caller's stream");
+    CT_CUDA_TRY(cudaStreamSynchronize(ws), "solve");
+
+    std::vector<float> trace(done > 0 ? done : 1, -1.0f);
+    if (p->x_ref && done > 0)
+        CT_CUDA_TRY(cudaMemcpy(trace.data(), W.trace, sizeof(float) * done, cudaMemcpyDeviceToHost), "read trace");
+    if (rep) {
+        rep->iters_done = done;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, ev_start, ev_end);
+        rep->seconds = ms * 1e-3;
+        rep->seconds_to_tol = -1.0;
+        rep->rmsd_hu_last = (p->x_ref && done > 0) ? trace[done - 1] : -1.0f;
+        for (int it = 0; it < done; it++) {
+            float mi = 0.0f;
+            cudaEventElapsedTime(&mi, ev_start, E.ev[3 + it]);
+            if (rep->iter_seconds) rep->iter_seconds[it] = mi * 1e-3;
+            if (p->x_ref) {
+                if (rep->rmsd_trace_hu) rep->rmsd_trace_hu[it] = trace[it];
+                if (rep->seconds_to_tol < 0.0 && trace[it] <= tol) rep->seconds_to_tol = mi * 1e-3;
+            }
+        }
+    }
+    return CT_OK;
+}

@@ -1,0 +1,228 @@
+"""Thin Python binding of the C ABI in ``include/ct.h`` (argument marshalling only).
+
+Every computation runs in the CUDA library ``_build/libct.so``; PyTorch only
+supplies device memory and streams.  Importing this module loads the
+library and raises if it is missing -- there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libct.so")
+
+CT_OK, CT_EINVAL, CT_ENOMEM, CT_ECUDA, CT_ETIMEOUT, CT_ENOTSUP = range(6)
+CT_FAN_ARC_2D = 1
+CT_POT_HYPERBOLA, CT_POT_FAIR, CT_POT_QUADRATIC = 0, 1, 2
+CT_ALG_PROPOSED, CT_ALG_SIMPLE = 0, 1
+POTENTIALS = {"hyperbola": CT_POT_HYPERBOLA, "fair": CT_POT_FAIR, "quadratic": CT_POT_QUADRATIC}
+ALGORITHMS = {"proposed": CT_ALG_PROPOSED, "simple": CT_ALG_SIMPLE}
+
+
+class ct_geom_desc(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+        ("offset_x", ctypes.c_double), ("offset_y", ctypes.c_double), ("offset_z", ctypes.c_double),
+        ("ns", ctypes.c_int), ("nt", ctypes.c_int), ("na", ctypes.c_int),
+        ("ds", ctypes.c_double), ("dt", ctypes.c_double),
+        ("offset_s", ctypes.c_double), ("offset_t", ctypes.c_double),
+        ("dso", ctypes.c_double), ("dsd", ctypes.c_double),
+        ("orbit_deg", ctypes.c_double), ("orbit_start_deg", ctypes.c_double),
+        ("pitch", ctypes.c_double),
+    ]
+
+
+class ct_solve_params(ctypes.Structure):
+    _fields_ = [
+        ("M", ctypes.c_int), ("n_iter", ctypes.c_int),
+        ("alpha", ctypes.c_float), ("beta", ctypes.c_float), ("delta", ctypes.c_float),
+        ("potential", ctypes.c_int), ("algorithm", ctypes.c_int), ("nonneg", ctypes.c_int),
+        ("continuation", ctypes.c_int), ("rho_fixed", ctypes.c_float),
+        ("x_ref", ctypes.c_void_p), ("hu_per_unit", ctypes.c_float), ("fov_radius", ctypes.c_float),
+        ("stop_rmsd_hu", ctypes.c_float),
+    ]
+
+
+class ct_solve_report(ctypes.Structure):
+    _fields_ = [
+        ("iters_done", ctypes.c_int),
+        ("seconds", ctypes.c_double), ("seconds_to_tol", ctypes.c_double),
+        ("rmsd_hu_last", ctypes.c_float),
+        ("rmsd_trace_hu", ctypes.POINTER(ctypes.c_float)),
+        ("iter_seconds", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, ip, cint, cfl = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_float
+    sigs = {
+        "ct_geom_create": [ctypes.POINTER(ct_geom_desc), ctypes.POINTER(vp)],
+        "ct_forward": [vp, vp, vp, ip, cint, vp],
+        "ct_back": [vp, vp, vp, ip, cint, cfl, cint, vp],
+        "ct_sqs_diag": [vp, vp, vp, vp],
+        "ct_reg_gradient": [vp, vp, cfl, cfl, cint, vp, vp, vp],
+        "ct_relaxed_oslalm_solve": [vp, vp, vp, ctypes.POINTER(ct_solve_params), vp,
+                                    ctypes.POINTER(ct_solve_report), vp],
+    }
+    for name, args in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = cint
+    lib.ct_geom_destroy.argtypes = [vp]
+    lib.ct_geom_destroy.restype = None
+    lib.ct_last_error.argtypes = []
+    lib.ct_last_error.restype = ctypes.c_char_p
+    lib.ct_version.restype = cint
+    return lib
+
+
+_lib = _load()
+EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_forward", "ct_back", "ct_sqs_diag", "ct_reg_gradient",
+            "ct_relaxed_oslalm_solve", "ct_last_error", "ct_version")
+
+
+class CTError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ct status {status}: {msg}")
+        self.status = status
+
+
+def _check(st: int):
+    if st != CT_OK:
+        raise CTError(st, _lib.ct_last_error().decode())
+
+
+def _ptr(t: torch.Tensor | None, name: str, numel: int | None = None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _views(views, na):
+    if views is None:
+        return None, na
+    arr = (ctypes.c_int * len(views))(*[int(v) for v in views])
+    return arr, len(views)
+
+
+class Geometry:
+    """Owner of a ``ct_geom`` handle (``ct_geom_create`` / ``ct_geom_destroy``)."""
+
+    def __init__(self, *, nx, ny, dx, dy, ns, ds, na, dso, dsd, offset_x=0.0, offset_y=0.0, offset_s=0.0,
+                 orbit_deg=360.0, orbit_start_deg=0.0, kind=CT_FAN_ARC_2D):
+        d = ct_geom_desc()
+        d.kind = kind
+        d.nx, d.ny, d.nz = nx, ny, 1
+        d.dx, d.dy, d.dz = dx, dy, 1.0
+        d.offset_x, d.offset_y = offset_x, offset_y
+        d.ns, d.nt, d.na = ns, 1, na
+        d.ds, d.dt, d.offset_s = ds, 1.0, offset_s
+        d.dso, d.dsd = dso, dsd
+        d.orbit_deg, d.orbit_start_deg = orbit_deg, orbit_start_deg
+        self.desc = d
+        self.nx, self.ny, self.ns, self.na = nx, ny, ns, na
+        h = ctypes.c_void_p()
+        _check(_lib.ct_geom_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+
+    @classmethod
+    def from_fan(cls, g) -> "Geometry":
+        return cls(nx=g.nx, ny=g.ny, dx=g.dx, dy=g.dy, ns=g.ns, ds=g.ds, na=g.na, dso=g.dso, dsd=g.dsd,
+                   offset_x=g.offset_x, offset_y=g.offset_y, offset_s=g.offset_s, orbit_deg=g.orbit_deg,
+                   orbit_start_deg=g.orbit_start_deg)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.ct_geom_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ct_forward(geom: Geometry, x: torch.Tensor, y: torch.Tensor, views=None, stream=None) -> torch.Tensor:
+    arr, nv = _views(views, geom.na)
+    _check(_lib.ct_forward(geom.handle, _ptr(x, "x", geom.nx * geom.ny), _ptr(y, "y", nv * geom.ns), arr, nv,
+                           _stream(stream)))
+    return y
+
+
+def ct_back(geom: Geometry, y: torch.Tensor, x: torch.Tensor, views=None, scale=1.0, accumulate=False,
+            stream=None) -> torch.Tensor:
+    arr, nv = _views(views, geom.na)
+    _check(_lib.ct_back(geom.handle, _ptr(y, "y", nv * geom.ns), _ptr(x, "x", geom.nx * geom.ny), arr, nv,
+                        float(scale), int(bool(accumulate)), _stream(stream)))
+    return x
+
+
+def ct_sqs_diag(geom: Geometry, w: torch.Tensor, d_l: torch.Tensor, stream=None) -> torch.Tensor:
+    _check(_lib.ct_sqs_diag(geom.handle, _ptr(w, "w", geom.na * geom.ns), _ptr(d_l, "d_l", geom.nx * geom.ny),
+                            _stream(stream)))
+    return d_l
+
+
+def ct_reg_gradient(geom: Geometry, x: torch.Tensor, beta: float, delta: float, potential: str | int,
+                    grad: torch.Tensor, curv: torch.Tensor | None = None, stream=None):
+    pot = POTENTIALS[potential] if isinstance(potential, str) else int(potential)
+    n = geom.nx * geom.ny
+    _check(_lib.ct_reg_gradient(geom.handle, _ptr(x, "x", n), float(beta), float(delta), pot,
+                                _ptr(grad, "grad", n), _ptr(curv, "curv", n), _stream(stream)))
+    return grad, curv
+
+
+def ct_relaxed_oslalm_solve(geom: Geometry, y: torch.Tensor, w: torch.Tensor, x: torch.Tensor, *, M: int,
+                            n_iter: int, alpha: float, beta: float, delta: float, potential="hyperbola",
+                            algorithm="proposed", nonneg=True, continuation=True, rho_fixed=0.0,
+                            x_ref: torch.Tensor | None = None, hu_per_unit=1.0, fov_radius=0.0,
+                            stop_rmsd_hu=0.0, stream=None) -> dict:
+    """Relaxed OS-LALM (Algorithm 1 / 2); x is updated in place.  Returns the report as a dict."""
+    n = geom.nx * geom.ny
+    p = ct_solve_params()
+    p.M, p.n_iter, p.alpha, p.beta, p.delta = M, n_iter, alpha, beta, delta
+    p.potential = POTENTIALS[potential] if isinstance(potential, str) else int(potential)
+    p.algorithm = ALGORITHMS[algorithm] if isinstance(algorithm, str) else int(algorithm)
+    p.nonneg, p.continuation, p.rho_fixed = int(bool(nonneg)), int(bool(continuation)), float(rho_fixed)
+    p.x_ref = _ptr(x_ref, "x_ref", n)
+    p.hu_per_unit, p.fov_radius, p.stop_rmsd_hu = hu_per_unit, fov_radius, stop_rmsd_hu
+    r = ct_solve_report()
+    trace = (ctypes.c_float * max(n_iter, 1))()
+    its = (ctypes.c_double * max(n_iter, 1))()
+    r.rmsd_trace_hu = ctypes.cast(trace, ctypes.POINTER(ctypes.c_float))
+    r.iter_seconds = ctypes.cast(its, ctypes.POINTER(ctypes.c_double))
+    _check(_lib.ct_relaxed_oslalm_solve(geom.handle, _ptr(y, "y", geom.na * geom.ns), _ptr(w, "w", geom.na * geom.ns),
+                                        ctypes.byref(p), _ptr(x, "x", n), ctypes.byref(r), _stream(stream)))
+    k = r.iters_done
+    return {
+        "iters_done": k,
+        "seconds": r.seconds,
+        "seconds_to_tol": r.seconds_to_tol,
+        "rmsd_hu_last": r.rmsd_hu_last,
+        "rmsd_trace_hu": list(trace[:k]) if x_ref is not None else [],
+        "iter_seconds": list(its[:k]),
+    }
+
+
+def version() -> int:
+    return int(_lib.ct_version())

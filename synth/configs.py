@@ -91,6 +91,21 @@ class ScanConfig:
         """Potential parameter delta in 1/mm."""
         return self.delta_hu * MU_WATER_PER_MM / 1000.0
 
+    @property
+    def beta_per_mm(self) -> float:
+        """beta for images in 1/mm.
+
+        The workload's beta is read for images expressed in units of water
+        attenuation (x / mu_water, so 1000 HU = 1); since R scales with the
+        square of the image unit, the same problem in 1/mm uses beta / mu_water^2.
+        """
+        return self.beta / MU_WATER_PER_MM ** 2
+
+    @property
+    def hu_per_unit(self) -> float:
+        """HU per 1/mm of attenuation (modified HU: air = 0, water = 1000)."""
+        return 1000.0 / MU_WATER_PER_MM
+
 
 def fan2d_128(seed: int = 0) -> ScanConfig:
     """128x128, 1 mm pixels, 256 bins x 1.0 mm, 180 views, M=10, alpha=1.999, 20 iterations."""

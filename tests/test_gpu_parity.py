@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (from the FP32 arithmetic of the kernels):
+* forward projection, per ray: |gpu - oracle| <= 1e-5 * max(|oracle|, 1e-3 max|oracle|);
+* back-projection, per pixel: the same rule;
+* <A x, y> vs <x, A'y> computed from the GPU outputs: 1e-5 relative;
+* relaxed OS-LALM after a fixed iteration count: RMSD(gpu, oracle) <= 0.1 HU.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import regularizer as oreg
+from oracle import solver as osolver
+from oracle.projector import FanProjector
+
+pytestmark = pytest.mark.gpu
+
+TOL_RAY = 1e-5
+SMALL = synth.FanArcGeometry(nx=37, ny=21, dx=1.1, dy=0.9, ns=61, ds=1.3, na=45, dso=200.0, dsd=350.0,
+                             offset_x=0.3, offset_y=-0.45, offset_s=0.25, orbit_start_deg=7.0, orbit_deg=300.0)
+
+
+@pytest.fixture(scope="module")
+def ct():
+    from paper_1512_04564_gb300 import ct as ctmod
+
+    return ctmod
+
+
+def rel_err(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    den = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+    return float(np.max(np.abs(got - ref) / den))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def phantom_image(g, seed=0):
+    rng = np.random.default_rng(seed)
+    E = [synth.Ellipse(0.0, 0.0, 0.42 * g.nx * g.dx, 0.38 * g.ny * g.dy, 0.2, 0.015)]
+    for _ in range(6):
+        E.append(synth.Ellipse(rng.uniform(-0.2, 0.2) * g.nx * g.dx, rng.uniform(-0.2, 0.2) * g.ny * g.dy,
+                               rng.uniform(0.03, 0.1) * g.nx * g.dx, rng.uniform(0.03, 0.1) * g.ny * g.dy,
+                               rng.uniform(0, 3), rng.uniform(-0.005, 0.005)))
+    x = synth.rasterize_ellipses(E, g.nx, g.ny, g.dx, g.dy, g.offset_x, g.offset_y, oversample=2)
+    return x.astype(np.float32)
+
+
+@pytest.mark.parametrize("gname", ["small", "fan2d_128"])
+@pytest.mark.parametrize("kind", ["phantom", "random"])
+def test_forward_parity(ct, gname, kind):
+    g = SMALL if gname == "small" else synth.fan2d_128().geom
+    x = phantom_image(g) if kind == "phantom" else np.random.default_rng(1).random((g.ny, g.nx)).astype(np.float32)
+    G = ct.Geometry.from_fan(g)
+    y = torch.empty(g.na, g.ns, device="cuda")
+    ct.ct_forward(G, dev(x), y)
+    torch.cuda.synchronize()
+    ref = FanProjector(g).forward(x.astype(np.float64))
+    assert rel_err(y.cpu().numpy(), ref) <= TOL_RAY
+
+
+@pytest.mark.parametrize("gname", ["small", "fan2d_128"])
+def test_back_parity(ct, gname):
+    g = SMALL if gname == "small" else synth.fan2d_128().geom
+    P = FanProjector(g)
+    G = ct.Geometry.from_fan(g)
+    sino = P.forward(phantom_image(g).astype(np.float64)).astype(np.float32)  # positive sinogram
+    x = torch.empty(g.ny, g.nx, device="cuda")
+    ct.ct_back(G, dev(sino), x)
+    torch.cuda.synchronize()
+    ref = P.back(sino.astype(np.float64))
+    assert rel_err(x.cpu().numpy(), ref) <= TOL_RAY
+    # signed data: error relative to the largest pixel
+    r = np.random.default_rng(2).standard_normal((g.na, g.ns)).astype(np.float32)
+    ct.ct_back(G, dev(r), x, scale=0.5)
+    torch.cuda.synchronize()
+    ref = 0.5 * P.back(r.astype(np.float64))
+    assert np.max(np.abs(x.cpu().numpy() - ref)) <= 1e-5 * np.abs(ref).max()
+
+
+def test_adjointness_gpu(ct):
+    g = synth.fan2d_128().geom
+    G = ct.Geometry.from_fan(g)
+    rng = np.random.default_rng(3)
+    x = dev(rng.random((g.ny, g.nx)))
+    yv = dev(rng.random((g.na, g.ns)))
+    Ax = torch.empty(g.na, g.ns, device="cuda")
+    Aty = torch.empty(g.ny, g.nx, device="cuda")
+    ct.ct_forward(G, x, Ax)
+    ct.ct_back(G, yv, Aty)
+    a = float((Ax.double() * yv.double()).sum())
+    b = float((x.double() * Aty.double()).sum())
+    assert abs(a - b) <= 1e-5 * abs(a)
+
+
+def test_view_lists_and_accumulate(ct):
+    g = SMALL
+    P = FanProjector(g)
+    G = ct.Geometry.from_fan(g)
+    x = phantom_image(g)
+    views = [44, 3, 17, 0, 29]
+    y = torch.empty(len(views), g.ns, device="cuda")
+    ct.ct_forward(G, dev(x), y, views=views)
+    torch.cuda.synchronize()
+    assert rel_err(y.cpu().numpy(), P.forward(x.astype(np.float64), views)) <= TOL_RAY
+    base = np.random.default_rng(4).random((g.ny, g.nx)).astype(np.float32)
+    xo = dev(base)
+    ct.ct_back(G, y, xo, views=views, scale=2.0, accumulate=True)
+    torch.cuda.synchronize()
+    ref = base + 2.0 * P.back(y.cpu().numpy().astype(np.float64), views)
+    assert rel_err(xo.cpu().numpy(), ref) <= TOL_RAY
+    one = torch.empty(1, g.ns, device="cuda")
+    ct.ct_forward(G, dev(x), one, views=[13])
+    torch.cuda.synchronize()
+    assert rel_err(one.cpu().numpy(), P.forward(x.astype(np.float64), [13])) <= TOL_RAY
+
+
+def test_zero_image_and_bad_views(ct):
+    g = SMALL
+    G = ct.Geometry.from_fan(g)
+    y = torch.full((g.na, g.ns), 7.0, device="cuda")
+    ct.ct_forward(G, torch.zeros(g.ny, g.nx, device="cuda"), y)
+    torch.cuda.synchronize()
+    assert float(y.abs().max()) == 0.0
+    with pytest.raises(ct.CTError) as e:
+        ct.ct_forward(G, torch.zeros(g.ny, g.nx, device="cuda"), torch.empty(1, g.ns, device="cuda"), views=[g.na])
+    assert e.value.status == ct.CT_EINVAL
+    with pytest.raises(ct.CTError):
+        ct.ct_forward(G, torch.zeros(g.ny, g.nx, device="cuda"), torch.empty(0, g.ns, device="cuda"), views=[])
+
+
+def test_sqs_diag_parity(ct):
+    c = synth.fan2d_128()
+    d = synth.make_scan(c)
+    w = d.w.astype(np.float32)
+    G = ct.Geometry.from_fan(c.geom)
+    dl = torch.empty(c.geom.ny, c.geom.nx, device="cuda")
+    ct.ct_sqs_diag(G, dev(w), dl)
+    torch.cuda.synchronize()
+    P = FanProjector(c.geom)
+    ref = P.back(w.astype(np.float64) * P.forward(np.ones((c.geom.ny, c.geom.nx))))
+    assert rel_err(dl.cpu().numpy(), ref) <= TOL_RAY
+
+
+@pytest.mark.parametrize("pot", ["hyperbola", "fair", "quadratic"])
+def test_reg_gradient_parity(ct, pot):
+    g = SMALL
+    G = ct.Geometry.from_fan(g)
+    x = phantom_image(g) + 1e-4 * np.random.default_rng(5).standard_normal((g.ny, g.nx)).astype(np.float32)
+    beta, delta = 3.0e6, 2e-4
+    gr = torch.empty(g.ny, g.nx, device="cuda")
+    cv = torch.empty(g.ny, g.nx, device="cuda")
+    ct.ct_reg_gradient(G, dev(x), beta, delta, pot, gr, cv)
+    torch.cuda.synchronize()
+    x64 = x.astype(np.float64)
+    rg = oreg.gradient(x64, beta, delta, pot)
+    rc = oreg.curvature(x64, beta, delta, pot)
+    assert np.max(np.abs(gr.cpu().numpy() - rg)) <= 1e-5 * np.abs(rg).max()
+    assert rel_err(cv.cpu().numpy(), rc) <= 1e-5
+
+
+def _solve_case(ct, c, M, alpha, n_iter, algorithm="proposed", continuation=True, rho_fixed=0.0, x0=None):
+    d = synth.make_scan(c)
+    y32, w32 = d.y.astype(np.float32), d.w.astype(np.float32)
+    g = c.geom
+    x0 = np.zeros((g.ny, g.nx), np.float32) if x0 is None else x0.astype(np.float32)
+    prob = osolver.PWLSProblem(FanProjector(g), y32.astype(np.float64), w32.astype(np.float64),
+                               c.beta_per_mm, c.delta, c.potential)
+    xo = osolver.relaxed_os_lalm(prob, x0.astype(np.float64), M, alpha, n_iter, algorithm=algorithm,
+                                 continuation=continuation, rho_fixed=rho_fixed)
+    G = ct.Geometry.from_fan(g)
+    xg = dev(x0)
+    ct.ct_relaxed_oslalm_solve(G, dev(y32), dev(w32), xg, M=M, n_iter=n_iter, alpha=alpha, beta=c.beta_per_mm,
+                               delta=c.delta, potential=c.potential, algorithm=algorithm,
+                               continuation=continuation, rho_fixed=rho_fixed)
+    mask = osolver.fov_mask(g)
+    return osolver.rmsd_hu(xg.cpu().numpy().astype(np.float64), xo, mask, c.hu_per_unit), xo
+
+
+@pytest.mark.parametrize("M,alpha,n_iter,alg", [
+    (10, 1.999, 20, "proposed"),   # the 128x128 workload as specified
+    (5, 1.999, 20, "proposed"),
+    (10, 1.0, 20, "proposed"),
+    (10, 1.999, 10, "simple"),
+    (1, 1.999, 15, "proposed"),
+    (7, 1.5, 6, "proposed"),       # uneven subsets (180 = 7 * 25 + 5)
+])
+def test_solve_parity_fan2d_128(ct, M, alpha, n_iter, alg):
+    rmsd, _ = _solve_case(ct, synth.fan2d_128(), M, alpha, n_iter, algorithm=alg)
+    assert rmsd <= 0.1, rmsd
+
+
+def test_solve_parity_fixed_rho(ct):
+    rmsd, _ = _solve_case(ct, synth.fan2d_128(), 5, 1.999, 8, continuation=False, rho_fixed=0.05)
+    assert rmsd <= 0.1, rmsd
+
+
+def test_solve_report_and_trace(ct):
+    c = synth.fan2d_128()
+    d = synth.make_scan(c)
+    g = c.geom
+    G = ct.Geometry.from_fan(g)
+    y, w = dev(d.y), dev(d.w)
+    xref = torch.zeros(g.ny, g.nx, device="cuda")
+    ct.ct_relaxed_oslalm_solve(G, y, w, xref, M=1, n_iter=40, alpha=1.999, beta=c.beta_per_mm, delta=c.delta)
+    x = torch.zeros(g.ny, g.nx, device="cuda")
+    rep = ct.ct_relaxed_oslalm_solve(G, y, w, x, M=5, n_iter=6, alpha=1.999, beta=c.beta_per_mm, delta=c.delta,
+                                     x_ref=xref, hu_per_unit=c.hu_per_unit)
+    assert rep["iters_done"] == 6 and len(rep["rmsd_trace_hu"]) == 6
+    mask = osolver.fov_mask(g)
+    direct = osolver.rmsd_hu(x.cpu().numpy().astype(np.float64), xref.cpu().numpy().astype(np.float64), mask,
+                             c.hu_per_unit)
+    assert abs(rep["rmsd_trace_hu"][-1] - direct) <= 1e-4 * max(direct, 1.0)
+    assert all(b >= a for a, b in zip(rep["iter_seconds"], rep["iter_seconds"][1:]))
+    # early stop at a loose tolerance
+    x2 = torch.zeros(g.ny, g.nx, device="cuda")
+    tol = rep["rmsd_trace_hu"][2] + 1e-3
+    rep2 = ct.ct_relaxed_oslalm_solve(G, y, w, x2, M=5, n_iter=6, alpha=1.999, beta=c.beta_per_mm, delta=c.delta,
+                                      x_ref=xref, hu_per_unit=c.hu_per_unit, stop_rmsd_hu=tol)
+    assert rep2["iters_done"] <= 3 and rep2["seconds_to_tol"] > 0
+
+
+def test_full_size_sampled_parity(ct):
+    """512x512, 984 views x 888 bins (the clinical-scale workload): sampled rays and pixels."""
+    c = synth.fan2d_512()
+    g = c.geom
+    d = synth.make_scan(c)
+    x = synth.rasterize_ellipses(d.ellipses, g.nx, g.ny, g.dx, g.dy, oversample=2).astype(np.float32)
+    G = ct.Geometry.from_fan(g)
+    y = torch.empty(g.na, g.ns, device="cuda")
+    ct.ct_forward(G, dev(x), y)
+    yb = y.cpu().numpy()
+    rng = np.random.default_rng(6)
+    rv = rng.integers(0, g.na, 48)
+    rb = rng.integers(0, g.ns, 48)
+    P = FanProjector(g)
+    ref = P.forward_rays(x.astype(np.float64), rv, rb)
+    scale = np.abs(yb).max()
+    den = np.maximum(np.abs(ref), 1e-3 * scale)
+    assert np.max(np.abs(yb[rv, rb] - ref) / den) <= TOL_RAY
+    # back-projection of the weighted residual-like sinogram at sampled pixels (a 41-subset's views)
+    views = list(range(7, g.na, 41))
+    sino = (d.w[views] * 1e-5).astype(np.float32)
+    xb = torch.empty(g.ny, g.nx, device="cuda")
+    ct.ct_back(G, dev(sino), xb, views=views)
+    pix = rng.integers(0, g.nx * g.ny, 48)
+    refp = P.back_pixels(sino.astype(np.float64), views, pix)
+    got = xb.cpu().numpy().reshape(-1)[pix]
+    den = np.maximum(np.abs(refp), 1e-3 * np.abs(xb.cpu().numpy()).max())
+    assert np.max(np.abs(got - refp) / den) <= TOL_RAY
