@@ -87,6 +87,21 @@ ct_status ct_geom_create(const ct_geom_desc *desc, ct_geom **out);
  * only once no work using it is pending on any stream. */
 void ct_geom_destroy(ct_geom *g);
 
+/* Build the resident system matrix of a 2-D geometry: the same SF weights
+ * a_ij that the projectors otherwise evaluate on the fly (Sec. III: A is the
+ * forward projection matrix of the scan), stored once in device memory
+ * owned by g as (1) ray-major compressed rows of (pixel, a_ij) for the
+ * ray-driven forward projector and (2) per-(view, pixel) footprint
+ * trapezoids for the voxel-driven back-projector.  Afterwards ct_forward,
+ * ct_back, ct_sqs_diag and ct_relaxed_oslalm_solve stream it instead of
+ * recomputing footprints; results stay within FP32 rounding of the
+ * on-the-fly path.  max_bytes: refuse with CT_ENOMEM (nothing kept) when the
+ * matrix needs more; 0 means "whatever device memory allows".  bytes_out
+ * (optional host pointer) receives the matrix size.  Runs on `stream` and
+ * synchronises it.  Calling it again is a no-op.  Errors: CT_EINVAL,
+ * CT_ENOMEM, CT_ECUDA. */
+ct_status ct_geom_precompute(ct_geom *g, unsigned long long max_bytes, unsigned long long *bytes_out, void *stream);
+
 /* Forward projection y = A_V x (Sec. III, Eq. (ct_problem); SF footprints,
  * ray-driven).  x: device [ny][nx]; y: device [nviews][ns], row k is view
  * views[k].  views: host array of nviews indices in [0, na), or NULL for all

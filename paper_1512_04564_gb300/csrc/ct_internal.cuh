@@ -26,11 +26,17 @@ struct FanDev {
     float dso;
     float x_edge0, y_edge0;   // x of the left edge of column 0, y of the lower edge of row 0 (mm)
     float cxo, cyo;           // (nx-1)/2 - offset_x, (ny-1)/2 - offset_y (pixel index of the origin)
+    int max_span;             // upper bound on the detector cells one pixel footprint overlaps
     const float4 *anchor;     // [na][ntx*nty]: view-frame (t_par, t_perp) of the tile centre,
                               // and its detector coordinate u = gamma/dgamma + (ns-1)/2 - offset_s
                               // split into hi + lo floats (FP64-derived)
     const float2 *view_cs;    // [na]: (cos beta, sin beta)
     const float *view_beta;   // [na]: beta in [0, 2 pi)
+    // resident system matrix (ct_geom_precompute); null when footprints are computed on the fly
+    const float4 *foot_t;     // [na][ntiles][256]: trapezoid vertices t0..t3 (cells, relative to n)
+    const float2 *foot_an;    // [na][ntiles][256]: amplitude, n (int bits)
+    const long long *row_ptr; // [na*ns + 1]: start of each ray's entries
+    const int2 *row_ent;      // (pixel index, a_ij bits), ray-major, march order within a ray
 };
 
 // Solver state shared by the kernels of one subiteration (device pointers).
@@ -63,6 +69,12 @@ struct ct_geom {
     size_t solve_bytes = 0;
     void *d_solve = nullptr;
     double fov_radius = 0.0;
+    // resident system matrix (ct_geom_precompute)
+    long long *d_row_ptr = nullptr;
+    int2 *d_row_ent = nullptr;
+    float4 *d_foot_t = nullptr;
+    float2 *d_foot_an = nullptr;
+    unsigned long long matrix_bytes = 0;
     int device = 0;
 };
 
@@ -126,7 +138,7 @@ __device__ __forceinline__ Footprint sf_footprint(const FanDev &G, float cb, flo
     const float f = (A.z - nf) + (A.w + du);  // centre's detector coordinate relative to cell nf
     // corners: angle relative to the centre, atan(cross(c, o) / (|c|^2 + c.o))
     const float r2 = fmaf(cpar, cpar, cperp * cperp);
-    const float ir2 = 1.0f / r2;
+    const float ir2 = __frcp_rn(r2);
     const float xpar = G.hx * cb, xperp = -G.hx * sb;  // +half pixel along x, view frame
     const float ypar = G.hy * sb, yperp = G.hy * cb;   // +half pixel along y
     const float cx = fmaf(cpar, xperp, -cperp * xpar), cy = fmaf(cpar, yperp, -cperp * ypar);
@@ -151,12 +163,12 @@ __device__ __forceinline__ Footprint sf_footprint(const FanDev &G, float cb, flo
     F.t1 = fminf(m0, m1);
     F.t2 = fmaxf(m0, m1);
     const float w1 = F.t1 - F.t0, w3 = F.t3 - F.t2;
-    F.i2w1 = w1 > 0.0f ? 0.5f / w1 : 0.0f;
-    F.i2w3 = w3 > 0.0f ? 0.5f / w3 : 0.0f;
+    F.i2w1 = w1 > 0.0f ? __fdividef(0.5f, w1) : 0.0f;
+    F.i2w3 = w3 > 0.0f ? __fdividef(0.5f, w3) : 0.0f;
     // amplitude: chord through the pixel along the centre ray = |c| / max(|c_x|/dx, |c_y|/dy)
     const float imx = fabsf(fmaf(cpar, cb, -cperp * sb)) * G.inv_dx;
     const float imy = fabsf(fmaf(cpar, sb, cperp * cb)) * G.inv_dy;
-    F.amp = sqrtf(r2) / fmaxf(imx, imy);
+    F.amp = __fdividef(r2 * rsqrtf(r2), fmaxf(imx, imy));
     F.n = (int)nf;
     return F;
 }
@@ -182,6 +194,77 @@ __device__ __forceinline__ Footprint pixel_footprint(const FanDev &G, int v, flo
     return sf_footprint(G, cb, sb, A, ox, oy);
 }
 
+// Weight a_ij of pixel footprint F in detector cell s.
+__device__ __forceinline__ float cell_weight(const Footprint &F, int s)
+{
+    const float j = (float)(s - F.n);
+    return F.amp * (trap_cdf(F, j + 0.5f) - trap_cdf(F, j - 0.5f));
+}
+
+constexpr float kRangePad = 0.02f;  // pixels of padding on a wedge's row/column range
+
+// Visit the pixels whose squares can meet the fan wedge of cell s in view v:
+// shallow rays march the columns (steep rays the rows) in [seg/nseg, (seg+1)/nseg)
+// of the image and visit, in each, the rows (columns) between the wedge's two
+// edge lines (padded by kRangePad pixels).  visit(ix, iy) is called in march order.
+template <class Visit>
+__device__ __forceinline__ void ray_visit(const FanDev &G, int v, int s, int seg, int nseg, Visit &&visit)
+{
+    const float2 cs = __ldg(&G.view_cs[v]);
+    const float beta = __ldg(&G.view_beta[v]);
+    const float phi = beta + fmaf((float)s, G.dgamma, G.gamma0);
+    float sp, cp;
+    sincosf(phi, &sp, &cp);
+    const float Sx = -G.dso * cs.x, Sy = -G.dso * cs.y;
+    const float phl = phi - 0.5f * G.dgamma, phh = phi + 0.5f * G.dgamma;
+    if (fabsf(cp) >= fabsf(sp)) {
+        // shallow ray: the wedge's edges are y = Sy + (x - Sx) tan(phi -+ dgamma/2)
+        const float tl = tanf(phl), th = tanf(phh);
+        const int c0 = seg * G.nx / nseg, c1 = (seg + 1) * G.nx / nseg;
+        for (int ix = c0; ix < c1; ix++) {
+            const float xl = fmaf((float)ix, G.dx, G.x_edge0) - Sx, xr = xl + G.dx;
+            const float y1 = fmaf(xl, tl, Sy), y2 = fmaf(xr, tl, Sy);
+            const float y3 = fmaf(xl, th, Sy), y4 = fmaf(xr, th, Sy);
+            const float ylo = (fminf(fminf(y1, y2), fminf(y3, y4)) - G.y_edge0) * G.inv_dy - kRangePad;
+            const float yhi = (fmaxf(fmaxf(y1, y2), fmaxf(y3, y4)) - G.y_edge0) * G.inv_dy + kRangePad;
+            const int iy0 = max(0, (int)floorf(fmaxf(ylo, -1.0f)));
+            const int iy1 = min(G.ny - 1, (int)floorf(fminf(yhi, (float)G.ny)));
+            for (int iy = iy0; iy <= iy1; iy++) visit(ix, iy);
+        }
+    } else {
+        // steep ray: x = Sx + (y - Sy) cot(phi -+ dgamma/2)
+        const float tl = cosf(phl) / sinf(phl), th = cosf(phh) / sinf(phh);
+        const int r0 = seg * G.ny / nseg, r1 = (seg + 1) * G.ny / nseg;
+        for (int iy = r0; iy < r1; iy++) {
+            const float yb = fmaf((float)iy, G.dy, G.y_edge0) - Sy, yt = yb + G.dy;
+            const float x1 = fmaf(yb, tl, Sx), x2 = fmaf(yt, tl, Sx);
+            const float x3 = fmaf(yb, th, Sx), x4 = fmaf(yt, th, Sx);
+            const float xlo = (fminf(fminf(x1, x2), fminf(x3, x4)) - G.x_edge0) * G.inv_dx - kRangePad;
+            const float xhi = (fmaxf(fmaxf(x1, x2), fmaxf(x3, x4)) - G.x_edge0) * G.inv_dx + kRangePad;
+            const int ix0 = max(0, (int)floorf(fmaxf(xlo, -1.0f)));
+            const int ix1 = min(G.nx - 1, (int)floorf(fminf(xhi, (float)G.nx)));
+            for (int ix = ix0; ix <= ix1; ix++) visit(ix, iy);
+        }
+    }
+}
+
+// Stored footprint of the pixel at position `local` (0..255, row-major in its
+// 16x16 tile) of tile `tile` in view v; same values sf_footprint returns.
+__device__ __forceinline__ Footprint stored_footprint(const FanDev &G, int v, int tile, int local)
+{
+    const size_t i = ((size_t)v * (G.ntx * G.nty) + tile) * (kTile * kTile) + local;
+    const float4 t = __ldcs(&G.foot_t[i]);
+    const float2 an = __ldcs(&G.foot_an[i]);
+    Footprint F;
+    F.t0 = t.x; F.t1 = t.y; F.t2 = t.z; F.t3 = t.w;
+    const float w1 = F.t1 - F.t0, w3 = F.t3 - F.t2;
+    F.i2w1 = w1 > 0.0f ? __fdividef(0.5f, w1) : 0.0f;
+    F.i2w3 = w3 > 0.0f ? __fdividef(0.5f, w3) : 0.0f;
+    F.amp = an.x;
+    F.n = __float_as_int(an.y);
+    return F;
+}
+
 // ---------------------------------------------------------------- launchers (projectors.cu)
 
 enum FpMode { FP_PLAIN = 0, FP_RESID = 1, FP_ONES_W = 2 };
@@ -196,6 +279,8 @@ cudaError_t launch_reg_gradient(const FanDev &G, const float *x, float beta, flo
                                 float *grad, float *curv, cudaStream_t st);
 cudaError_t launch_reg_update(const FanDev &G, const SolveDev &S, float beta, float delta, int potential,
                               cudaStream_t st);
+
+cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t st, bool *too_big);
 
 ct_status validate_views(const ct_geom *g, const int *views, int nviews);
 ct_status stage_views(const ct_geom *g, const int *views, int nviews, const int **dev_views, cudaStream_t st);

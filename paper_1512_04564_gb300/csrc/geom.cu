@@ -78,6 +78,10 @@ static void free_geom(ct_geom *g)
     cudaFree(g->d_views_stage);
     cudaFree(g->d_sino_ws);
     cudaFree(g->d_solve);
+    cudaFree(g->d_row_ptr);
+    cudaFree(g->d_row_ent);
+    cudaFree(g->d_foot_t);
+    cudaFree(g->d_foot_an);
     delete g;
 }
 
@@ -141,6 +145,8 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     F.x_edge0 = (float)((-0.5 - cxo) * d->dx);
     F.y_edge0 = (float)((-0.5 - cyo) * d->dy);
     F.cxo = (float)cxo; F.cyo = (float)cyo;
+    // widest footprint: a pixel diagonal at the smallest source distance, plus partial cells at both ends
+    F.max_span = (int)std::ceil(std::sqrt(d->dx * d->dx + d->dy * d->dy) / ((d->dso - r_img) * dg)) + 2;
 
     const int na = d->na, ntiles = F.ntx * F.nty;
     std::vector<float2> cs(na);

@@ -1,0 +1,199 @@
+// Resident system matrix of a 2-D fan-beam geometry (ct_geom_precompute).
+//
+// The SF weights a_ij (Sec. III, Eq. (ct_problem): A is the projection
+// matrix) depend on the geometry only.  For a 2-D scan the whole matrix fits
+// in HBM (about 15 GB for 512x512 pixels, 984 views x 888 cells), so it is
+// evaluated once with the same device functions the on-the-fly projectors
+// use and then streamed:
+//   * ray-major rows: for every ray, the (pixel, a_ij) pairs in the order the
+//     ray kernel visits them (march order), for the ray-driven projector;
+//   * per-(view, pixel) footprints: trapezoid vertices, amplitude and base
+//     cell, laid out tile by tile, for the voxel-driven back-projector.
+// Building it: count each ray's nonzero weights, exclusive-scan the counts
+// into row pointers, fill the rows, store the footprints.
+#include <vector>
+
+#include "ct_internal.cuh"
+
+namespace ct {
+namespace {
+
+__global__ void __launch_bounds__(256) matrix_count_kernel(FanDev G, long long *__restrict__ counts)
+{
+    const long ray = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= (long)G.na * G.ns) return;
+    const int v = (int)(ray / G.ns), s = (int)(ray - (long)v * G.ns);
+    const float2 cs = __ldg(&G.view_cs[v]);
+    long long c = 0;
+    ray_visit(G, v, s, 0, 1, [&](int ix, int iy) {
+        const Footprint F = pixel_footprint(G, v, cs.x, cs.y, ix, iy);
+        if (cell_weight(F, s) != 0.0f) c++;
+    });
+    counts[ray] = c;
+}
+
+__global__ void __launch_bounds__(256) matrix_fill_kernel(FanDev G, const long long *__restrict__ row_ptr,
+                                                          int2 *__restrict__ ent)
+{
+    const long ray = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= (long)G.na * G.ns) return;
+    const int v = (int)(ray / G.ns), s = (int)(ray - (long)v * G.ns);
+    const float2 cs = __ldg(&G.view_cs[v]);
+    long long p = row_ptr[ray];
+    const long long end = row_ptr[ray + 1];
+    ray_visit(G, v, s, 0, 1, [&](int ix, int iy) {
+        const Footprint F = pixel_footprint(G, v, cs.x, cs.y, ix, iy);
+        const float wv = cell_weight(F, s);
+        if (wv != 0.0f && p < end) ent[p++] = make_int2(iy * G.nx + ix, __float_as_int(wv));
+    });
+}
+
+__global__ void __launch_bounds__(256) matrix_foot_kernel(FanDev G, float4 *__restrict__ ft, float2 *__restrict__ fan)
+{
+    const int ntiles = G.ntx * G.nty;
+    const int v = blockIdx.x / ntiles, tile = blockIdx.x - v * ntiles;
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    const float2 cs = __ldg(&G.view_cs[v]);
+    const float4 A = __ldg(&G.anchor[(size_t)v * (G.ntx * G.nty) + tile]);
+    const Footprint F = sf_footprint(G, cs.x, cs.y, A, ((float)lx - kTileHalf) * G.dx, ((float)ly - kTileHalf) * G.dy);
+    const size_t i = ((size_t)v * (G.ntx * G.nty) + tile) * (kTile * kTile) + threadIdx.x;
+    ft[i] = make_float4(F.t0, F.t1, F.t2, F.t3);
+    fan[i] = make_float2(F.amp, __int_as_float(F.n));
+}
+
+// in-place exclusive scan of blocks of 1024 values; block totals to sums
+__global__ void __launch_bounds__(1024) scan_block_kernel(long long *__restrict__ a, long long n,
+                                                          long long *__restrict__ sums)
+{
+    __shared__ long long sm[32];
+    const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long v = i < n ? a[i] : 0;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) sm[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long t = sm[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        sm[lane] = t;
+    }
+    __syncthreads();
+    const long long incl = x + (warp > 0 ? sm[warp - 1] : 0);
+    if (i < n) a[i] = incl - v;
+    if (threadIdx.x == 1023) sums[blockIdx.x] = incl;
+}
+
+__global__ void __launch_bounds__(1024) scan_add_kernel(long long *__restrict__ a, long long n,
+                                                        const long long *__restrict__ sums)
+{
+    const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) a[i] += sums[blockIdx.x];
+}
+
+cudaError_t exclusive_scan(long long *a, long long n, cudaStream_t st)
+{
+    const long long nb = (n + 1023) / 1024;
+    long long *sums = nullptr;
+    cudaError_t e = cudaMalloc(&sums, sizeof(long long) * nb);
+    if (e != cudaSuccess) return e;
+    scan_block_kernel<<<(unsigned)nb, 1024, 0, st>>>(a, n, sums);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && nb > 1) {
+        e = exclusive_scan(sums, nb, st);
+        if (e == cudaSuccess) {
+            scan_add_kernel<<<(unsigned)nb, 1024, 0, st>>>(a, n, sums);
+            e = cudaGetLastError();
+        }
+    }
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(sums);
+    return e != cudaSuccess ? e : e2;
+}
+
+}  // namespace
+
+cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t st, bool *too_big)
+{
+    *too_big = false;
+    FanDev G = g->fan;
+    const long long R = (long long)G.na * G.ns;
+    const size_t ntile_px = (size_t)G.ntx * G.nty * kTile * kTile;
+    long long *rp = nullptr;
+    int2 *ent = nullptr;
+    float4 *ft = nullptr;
+    float2 *fan = nullptr;
+    cudaError_t e = cudaMalloc(&rp, sizeof(long long) * (R + 1));
+    if (e != cudaSuccess) return e;
+    auto fail = [&](cudaError_t err) {
+        cudaFree(rp);
+        cudaFree(ent);
+        cudaFree(ft);
+        cudaFree(fan);
+        return err;
+    };
+    if ((e = cudaMemsetAsync(rp + R, 0, sizeof(long long), st)) != cudaSuccess) return fail(e);
+    matrix_count_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(G, rp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    if ((e = exclusive_scan(rp, R + 1, st)) != cudaSuccess) return fail(e);
+    long long nnz = 0;
+    if ((e = cudaMemcpy(&nnz, rp + R, sizeof(long long), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
+    const unsigned long long bytes = (unsigned long long)(R + 1) * 8ull + (unsigned long long)nnz * 8ull +
+                                     (unsigned long long)G.na * ntile_px * 24ull;
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    if ((max_bytes && bytes > max_bytes) || bytes > (unsigned long long)(0.9 * (double)free_b)) {
+        *too_big = true;
+        g->matrix_bytes = bytes;
+        return fail(cudaSuccess);
+    }
+    if ((e = cudaMalloc(&ent, sizeof(int2) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&ft, sizeof(float4) * G.na * ntile_px)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&fan, sizeof(float2) * G.na * ntile_px)) != cudaSuccess) return fail(e);
+    matrix_fill_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(G, rp, ent);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    matrix_foot_kernel<<<(unsigned)((size_t)G.ntx * G.nty * G.na), 256, 0, st>>>(G, ft, fan);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    g->d_row_ptr = rp;
+    g->d_row_ent = ent;
+    g->d_foot_t = ft;
+    g->d_foot_an = fan;
+    g->matrix_bytes = bytes;
+    g->fan.row_ptr = rp;
+    g->fan.row_ent = ent;
+    g->fan.foot_t = ft;
+    g->fan.foot_an = fan;
+    return cudaSuccess;
+}
+
+}  // namespace ct
+
+using namespace ct;
+
+extern "C" ct_status ct_geom_precompute(ct_geom *g, unsigned long long max_bytes, unsigned long long *bytes_out,
+                                        void *stream)
+{
+    if (!g) { set_error("ct_geom_precompute: null geometry"); return CT_EINVAL; }
+    if (!g->d_row_ptr) {
+        bool too_big = false;
+        cudaError_t e = build_matrix(g, max_bytes, (cudaStream_t)stream, &too_big);
+        if (e != cudaSuccess) return cuda_fail(e, "building the system matrix");
+        if (too_big) {
+            if (bytes_out) *bytes_out = g->matrix_bytes;
+            set_error("system matrix needs %llu bytes (limit %llu, or 90%% of free device memory)", g->matrix_bytes,
+                      max_bytes);
+            return CT_ENOMEM;
+        }
+    }
+    if (bytes_out) *bytes_out = g->matrix_bytes;
+    return CT_OK;
+}

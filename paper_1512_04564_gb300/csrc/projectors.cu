@@ -6,12 +6,21 @@
 // pair is matched.  Both are FP32-ALU bound gathers (no tensor-core
 // contraction exists in them).
 //
-// Forward projector: each detector cell (ray) is owned by 8 lanes of one
-// warp, each lane marching 1/8 of the image columns (or rows, for steep
-// rays) through the cell's fan wedge; the 8 partial sums are combined with
-// warp shuffles.  No atomics.  Fused epilogues: plain y = A x, the weighted
-// residual r = w (A x - y) of the subset gradient (Eq. (ct_substitution)), and
-// w * (A 1) for the SQS diagonal.
+// Forward projector (ray-driven, cell-owned outputs, no atomics):
+// * bundle kernel: one CTA per (view, 32 adjacent detector cells); its 8 warps
+//   split the image columns (rows, for steep bundles) that the bundle's fan
+//   wedge crosses.  In each round a warp packs the next 32 wedge pixels
+//   (across columns, by a warp prefix scan) one per lane, evaluates each
+//   pixel's footprint once and stages its cell weights in shared memory;
+//   then every lane, as the owner of one cell, gathers the weights of the
+//   pixels its own wedge crosses.  The 8 warps' partial sums are added in a
+//   fixed order, so results are deterministic.
+// * ray kernel (fallback for detectors so fine that one footprint covers more
+//   than kMaxSpan cells): 8 lanes per cell march 1/8 of the columns each,
+//   evaluating every wedge pixel's footprint, combined by warp shuffles.
+// Fused epilogues: plain y = A x, the weighted residual r = w (A x - y) of
+// the subset gradient (Eq. (ct_substitution)), and w (A 1) for the SQS
+// diagonal.
 //
 // Back-projector: one CTA per 16x16 pixel tile (one anchor per view), one
 // pixel per thread, gathering from the cells its footprint covers.  Fused
@@ -26,20 +35,208 @@ namespace ct {
 namespace {
 
 constexpr int kFpThreads = 256;
-constexpr int kFpSeg = 8;  // lanes per ray
-constexpr float kRangePad = 0.02f;  // pixels of padding on the wedge's row/column range
+constexpr int kFpSeg = 8;  // lanes per ray (ray kernel)
+constexpr int kBundleWarps = 8;     // warps per bundle CTA
+constexpr int kMaxSpan = 12;        // cells per staged footprint (bundle kernel)
+constexpr int kMaxMarch = 2048;     // longest march axis the bundle kernel stages
+constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ float cell_weight(const Footprint &F, int s)
+// Marching frame of a bundle: "march" is the axis the wedge is walked along
+// (x for shallow bundles, y for steep ones), "cross" the other axis.
+struct March {
+    float m_edge0, m_d;     // march axis: edge of index 0, pixel size
+    float c_edge0, c_invd;  // cross axis: edge of index 0, 1/pixel size
+    float Sm, Sc;           // source position (march, cross)
+    int n_march, n_cross;
+    bool col;
+};
+
+// Cross-axis pixel range [lo, hi] of the wedge between the lines of slopes T1, T2
+// (cross = Sc + (march - Sm) T) inside the march slab of index a.
+__device__ __forceinline__ void wedge_range(const March &M, int a, float T1, float T2, int &lo, int &hi)
 {
-    const float j = (float)(s - F.n);
-    return F.amp * (trap_cdf(F, j + 0.5f) - trap_cdf(F, j - 0.5f));
+    const float ml = fmaf((float)a, M.m_d, M.m_edge0) - M.Sm, mr = ml + M.m_d;
+    const float c1 = fmaf(ml, T1, M.Sc), c2 = fmaf(mr, T1, M.Sc);
+    const float c3 = fmaf(ml, T2, M.Sc), c4 = fmaf(mr, T2, M.Sc);
+    const float clo = (fminf(fminf(c1, c2), fminf(c3, c4)) - M.c_edge0) * M.c_invd - kRangePad;
+    const float chi = (fmaxf(fmaxf(c1, c2), fmaxf(c3, c4)) - M.c_edge0) * M.c_invd + kRangePad;
+    lo = max(0, (int)floorf(fmaxf(clo, -1.0f)));
+    hi = min(M.n_cross - 1, (int)floorf(fminf(chi, (float)M.n_cross)));
+}
+
+__device__ __forceinline__ float march_slope(const March &M, float ang)
+{
+    float sn, cn;
+    sincosf(ang, &sn, &cn);
+    return M.col ? sn / cn : cn / sn;
+}
+
+// Number of entries of the warp-wide nondecreasing array `incl` that are <= key (< 32 if incl[31] > key).
+__device__ __forceinline__ int count_le(int incl, int key)
+{
+    int pos = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const int v = __shfl_sync(kFull, incl, pos + step - 1);
+        if (v <= key) pos += step;
+    }
+    return pos;
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kFpThreads) fp_fan2d_kernel(FanDev G, const float *__restrict__ x,
-                                                              const int *__restrict__ views, int nviews,
-                                                              float *__restrict__ out, const float *__restrict__ y,
-                                                              const float *__restrict__ w)
+__global__ void __launch_bounds__(kBundleWarps * 32, 5) fp_bundle_kernel(FanDev G, const float *__restrict__ x,
+                                                                       const int *__restrict__ views, int nviews,
+                                                                       float *__restrict__ out,
+                                                                       const float *__restrict__ y,
+                                                                       const float *__restrict__ w)
+{
+    __shared__ int s_pre[kMaxMarch + 1];  // pixels of the bundle's wedge before march index a
+    __shared__ int s_lo[kMaxMarch];       // first wedge pixel (cross index) at march index a
+    __shared__ float s_w[kBundleWarps][32][kMaxSpan + 1];
+    __shared__ int s_c[kBundleWarps][32];  // first cell (relative to s0) of each staged pixel
+    __shared__ int s_n[kBundleWarps][32];  // number of staged cells of each pixel
+    __shared__ int s_part[kBundleWarps];
+    __shared__ float s_acc[kBundleWarps][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = (G.ns + 31) >> 5;
+    const int k = blockIdx.x / nb;
+    const int s0 = (blockIdx.x - k * nb) * 32;
+    const int v = __ldg(&views[k]);
+    const float2 cs = __ldg(&G.view_cs[v]);
+    const float beta = __ldg(&G.view_beta[v]);
+    const int s_last = min(s0 + 31, G.ns - 1);
+    const float a_lo = beta + fmaf((float)s0 - 0.5f, G.dgamma, G.gamma0);
+    const float a_hi = beta + fmaf((float)s_last + 0.5f, G.dgamma, G.gamma0);
+    float sn, cn;
+    sincosf(0.5f * (a_lo + a_hi), &sn, &cn);
+    March M;
+    M.col = fabsf(cn) >= fabsf(sn);
+    const float Sx = -G.dso * cs.x, Sy = -G.dso * cs.y;
+    if (M.col) {
+        M.m_edge0 = G.x_edge0; M.m_d = G.dx; M.c_edge0 = G.y_edge0; M.c_invd = G.inv_dy;
+        M.Sm = Sx; M.Sc = Sy; M.n_march = G.nx; M.n_cross = G.ny;
+    } else {
+        M.m_edge0 = G.y_edge0; M.m_d = G.dy; M.c_edge0 = G.x_edge0; M.c_invd = G.inv_dx;
+        M.Sm = Sy; M.Sc = Sx; M.n_march = G.ny; M.n_cross = G.nx;
+    }
+    const int nm = M.n_march;
+    {   // wedge pixel counts per march index, then an exclusive scan over the CTA
+        const float TB1 = march_slope(M, a_lo), TB2 = march_slope(M, a_hi);
+        const int per = (nm + kBundleWarps * 32 - 1) / (kBundleWarps * 32);
+        const int a0 = threadIdx.x * per;
+        int run = 0;
+        for (int i = 0; i < per; i++) {
+            const int a = a0 + i;
+            if (a < nm) {
+                int lo, hi;
+                wedge_range(M, a, TB1, TB2, lo, hi);
+                s_lo[a] = lo;
+                const int c = max(hi - lo + 1, 0);
+                s_pre[a] = c;
+                run += c;
+            }
+        }
+        int incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_part[warp] = incl;
+        __syncthreads();
+        int base = 0;
+        for (int q = 0; q < warp; q++) base += s_part[q];
+        int pos = base + incl - run;
+        for (int i = 0; i < per; i++) {
+            const int a = a0 + i;
+            if (a < nm) {
+                const int c = s_pre[a];
+                s_pre[a] = pos;
+                pos += c;
+            }
+        }
+        if (threadIdx.x == kBundleWarps * 32 - 1) s_pre[nm] = pos;
+        __syncthreads();
+    }
+    const int T = s_pre[nm];
+    const int s_mine = s0 + lane;
+    const float my_a = beta + fmaf((float)s_mine, G.dgamma, G.gamma0);
+    const float t1 = march_slope(M, my_a - 0.5f * G.dgamma), t2 = march_slope(M, my_a + 0.5f * G.dgamma);
+    float(*sw)[kMaxSpan + 1] = s_w[warp];
+    int *scf = s_c[warp];
+    int *sns = s_n[warp];
+    float acc = 0.0f;
+    // this warp's equal share of the wedge pixels
+    const int t_end = (int)(((long)(warp + 1) * T) / kBundleWarps);
+    int t0 = (int)(((long)warp * T) / kBundleWarps);
+    int col = 0;
+    while (t0 < t_end) {
+        while (s_pre[col + 1] <= t0) col++;  // march index holding task t0 (uniform)
+        // lane l: end (exclusive) task index of march index col + l
+        const int e = s_pre[min(col + lane + 1, nm)];
+        const int n = min(min(32, t_end - t0), __shfl_sync(kFull, e, 31) - t0);
+        const int t = t0 + lane;
+        const int ls = min(count_le(e, t), 31);
+        const int c = col + ls;
+        int cf = 1 << 20, cnt = 0;
+        if (lane < n) {  // pixel role
+            const int bc = s_lo[c] + (t - s_pre[c]);
+            const int ix = M.col ? c : bc, iy = M.col ? bc : c;
+            const float xv = (MODE == FP_ONES_W) ? 1.0f : __ldg(&x[(size_t)iy * G.nx + ix]);
+            if (xv != 0.0f) {
+                const Footprint F = pixel_footprint(G, v, cs.x, cs.y, ix, iy);
+                const int j0 = (int)floorf(F.t0 - 0.5f) + 1;
+                cnt = max(min((int)ceilf(F.t3 + 0.5f) - j0, kMaxSpan), 0);
+                const float xa = xv * F.amp;
+                float Fp = trap_cdf(F, (float)j0 - 0.5f);
+                for (int i = 0; i < cnt; i++) {
+                    const float Fn = trap_cdf(F, (float)(j0 + i) + 0.5f);
+                    sw[lane][i] = (Fn - Fp) * xa;
+                    Fp = Fn;
+                }
+                cf = F.n + j0 - s0;
+            }
+        }
+        scf[lane] = cf;
+        sns[lane] = cnt;
+        __syncwarp();
+        // cell role: gather the staged weights of the pixels this lane's wedge crosses
+        const int lmax = __shfl_sync(kFull, ls, n - 1);
+        for (int l = 0; l <= lmax; l++) {
+            const int cc = col + l;
+            const int pre_c = s_pre[cc];
+            const int task_lo = max(pre_c, t0), task_hi = min(__shfl_sync(kFull, e, l), t0 + n);  // [lo, hi)
+            const int row0 = s_lo[cc] - pre_c;  // cross index of task t is row0 + t
+            int q_lo, q_hi;
+            wedge_range(M, cc, t1, t2, q_lo, q_hi);
+            q_lo = max(q_lo, row0 + task_lo);
+            q_hi = min(q_hi, row0 + task_hi - 1);
+            for (int q = q_lo; q <= q_hi; q++) {
+                const int slot = q - row0 - t0;
+                const int i = lane - scf[slot];
+                if ((unsigned)i < (unsigned)sns[slot]) acc += sw[slot][i];
+            }
+        }
+        __syncwarp();
+        t0 += n;
+    }
+    s_acc[warp][lane] = acc;
+    __syncthreads();
+    if (warp != 0 || s_mine >= G.ns) return;
+    float sum = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kBundleWarps; q++) sum += s_acc[q][lane];
+    const size_t yi = (size_t)v * G.ns + s_mine;
+    if (MODE == FP_PLAIN) out[(size_t)k * G.ns + s_mine] = sum;
+    else if (MODE == FP_RESID) out[(size_t)k * G.ns + s_mine] = __ldg(&w[yi]) * (sum - __ldg(&y[yi]));
+    else out[yi] = __ldg(&w[yi]) * sum;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kFpThreads) fp_ray_kernel(FanDev G, const float *__restrict__ x,
+                                                            const int *__restrict__ views, int nviews,
+                                                            float *__restrict__ out, const float *__restrict__ y,
+                                                            const float *__restrict__ w)
 {
     const int lane = threadIdx.x & 31;
     const long gwarp = ((long)blockIdx.x * kFpThreads + threadIdx.x) >> 5;
@@ -54,51 +251,12 @@ __global__ void __launch_bounds__(kFpThreads) fp_fan2d_kernel(FanDev G, const fl
         s = (int)(ray - (long)k * G.ns);
         v = __ldg(&views[k]);
         const float2 cs = __ldg(&G.view_cs[v]);
-        const float beta = __ldg(&G.view_beta[v]);
-        const float phi = beta + fmaf((float)s, G.dgamma, G.gamma0);
-        float sp, cp;
-        sincosf(phi, &sp, &cp);
-        const float Sx = -G.dso * cs.x, Sy = -G.dso * cs.y;
-        const float phl = phi - 0.5f * G.dgamma, phh = phi + 0.5f * G.dgamma;
-        if (fabsf(cp) >= fabsf(sp)) {
-            // shallow ray: march columns; the wedge's edges are y = Sy + (x - Sx) tan(phi -+ dgamma/2)
-            const float tl = tanf(phl), th = tanf(phh);
-            const int c0 = seg * G.nx / kFpSeg, c1 = (seg + 1) * G.nx / kFpSeg;
-            for (int ix = c0; ix < c1; ix++) {
-                const float xl = fmaf((float)ix, G.dx, G.x_edge0) - Sx, xr = xl + G.dx;
-                const float y1 = fmaf(xl, tl, Sy), y2 = fmaf(xr, tl, Sy);
-                const float y3 = fmaf(xl, th, Sy), y4 = fmaf(xr, th, Sy);
-                const float ylo = (fminf(fminf(y1, y2), fminf(y3, y4)) - G.y_edge0) * G.inv_dy - kRangePad;
-                const float yhi = (fmaxf(fmaxf(y1, y2), fmaxf(y3, y4)) - G.y_edge0) * G.inv_dy + kRangePad;
-                const int iy0 = max(0, (int)floorf(fmaxf(ylo, -1.0f)));
-                const int iy1 = min(G.ny - 1, (int)floorf(fminf(yhi, (float)G.ny)));
-                for (int iy = iy0; iy <= iy1; iy++) {
-                    const float xv = (MODE == FP_ONES_W) ? 1.0f : __ldg(&x[(size_t)iy * G.nx + ix]);
-                    if (xv == 0.0f) continue;
-                    const Footprint F = pixel_footprint(G, v, cs.x, cs.y, ix, iy);
-                    acc = fmaf(cell_weight(F, s), xv, acc);
-                }
-            }
-        } else {
-            // steep ray: march rows; x = Sx + (y - Sy) cot(phi -+ dgamma/2)
-            const float tl = cosf(phl) / sinf(phl), th = cosf(phh) / sinf(phh);
-            const int r0 = seg * G.ny / kFpSeg, r1 = (seg + 1) * G.ny / kFpSeg;
-            for (int iy = r0; iy < r1; iy++) {
-                const float yb = fmaf((float)iy, G.dy, G.y_edge0) - Sy, yt = yb + G.dy;
-                const float x1 = fmaf(yb, tl, Sx), x2 = fmaf(yt, tl, Sx);
-                const float x3 = fmaf(yb, th, Sx), x4 = fmaf(yt, th, Sx);
-                const float xlo = (fminf(fminf(x1, x2), fminf(x3, x4)) - G.x_edge0) * G.inv_dx - kRangePad;
-                const float xhi = (fmaxf(fmaxf(x1, x2), fmaxf(x3, x4)) - G.x_edge0) * G.inv_dx + kRangePad;
-                const int ix0 = max(0, (int)floorf(fmaxf(xlo, -1.0f)));
-                const int ix1 = min(G.nx - 1, (int)floorf(fminf(xhi, (float)G.nx)));
-                for (int ix = ix0; ix <= ix1; ix++) {
-                    const float xv = (MODE == FP_ONES_W) ? 1.0f : __ldg(&x[(size_t)iy * G.nx + ix]);
-                    if (xv == 0.0f) continue;
-                    const Footprint F = pixel_footprint(G, v, cs.x, cs.y, ix, iy);
-                    acc = fmaf(cell_weight(F, s), xv, acc);
-                }
-            }
-        }
+        ray_visit(G, v, s, seg, kFpSeg, [&](int ix, int iy) {
+            const float xv = (MODE == FP_ONES_W) ? 1.0f : __ldg(&x[(size_t)iy * G.nx + ix]);
+            if (xv == 0.0f) return;
+            const Footprint F = pixel_footprint(G, v, cs.x, cs.y, ix, iy);
+            acc = fmaf(cell_weight(F, s), xv, acc);
+        });
     }
 #pragma unroll
     for (int o = kFpSeg / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -115,8 +273,56 @@ __global__ void __launch_bounds__(kFpThreads) fp_fan2d_kernel(FanDev G, const fl
     }
 }
 
+// Resident-matrix forward projection: one warp per ray streams the ray's
+// (pixel, a_ij) entries (4 loads in flight per lane), gathers x from L1/L2 and
+// reduces by shuffles.  The 8 warps of a CTA take 8 adjacent cells of one view,
+// whose wedges cover nearly the same pixels.
 template <int MODE>
-__global__ void __launch_bounds__(256) bp_fan2d_kernel(FanDev G, const float *__restrict__ sino,
+__global__ void __launch_bounds__(256) fp_csr_kernel(FanDev G, const float *__restrict__ x,
+                                                     const int *__restrict__ views, int nviews,
+                                                     float *__restrict__ out, const float *__restrict__ y,
+                                                     const float *__restrict__ w)
+{
+    const int lane = threadIdx.x & 31;
+    const long ray = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (ray >= (long)nviews * G.ns) return;  // whole warp
+    const int k = (int)(ray / G.ns);
+    const int s = (int)(ray - (long)k * G.ns);
+    const int v = __ldg(&views[k]);
+    const size_t r = (size_t)v * G.ns + s;
+    const long long b = __ldg(&G.row_ptr[r]), e = __ldg(&G.row_ptr[r + 1]);
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    long long i = b + lane;
+    for (; i + 96 < e; i += 128) {
+        const int2 q0 = __ldcs(&G.row_ent[i]);
+        const int2 q1 = __ldcs(&G.row_ent[i + 32]);
+        const int2 q2 = __ldcs(&G.row_ent[i + 64]);
+        const int2 q3 = __ldcs(&G.row_ent[i + 96]);
+        if (MODE == FP_ONES_W) {
+            a0 += __int_as_float(q0.y); a1 += __int_as_float(q1.y);
+            a2 += __int_as_float(q2.y); a3 += __int_as_float(q3.y);
+        } else {
+            a0 = fmaf(__int_as_float(q0.y), __ldg(&x[q0.x]), a0);
+            a1 = fmaf(__int_as_float(q1.y), __ldg(&x[q1.x]), a1);
+            a2 = fmaf(__int_as_float(q2.y), __ldg(&x[q2.x]), a2);
+            a3 = fmaf(__int_as_float(q3.y), __ldg(&x[q3.x]), a3);
+        }
+    }
+    for (; i < e; i += 32) {
+        const int2 q = __ldcs(&G.row_ent[i]);
+        a0 = (MODE == FP_ONES_W) ? a0 + __int_as_float(q.y) : fmaf(__int_as_float(q.y), __ldg(&x[q.x]), a0);
+    }
+    float acc = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane != 0) return;
+    if (MODE == FP_PLAIN) out[(size_t)k * G.ns + s] = acc;
+    else if (MODE == FP_RESID) out[(size_t)k * G.ns + s] = __ldg(&w[r]) * (acc - __ldg(&y[r]));
+    else out[r] = __ldg(&w[r]) * acc;
+}
+
+template <int MODE, bool STORED>
+__global__ void __launch_bounds__(256, 8) bp_fan2d_kernel(FanDev G, const float *__restrict__ sino,
                                                        const int *__restrict__ views, int nviews,
                                                        float *__restrict__ xo, float scale, int accumulate,
                                                        SolveDev S)
@@ -132,9 +338,14 @@ __global__ void __launch_bounds__(256) bp_fan2d_kernel(FanDev G, const float *__
     float acc = 0.0f;
     for (int k = 0; k < nviews; k++) {
         const int v = __ldg(&views[k]);
-        const float2 cs = __ldg(&G.view_cs[v]);
-        const float4 A = __ldg(&G.anchor[(size_t)v * ntiles + tile]);
-        const Footprint F = sf_footprint(G, cs.x, cs.y, A, ox, oy);
+        Footprint F;
+        if (STORED) {
+            F = stored_footprint(G, v, tile, threadIdx.x);
+        } else {
+            const float2 cs = __ldg(&G.view_cs[v]);
+            const float4 A = __ldg(&G.anchor[(size_t)v * ntiles + tile]);
+            F = sf_footprint(G, cs.x, cs.y, A, ox, oy);
+        }
         const int slo = max(F.n + (int)floorf(F.t0 - 0.5f) + 1, 0);
         const int shi = min(F.n + (int)ceilf(F.t3 + 0.5f) - 1, G.ns - 1);
         const float *row = sino + (size_t)k * G.ns;
@@ -192,14 +403,32 @@ __global__ void __launch_bounds__(256) bp_fan2d_kernel(FanDev G, const float *__
 cudaError_t launch_fp(const FanDev &G, int mode, const float *x, const int *views, int nviews, float *out,
                       const float *y, const float *w, cudaStream_t st)
 {
+    if (nviews <= 0) return cudaSuccess;
+    if (G.row_ptr) {
+        const unsigned blocks = (unsigned)(((long)nviews * G.ns + 7) / 8);
+        switch (mode) {
+        case FP_PLAIN: fp_csr_kernel<FP_PLAIN><<<blocks, 256, 0, st>>>(G, x, views, nviews, out, y, w); break;
+        case FP_RESID: fp_csr_kernel<FP_RESID><<<blocks, 256, 0, st>>>(G, x, views, nviews, out, y, w); break;
+        default: fp_csr_kernel<FP_ONES_W><<<blocks, 256, 0, st>>>(G, x, views, nviews, out, y, w); break;
+        }
+        return cudaGetLastError();
+    }
+    if (G.max_span <= kMaxSpan && G.nx <= kMaxMarch && G.ny <= kMaxMarch) {
+        const unsigned blocks = (unsigned)nviews * (unsigned)((G.ns + 31) / 32);
+        switch (mode) {
+        case FP_PLAIN: fp_bundle_kernel<FP_PLAIN><<<blocks, kBundleWarps * 32, 0, st>>>(G, x, views, nviews, out, y, w); break;
+        case FP_RESID: fp_bundle_kernel<FP_RESID><<<blocks, kBundleWarps * 32, 0, st>>>(G, x, views, nviews, out, y, w); break;
+        default: fp_bundle_kernel<FP_ONES_W><<<blocks, kBundleWarps * 32, 0, st>>>(G, x, views, nviews, out, y, w); break;
+        }
+        return cudaGetLastError();
+    }
     const long nrays = (long)nviews * G.ns;
     const long rays_per_block = kFpThreads / kFpSeg;
     const unsigned blocks = (unsigned)((nrays + rays_per_block - 1) / rays_per_block);
-    if (blocks == 0) return cudaSuccess;
     switch (mode) {
-    case FP_PLAIN: fp_fan2d_kernel<FP_PLAIN><<<blocks, kFpThreads, 0, st>>>(G, x, views, nviews, out, y, w); break;
-    case FP_RESID: fp_fan2d_kernel<FP_RESID><<<blocks, kFpThreads, 0, st>>>(G, x, views, nviews, out, y, w); break;
-    default: fp_fan2d_kernel<FP_ONES_W><<<blocks, kFpThreads, 0, st>>>(G, x, views, nviews, out, y, w); break;
+    case FP_PLAIN: fp_ray_kernel<FP_PLAIN><<<blocks, kFpThreads, 0, st>>>(G, x, views, nviews, out, y, w); break;
+    case FP_RESID: fp_ray_kernel<FP_RESID><<<blocks, kFpThreads, 0, st>>>(G, x, views, nviews, out, y, w); break;
+    default: fp_ray_kernel<FP_ONES_W><<<blocks, kFpThreads, 0, st>>>(G, x, views, nviews, out, y, w); break;
     }
     return cudaGetLastError();
 }
@@ -210,10 +439,18 @@ cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *v
     dim3 grid(G.ntx, G.nty);
     SolveDev s0{};
     const SolveDev &SS = S ? *S : s0;
+    if (G.foot_t) {
+        switch (mode) {
+        case BP_PLAIN: bp_fan2d_kernel<BP_PLAIN, true><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+        case BP_SOLVE_INIT: bp_fan2d_kernel<BP_SOLVE_INIT, true><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+        default: bp_fan2d_kernel<BP_SOLVE_UPDATE, true><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+        }
+        return cudaGetLastError();
+    }
     switch (mode) {
-    case BP_PLAIN: bp_fan2d_kernel<BP_PLAIN><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
-    case BP_SOLVE_INIT: bp_fan2d_kernel<BP_SOLVE_INIT><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
-    default: bp_fan2d_kernel<BP_SOLVE_UPDATE><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+    case BP_PLAIN: bp_fan2d_kernel<BP_PLAIN, false><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+    case BP_SOLVE_INIT: bp_fan2d_kernel<BP_SOLVE_INIT, false><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+    default: bp_fan2d_kernel<BP_SOLVE_UPDATE, false><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
     }
     return cudaGetLastError();
 }

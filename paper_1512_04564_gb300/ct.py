@@ -69,6 +69,7 @@ def _load():
         "ct_forward": [vp, vp, vp, ip, cint, vp],
         "ct_back": [vp, vp, vp, ip, cint, cfl, cint, vp],
         "ct_sqs_diag": [vp, vp, vp, vp],
+        "ct_geom_precompute": [vp, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong), vp],
         "ct_reg_gradient": [vp, vp, cfl, cfl, cint, vp, vp, vp],
         "ct_relaxed_oslalm_solve": [vp, vp, vp, ctypes.POINTER(ct_solve_params), vp,
                                     ctypes.POINTER(ct_solve_report), vp],
@@ -86,7 +87,7 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_forward", "ct_back", "ct_sqs_diag", "ct_reg_gradient",
+EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_geom_precompute", "ct_forward", "ct_back", "ct_sqs_diag", "ct_reg_gradient",
             "ct_relaxed_oslalm_solve", "ct_last_error", "ct_version")
 
 
@@ -160,6 +161,13 @@ class Geometry:
             self.close()
         except Exception:
             pass
+
+
+def ct_geom_precompute(geom: Geometry, max_bytes: int = 0, stream=None) -> int:
+    """Build the resident system matrix; returns its size in bytes."""
+    b = ctypes.c_ulonglong(0)
+    _check(_lib.ct_geom_precompute(geom.handle, ctypes.c_ulonglong(int(max_bytes)), ctypes.byref(b), _stream(stream)))
+    return int(b.value)
 
 
 def ct_forward(geom: Geometry, x: torch.Tensor, y: torch.Tensor, views=None, stream=None) -> torch.Tensor:
