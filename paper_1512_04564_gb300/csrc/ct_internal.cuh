@@ -117,7 +117,8 @@ __device__ __forceinline__ float atan_tiny(float z)
 struct Footprint {
     float t0, t1, t2, t3;
     float amp;
-    float i2w1, i2w3;  // 1/(2 (t1 - t0)) and 1/(2 (t3 - t2)), 0 for a vertical edge
+    float w1, w2, w3;  // t1 - t0, t2 - t1, t3 - t2
+    float i2w1, i2w3;  // 1/(2 w1) and 1/(2 w3), 0 for a vertical edge
     int n;
 };
 
@@ -162,9 +163,11 @@ __device__ __forceinline__ Footprint sf_footprint(const FanDev &G, float cb, flo
     const float m0 = fmaxf(a0, b0), m1 = fminf(a1, b1);
     F.t1 = fminf(m0, m1);
     F.t2 = fmaxf(m0, m1);
-    const float w1 = F.t1 - F.t0, w3 = F.t3 - F.t2;
-    F.i2w1 = w1 > 0.0f ? __fdividef(0.5f, w1) : 0.0f;
-    F.i2w3 = w3 > 0.0f ? __fdividef(0.5f, w3) : 0.0f;
+    F.w1 = F.t1 - F.t0;
+    F.w2 = F.t2 - F.t1;
+    F.w3 = F.t3 - F.t2;
+    F.i2w1 = F.w1 > 0.0f ? __fdividef(0.5f, F.w1) : 0.0f;
+    F.i2w3 = F.w3 > 0.0f ? __fdividef(0.5f, F.w3) : 0.0f;
     // amplitude: chord through the pixel along the centre ray = |c| / max(|c_x|/dx, |c_y|/dy)
     const float imx = fabsf(fmaf(cpar, cb, -cperp * sb)) * G.inv_dx;
     const float imy = fabsf(fmaf(cpar, sb, cperp * cb)) * G.inv_dy;
@@ -173,15 +176,43 @@ __device__ __forceinline__ Footprint sf_footprint(const FanDev &G, float cb, flo
     return F;
 }
 
-// Integral of the unit trapezoid over (-inf, u].
+// Integral of the unit trapezoid over (-inf, u], branch-free: rising ramp
+// a^2/(2 w1) with a = clamp(u - t0, 0, w1), flat part clamp(u - t1, 0, w2),
+// falling ramp w3/2 - b^2/(2 w3) with b = clamp(t3 - u, 0, w3).  For u <= t2
+// the falling term is the rounding residue of w3/2 - w3^2/(2 w3), the same
+// constant for every such u, so it cancels in cell differences.
 __device__ __forceinline__ float trap_cdf(const Footprint &F, float u)
 {
-    const float a = fminf(fmaxf(u - F.t0, 0.0f), F.t1 - F.t0);     // rising edge
-    const float b = fminf(fmaxf(F.t3 - u, 0.0f), F.t3 - F.t2);     // falling edge still ahead
-    const float flat = fminf(fmaxf(u - F.t1, 0.0f), F.t2 - F.t1);
-    const float w3 = F.t3 - F.t2;
-    const float fall = (u > F.t2) ? fmaf(-b * b, F.i2w3, 0.5f * w3) : 0.0f;
-    return fmaf(a * a, F.i2w1, flat) + fall;
+    const float a = fminf(fmaxf(u - F.t0, 0.0f), F.w1);
+    const float b = fminf(fmaxf(F.t3 - u, 0.0f), F.w3);
+    const float flat = fminf(fmaxf(u - F.t1, 0.0f), F.w2);
+    return fmaf(a * a, F.i2w1, flat) + fmaf(-b * b, F.i2w3, 0.5f * F.w3);
+}
+
+// Area of the unit trapezoid.
+__device__ __forceinline__ float trap_area(const Footprint &F)
+{
+    return fmaf(0.5f, F.w1 + F.w3, F.w2);
+}
+
+// sum_s a_s r_s over the cells of one footprint (row = detector row of one view),
+// by summation by parts over the cell edges: the trapezoid's integral is 0 at the
+// first cell's lower edge and its area at the last cell's upper edge, so only the
+// interior edges need the CDF.  Cells outside [0, ns) read as 0.
+__device__ __forceinline__ float footprint_dot(const Footprint &F, const float *__restrict__ row, int ns)
+{
+    const int j0 = (int)floorf(F.t0 - 0.5f) + 1;  // first cell, relative to n
+    const int jl = (int)ceilf(F.t3 + 0.5f) - 1;   // last cell
+    int s = F.n + j0;
+    float rp = ((unsigned)s < (unsigned)ns) ? __ldg(&row[s]) : 0.0f;
+    float acc = 0.0f;
+    for (int j = j0; j < jl; j++) {
+        s++;
+        const float rn = ((unsigned)s < (unsigned)ns) ? __ldg(&row[s]) : 0.0f;
+        acc = fmaf(trap_cdf(F, (float)j + 0.5f), rp - rn, acc);
+        rp = rn;
+    }
+    return F.amp * fmaf(trap_area(F), rp, acc);
 }
 
 // Footprint of pixel (ix, iy) in view v (loads the tile anchor).
@@ -248,18 +279,17 @@ __device__ __forceinline__ void ray_visit(const FanDev &G, int v, int s, int seg
     }
 }
 
-// Stored footprint of the pixel at position `local` (0..255, row-major in its
-// 16x16 tile) of tile `tile` in view v; same values sf_footprint returns.
-__device__ __forceinline__ Footprint stored_footprint(const FanDev &G, int v, int tile, int local)
+// Footprint rebuilt from its stored form (vertices; amplitude and base cell):
+// the same values sf_footprint returns.
+__device__ __forceinline__ Footprint footprint_from(float4 t, float2 an)
 {
-    const size_t i = ((size_t)v * (G.ntx * G.nty) + tile) * (kTile * kTile) + local;
-    const float4 t = __ldcs(&G.foot_t[i]);
-    const float2 an = __ldcs(&G.foot_an[i]);
     Footprint F;
     F.t0 = t.x; F.t1 = t.y; F.t2 = t.z; F.t3 = t.w;
-    const float w1 = F.t1 - F.t0, w3 = F.t3 - F.t2;
-    F.i2w1 = w1 > 0.0f ? __fdividef(0.5f, w1) : 0.0f;
-    F.i2w3 = w3 > 0.0f ? __fdividef(0.5f, w3) : 0.0f;
+    F.w1 = F.t1 - F.t0;
+    F.w2 = F.t2 - F.t1;
+    F.w3 = F.t3 - F.t2;
+    F.i2w1 = F.w1 > 0.0f ? __fdividef(0.5f, F.w1) : 0.0f;
+    F.i2w3 = F.w3 > 0.0f ? __fdividef(0.5f, F.w3) : 0.0f;
     F.amp = an.x;
     F.n = __float_as_int(an.y);
     return F;

@@ -40,6 +40,7 @@ constexpr int kBundleWarps = 8;     // warps per bundle CTA
 constexpr int kMaxSpan = 12;        // cells per staged footprint (bundle kernel)
 constexpr int kMaxMarch = 2048;     // longest march axis the bundle kernel stages
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBpThreads = 128;     // back-projector CTA: one 16x16 tile, two pixels per thread
 
 // Marching frame of a bundle: "march" is the axis the wedge is walked along
 // (x for shallow bundles, y for steep ones), "cross" the other axis.
@@ -321,68 +322,88 @@ __global__ void __launch_bounds__(256) fp_csr_kernel(FanDev G, const float *__re
     else out[r] = __ldg(&w[r]) * acc;
 }
 
-template <int MODE, bool STORED>
-__global__ void __launch_bounds__(256, 8) bp_fan2d_kernel(FanDev G, const float *__restrict__ sino,
-                                                       const int *__restrict__ views, int nviews,
-                                                       float *__restrict__ xo, float scale, int accumulate,
-                                                       SolveDev S)
+template <int MODE>
+__device__ __forceinline__ void bp_epilogue(const FanDev &G, const SolveDev &S, float *__restrict__ xo, int ix,
+                                            int iy, float acc, float rho, float scale, int accumulate)
 {
-    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
-    const int ix = blockIdx.x * kTile + lx, iy = blockIdx.y * kTile + ly;
-    const int tile = blockIdx.y * G.ntx + blockIdx.x;
-    const int ntiles = G.ntx * G.nty;
-    const float ox = ((float)lx - kTileHalf) * G.dx;
-    const float oy = ((float)ly - kTileHalf) * G.dy;
-    float rho = 1.0f;
-    if (MODE == BP_SOLVE_UPDATE) rho = __ldcg(&S.rho_tab[__ldcg(&S.counter[0])]);
-    float acc = 0.0f;
-    for (int k = 0; k < nviews; k++) {
-        const int v = __ldg(&views[k]);
-        Footprint F;
-        if (STORED) {
-            F = stored_footprint(G, v, tile, threadIdx.x);
-        } else {
-            const float2 cs = __ldg(&G.view_cs[v]);
-            const float4 A = __ldg(&G.anchor[(size_t)v * ntiles + tile]);
-            F = sf_footprint(G, cs.x, cs.y, A, ox, oy);
-        }
-        const int slo = max(F.n + (int)floorf(F.t0 - 0.5f) + 1, 0);
-        const int shi = min(F.n + (int)ceilf(F.t3 + 0.5f) - 1, G.ns - 1);
-        const float *row = sino + (size_t)k * G.ns;
-        float Fp = trap_cdf(F, (float)(slo - F.n) - 0.5f);
-        float vacc = 0.0f;
-        for (int s = slo; s <= shi; s++) {
-            const float Fn = trap_cdf(F, (float)(s - F.n) + 0.5f);
-            vacc = fmaf(Fn - Fp, __ldg(&row[s]), vacc);
-            Fp = Fn;
-        }
-        acc = fmaf(F.amp, vacc, acc);
-    }
-    const bool inside = ix < G.nx && iy < G.ny;
+    if (ix >= G.nx || iy >= G.ny) return;
     const size_t j = (size_t)iy * G.nx + ix;
     if (MODE == BP_PLAIN) {
-        if (inside) xo[j] = accumulate ? fmaf(scale, acc, xo[j]) : scale * acc;
+        xo[j] = accumulate ? fmaf(scale, acc, xo[j]) : scale * acc;
         return;
     }
-    if (inside) {
-        const float zeta = S.M_scale * acc;  // M grad L_m
-        if (MODE == BP_SOLVE_INIT) {
-            // zeta = g = M grad L_M(x); h = D_L x - zeta (Algorithm 2 keeps zeta in h)
-            S.g[j] = zeta;
-            S.h[j] = (S.algorithm == CT_ALG_PROPOSED) ? fmaf(S.d_l[j], S.x[j], -zeta) : zeta;
-        } else {
-            const float g = S.g[j];
-            const float xp = S.x_new[j];
-            const float a = S.alpha;
-            const float ir = 1.0f / (rho + 1.0f);
-            S.g[j] = fmaf(rho * ir, fmaf(a, zeta, (1.0f - a) * g), g * ir);
-            if (S.algorithm == CT_ALG_PROPOSED)
-                S.h[j] = fmaf(a, fmaf(S.d_l[j], xp, -zeta), (1.0f - a) * S.h[j]);
-            else
-                S.h[j] = zeta;
-            S.x[j] = xp;
+    const float zeta = S.M_scale * acc;  // M grad L_m
+    if (MODE == BP_SOLVE_INIT) {
+        // zeta = g = M grad L_M(x); h = D_L x - zeta (Algorithm 2 keeps zeta in h)
+        S.g[j] = zeta;
+        S.h[j] = (S.algorithm == CT_ALG_PROPOSED) ? fmaf(S.d_l[j], S.x[j], -zeta) : zeta;
+    } else {
+        const float g = S.g[j];
+        const float xp = S.x_new[j];
+        const float a = S.alpha;
+        const float ir = 1.0f / (rho + 1.0f);
+        S.g[j] = fmaf(rho * ir, fmaf(a, zeta, (1.0f - a) * g), g * ir);
+        if (S.algorithm == CT_ALG_PROPOSED)
+            S.h[j] = fmaf(a, fmaf(S.d_l[j], xp, -zeta), (1.0f - a) * S.h[j]);
+        else
+            S.h[j] = zeta;
+        S.x[j] = xp;
+    }
+}
+
+// One CTA per 16x16 tile, 128 threads, two pixels per thread (rows ly and
+// ly + 8 of the tile).  With the resident matrix, the next view's footprints
+// are loaded while the current view's are used.
+template <int MODE, bool STORED>
+__global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const float *__restrict__ sino,
+                                                              const int *__restrict__ views, int nviews,
+                                                              float *__restrict__ xo, float scale, int accumulate,
+                                                              SolveDev S)
+{
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    const int ix = blockIdx.x * kTile + lx, iy0 = blockIdx.y * kTile + ly, iy1 = iy0 + kTile / 2;
+    const int tile = blockIdx.y * G.ntx + blockIdx.x;
+    const int ntiles = G.ntx * G.nty;
+    float rho = 1.0f;
+    if (MODE == BP_SOLVE_UPDATE) rho = __ldcg(&S.rho_tab[__ldcg(&S.counter[0])]);
+    float acc0 = 0.0f, acc1 = 0.0f;
+    if (STORED) {
+        const size_t vstride = (size_t)ntiles * (kTile * kTile);
+        const size_t base = (size_t)tile * (kTile * kTile) + threadIdx.x;
+        float4 tn0 = make_float4(0.f, 0.f, 0.f, 0.f), tn1 = tn0;
+        float2 an0 = make_float2(0.f, 0.f), an1 = an0;
+        if (nviews > 0) {
+            const size_t i = (size_t)__ldg(&views[0]) * vstride + base;
+            tn0 = __ldcs(&G.foot_t[i]); an0 = __ldcs(&G.foot_an[i]);
+            tn1 = __ldcs(&G.foot_t[i + kBpThreads]); an1 = __ldcs(&G.foot_an[i + kBpThreads]);
+        }
+        for (int k = 0; k < nviews; k++) {
+            const Footprint F0 = footprint_from(tn0, an0), F1 = footprint_from(tn1, an1);
+            if (k + 1 < nviews) {
+                const size_t i = (size_t)__ldg(&views[k + 1]) * vstride + base;
+                tn0 = __ldcs(&G.foot_t[i]); an0 = __ldcs(&G.foot_an[i]);
+                tn1 = __ldcs(&G.foot_t[i + kBpThreads]); an1 = __ldcs(&G.foot_an[i + kBpThreads]);
+            }
+            const float *row = sino + (size_t)k * G.ns;
+            acc0 += footprint_dot(F0, row, G.ns);
+            acc1 += footprint_dot(F1, row, G.ns);
+        }
+    } else {
+        const float ox = ((float)lx - kTileHalf) * G.dx;
+        const float oy0 = ((float)ly - kTileHalf) * G.dy, oy1 = ((float)(ly + kTile / 2) - kTileHalf) * G.dy;
+        for (int k = 0; k < nviews; k++) {
+            const int v = __ldg(&views[k]);
+            const float2 cs = __ldg(&G.view_cs[v]);
+            const float4 A = __ldg(&G.anchor[(size_t)v * ntiles + tile]);
+            const Footprint F0 = sf_footprint(G, cs.x, cs.y, A, ox, oy0);
+            const Footprint F1 = sf_footprint(G, cs.x, cs.y, A, ox, oy1);
+            const float *row = sino + (size_t)k * G.ns;
+            acc0 += footprint_dot(F0, row, G.ns);
+            acc1 += footprint_dot(F1, row, G.ns);
         }
     }
+    bp_epilogue<MODE>(G, S, xo, ix, iy0, acc0, rho, scale, accumulate);
+    bp_epilogue<MODE>(G, S, xo, ix, iy1, acc1, rho, scale, accumulate);
     if (MODE == BP_SOLVE_UPDATE) {
         // the last block to finish advances the subiteration counter (rho for the next one)
         __syncthreads();
@@ -441,16 +462,16 @@ cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *v
     const SolveDev &SS = S ? *S : s0;
     if (G.foot_t) {
         switch (mode) {
-        case BP_PLAIN: bp_fan2d_kernel<BP_PLAIN, true><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
-        case BP_SOLVE_INIT: bp_fan2d_kernel<BP_SOLVE_INIT, true><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
-        default: bp_fan2d_kernel<BP_SOLVE_UPDATE, true><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+        case BP_PLAIN: bp_fan2d_kernel<BP_PLAIN, true><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+        case BP_SOLVE_INIT: bp_fan2d_kernel<BP_SOLVE_INIT, true><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+        default: bp_fan2d_kernel<BP_SOLVE_UPDATE, true><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
         }
         return cudaGetLastError();
     }
     switch (mode) {
-    case BP_PLAIN: bp_fan2d_kernel<BP_PLAIN, false><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
-    case BP_SOLVE_INIT: bp_fan2d_kernel<BP_SOLVE_INIT, false><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
-    default: bp_fan2d_kernel<BP_SOLVE_UPDATE, false><<<grid, 256, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+    case BP_PLAIN: bp_fan2d_kernel<BP_PLAIN, false><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+    case BP_SOLVE_INIT: bp_fan2d_kernel<BP_SOLVE_INIT, false><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+    default: bp_fan2d_kernel<BP_SOLVE_UPDATE, false><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
     }
     return cudaGetLastError();
 }
