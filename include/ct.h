@@ -75,10 +75,10 @@ typedef struct {
 } ct_geom_desc;
 
 /* Create the device-side description of a scan geometry (Sec. III: A is the
- * forward projection matrix of the scan).  Checks that every pixel lies in
- * front of the source (image inside the circle of radius 0.95 dso) and
- * precomputes per-view and per-(view, 16x16 pixel tile) FP64-derived tables
- * in device memory.  On success *out owns that memory; release it with
+ * forward projection matrix of the scan).  Checks that every pixel lies at
+ * least 50 pixel widths in front of the source and that the fan half-angle is
+ * below 1.4 rad, and precomputes per-view and per-(view, 16x16 pixel tile)
+ * FP64-derived tables in device memory.  On success *out owns that memory; release it with
  * ct_geom_destroy.  Errors: CT_EINVAL (bad sizes), CT_ENOTSUP (kind),
  * CT_ENOMEM, CT_ECUDA. */
 ct_status ct_geom_create(const ct_geom_desc *desc, ct_geom **out);
