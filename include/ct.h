@@ -121,6 +121,20 @@ ct_status ct_back(const ct_geom *g, const float *y, float *x, const int *views, 
  * workspace.  Errors: CT_EINVAL, CT_ENOMEM, CT_ECUDA. */
 ct_status ct_sqs_diag(const ct_geom *g, const float *w, float *d_l, void *stream);
 
+/* Same result as ct_sqs_diag, without using or allocating any device memory
+ * beyond its arguments: for callers that cannot allocate once running (a
+ * process whose device memory is reserved up front by its own pool, or a
+ * latency-critical loop that must not enter cudaMalloc/cudaFree, which can
+ * block and synchronise the device).  The paper has no counterpart; it is an
+ * operational variant.  The intermediate sinogram w (A 1) lives in a 4 MiB
+ * device array inside the library (held by every GPU that loads it until the
+ * process exits), so na * ns must be <= 1,048,576 (CT_EINVAL otherwise).  The
+ * first call on a device looks up that array's address with the device
+ * current; make it before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU race.  The geometry's device must be
+ * current.  Errors: CT_EINVAL, CT_ECUDA. */
+ct_status ct_sqs_diag_noalloc(const ct_geom *g, const float *w, float *d_l, void *stream);
+
 enum { CT_POT_HYPERBOLA = 0, CT_POT_FAIR = 1, CT_POT_QUADRATIC = 2 };
 enum { CT_ALG_PROPOSED = 0, CT_ALG_SIMPLE = 1 };
 

@@ -69,6 +69,7 @@ def _load():
         "ct_forward": [vp, vp, vp, ip, cint, vp],
         "ct_back": [vp, vp, vp, ip, cint, cfl, cint, vp],
         "ct_sqs_diag": [vp, vp, vp, vp],
+        "ct_sqs_diag_noalloc": [vp, vp, vp, vp],
         "ct_geom_precompute": [vp, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong), vp],
         "ct_reg_gradient": [vp, vp, cfl, cfl, cint, vp, vp, vp],
         "ct_relaxed_oslalm_solve": [vp, vp, vp, ctypes.POINTER(ct_solve_params), vp,
@@ -87,8 +88,8 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_geom_precompute", "ct_forward", "ct_back", "ct_sqs_diag", "ct_reg_gradient",
-            "ct_relaxed_oslalm_solve", "ct_last_error", "ct_version")
+EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_geom_precompute", "ct_forward", "ct_back", "ct_sqs_diag",
+            "ct_sqs_diag_noalloc", "ct_reg_gradient", "ct_relaxed_oslalm_solve", "ct_last_error", "ct_version")
 
 
 class CTError(RuntimeError):
@@ -188,6 +189,13 @@ def ct_back(geom: Geometry, y: torch.Tensor, x: torch.Tensor, views=None, scale=
 def ct_sqs_diag(geom: Geometry, w: torch.Tensor, d_l: torch.Tensor, stream=None) -> torch.Tensor:
     _check(_lib.ct_sqs_diag(geom.handle, _ptr(w, "w", geom.na * geom.ns), _ptr(d_l, "d_l", geom.nx * geom.ny),
                             _stream(stream)))
+    return d_l
+
+
+def ct_sqs_diag_noalloc(geom: Geometry, w: torch.Tensor, d_l: torch.Tensor, stream=None) -> torch.Tensor:
+    """ct_sqs_diag without device allocation (scratch in a fixed 4 MiB library array; na*ns <= 2^20)."""
+    _check(_lib.ct_sqs_diag_noalloc(geom.handle, _ptr(w, "w", geom.na * geom.ns),
+                                    _ptr(d_l, "d_l", geom.nx * geom.ny), _stream(stream)))
     return d_l
 
 
