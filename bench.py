@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--tol-hu", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-matrix", action="store_true", help="footprints on the fly instead of the resident matrix")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="only time one subset forward and back projection (profiling mode)")
+    ap.add_argument("--views", type=int, default=None,
+                    help="override the number of views over 360 deg (profiling smaller cases)")
     return ap.parse_args()
 
 
@@ -122,6 +126,10 @@ class ClockSampler:
 
 def make_problem(args, rank: int):
     cfg = synth.config_by_name(args.workload, seed=rank)
+    if args.views is not None:
+        import dataclasses
+
+        cfg = dataclasses.replace(cfg, geom=cfg.geom.with_(na=args.views))
     alpha = args.alpha if args.alpha is not None else cfg.alpha
     # relaxed OS-LALM: half the subsets of the unrelaxed method (Sec. III-A)
     M = args.M if args.M is not None else (max(1, cfg.M // 2) if alpha > 1.0 else cfg.M)
@@ -243,6 +251,14 @@ def main():
     w = torch.from_numpy(data.w.astype(np.float32)).cuda()
     beta, delta, hu = cfg.beta_per_mm, cfg.delta, cfg.hu_per_unit
     common = dict(beta=beta, delta=delta, potential=cfg.potential)
+    if args.kernels_only:
+        xk = torch.from_numpy(synth.rasterize_ellipses(data.ellipses, g.nx, g.ny, g.dx, g.dy,
+                                                       oversample=1).astype(np.float32)).cuda()
+        roof = kernel_roofline(ct, G, g, M, y, w, xk, matrix_bytes)
+        if rank == 0:
+            print(json.dumps({"mode": "kernels-only", "workload": cfg.name, "views": g.na, "M": M,
+                              "matrix_bytes": matrix_bytes, "roofline": roof}), flush=True)
+        return 0
 
     # x*: M = 1 relaxed LALM from zero, then its KKT residual
     xstar = torch.zeros(g.ny, g.nx, device="cuda")
