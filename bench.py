@@ -43,8 +43,8 @@ import synth  # noqa: E402
 
 METRIC = "time to RMSD<=1 HU vs x* (s)"
 UNIT = "s"
-# outer iterations to RMSD <= 1 HU measured by the GPU arm (config.iters_to_tol), keyed by (workload, M, alpha)
-REFERENCE_ITERS_TO_TOL = {("fan2d_512", 20, 1.999): 14}
+# outer iterations to RMSD <= 1 HU measured by the GPU arm (config.iters_to_tol), keyed by (workload, M, alpha, x0)
+REFERENCE_ITERS_TO_TOL = {("fan2d_512", 20, 1.999, "fbp"): 6, ("fan2d_512", 20, 1.999, "zeros"): 14}
 
 
 def parse():
@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--tol-hu", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-matrix", action="store_true", help="footprints on the fly instead of the resident matrix")
+    ap.add_argument("--x0", default="fbp", choices=["fbp", "zeros"],
+                    help="initial image: Hann-windowed FBP of the data (timed inside the solve) or zeros")
     ap.add_argument("--kernels-only", action="store_true",
                     help="only time one subset forward and back projection (profiling mode)")
     ap.add_argument("--views", type=int, default=None,
@@ -138,7 +140,7 @@ def make_problem(args, rank: int):
     return cfg, alpha, M, n_iter, data
 
 
-def cpu_oracle_time_to_tol(cfg, data, alpha, M, iters_to_tol, budget_s=20.0):
+def cpu_oracle_time_to_tol(cfg, data, alpha, M, iters_to_tol, budget_s=20.0, x0="fbp"):
     """Time the FP64 oracle (as it stands) on a bounded sample and scale it to a time-to-tol.
 
     Sample: the oracle's D_L (full A'WA1) and as many subiterations of Algorithm 1 as fit in
@@ -151,6 +153,14 @@ def cpu_oracle_time_to_tol(cfg, data, alpha, M, iters_to_tol, budget_s=20.0):
     prob = osolver.PWLSProblem(FanProjector(g), data.y.astype(np.float32).astype(np.float64),
                                data.w.astype(np.float32).astype(np.float64), cfg.beta_per_mm, cfg.delta,
                                cfg.potential)
+    t_fbp = 0.0
+    xinit = np.zeros((g.ny, g.nx))
+    if x0 == "fbp":
+        from oracle.fbp import fbp_fan_arc
+
+        t0 = time.perf_counter()
+        xinit = fbp_fan_arc(g, data.y.astype(np.float32).astype(np.float64), "hann")
+        t_fbp = time.perf_counter() - t0
     t0 = time.perf_counter()
     DL = prob.D_L()
     t_dl = time.perf_counter() - t0
@@ -169,16 +179,16 @@ def cpu_oracle_time_to_tol(cfg, data, alpha, M, iters_to_tol, budget_s=20.0):
 
     try:
         last[0] = time.perf_counter()
-        osolver.relaxed_os_lalm(prob, np.zeros((g.ny, g.nx)), M, alpha, 1, D_L=DL, sub_callback=cb)
+        osolver.relaxed_os_lalm(prob, xinit, M, alpha, 1, D_L=DL, sub_callback=cb)
     except Stop:
         pass
     # the first interval also holds the initialisation (one subset gradient)
     t_sub = statistics.mean(subs[1:]) if len(subs) > 1 else subs[0]
     t_init = max(subs[0] - t_sub, 0.0)
-    value = t_dl + t_init + iters_to_tol * M * t_sub
+    value = t_fbp + t_dl + t_init + iters_to_tol * M * t_sub
     return {
         "value": value, "unit": UNIT, "cores": num_threads(), "kind": "oracle",
-        "sample": (f"FP64 oracle on the same workload: D_L ({t_dl:.2f} s) + init ({t_init:.2f} s) + "
+        "sample": (f"FP64 oracle on the same workload: FBP ({t_fbp:.2f} s) + D_L ({t_dl:.2f} s) + init ({t_init:.2f} s) + "
                    f"{len(subs)} of {M} subiterations ({t_sub:.3f} s each) timed, scaled to "
                    f"{iters_to_tol} outer iterations (the GPU's iteration count to the tolerance)"),
     }
@@ -192,11 +202,12 @@ def run_reference(args):
     # The oracle follows the GPU solver's iterates (parity <= 0.1 HU), so it needs the same number of
     # outer iterations to reach 1 HU: REFERENCE_ITERS_TO_TOL, measured by this script's GPU arm
     # (config.iters_to_tol) on the seed-0 workload.
-    iters = int(os.environ.get("CT_REFERENCE_ITERS", REFERENCE_ITERS_TO_TOL.get((cfg.name, M, alpha), n_iter)))
+    iters = int(os.environ.get("CT_REFERENCE_ITERS", REFERENCE_ITERS_TO_TOL.get((cfg.name, M, alpha, args.x0), n_iter)))
     per_step = []
     cb = None
     for _ in range(args.warmup + args.steps):
-        cb = cpu_oracle_time_to_tol(cfg, data, alpha, M, iters, budget_s=max(5.0, 60.0 / (args.warmup + args.steps)))
+        cb = cpu_oracle_time_to_tol(cfg, data, alpha, M, iters, budget_s=max(5.0, 60.0 / (args.warmup + args.steps)),
+                                    x0=args.x0)
         per_step.append(cb["value"])
     vals = per_step[args.warmup:]
     v = statistics.mean(vals)
@@ -205,7 +216,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": cfg.name, "alpha": alpha, "M": M, "n_iter": n_iter, "iters_assumed": iters},
+        "config": {"workload": cfg.name, "alpha": alpha, "M": M, "n_iter": n_iter, "x0": args.x0,
+                   "iters_assumed": iters},
         "cpu_baseline": cb,
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -267,10 +279,12 @@ def main():
     t_xstar = time.perf_counter() - t0
     kkt = kkt_rms_hu(ct, G, g, y, w, xstar, beta, delta, cfg.potential, hu)
 
+    fbp0 = args.x0 == "fbp"
+
     def solve_once(stop=0.0):
         x = torch.zeros(g.ny, g.nx, device="cuda")
         rep = ct.ct_relaxed_oslalm_solve(G, y, w, x, M=M, n_iter=n_iter, alpha=alpha, x_ref=xstar, hu_per_unit=hu,
-                                         stop_rmsd_hu=stop, **common)
+                                         stop_rmsd_hu=stop, init_fbp=fbp0, **common)
         return rep, x
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -317,7 +331,7 @@ def main():
         wd = w_h.to("cuda", non_blocking=True)
         x = torch.zeros(g.ny, g.nx, device="cuda")
         ct.ct_relaxed_oslalm_solve(G, yd, wd, x, M=M, n_iter=n_iter, alpha=alpha, x_ref=xstar, hu_per_unit=hu,
-                                   stop_rmsd_hu=args.tol_hu, **common)
+                                   stop_rmsd_hu=args.tol_hu, init_fbp=fbp0, **common)
         x_h.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
@@ -325,14 +339,14 @@ def main():
            "d2h_bytes_per_step": x_h.numel() * 4}
 
     roof = kernel_roofline(ct, G, g, M, y, w, xstar, matrix_bytes)
-    launches = 4 + n_iter * (3 * M + 1)
+    launches = 4 + (2 if fbp0 else 0) + n_iter * (3 * M + 1)
     # the workload's own subset count, for the record (untimed)
     m41 = {}
     if M != cfg.M:
         for a41 in (alpha, 1.0):
             x41 = torch.zeros(g.ny, g.nx, device="cuda")
             r41 = ct.ct_relaxed_oslalm_solve(G, y, w, x41, M=cfg.M, n_iter=n_iter, alpha=a41, x_ref=xstar,
-                                             hu_per_unit=hu, **common)
+                                             hu_per_unit=hu, init_fbp=fbp0, **common)
             tr = r41["rmsd_trace_hu"]
             hit = next((i + 1 for i, r in enumerate(tr) if r <= args.tol_hu), None)
             m41[f"alpha{a41:g}"] = {"iters_to_tol": hit, "min_rmsd_hu": round(min(tr), 3),
@@ -343,7 +357,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": cfg.name, "image": [g.ny, g.nx], "views": g.na, "bins": g.ns, "M": M,
                    "alpha": alpha, "n_iter": n_iter, "M_named": cfg.M, "beta_water_units": cfg.beta,
-                   "x0": "zeros", "xstar_iters": args.xstar_iters,
+                   "x0": args.x0, "xstar_iters": args.xstar_iters,
                    "system_matrix": {"resident": matrix_bytes > 0, "bytes": matrix_bytes, "build_s": round(t_matrix, 4)},
                    "M_named_runs": m41,
                    "xstar_kkt_rms_hu": kkt, "iters_to_tol": iters_to_tol, "l2": "flushed (256 MB write) between steps",
@@ -357,7 +371,7 @@ def main():
         "source_digest": _source_digest(),
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_oracle_time_to_tol(cfg, data, alpha, M, iters_to_tol or n_iter)
+        line["cpu_baseline"] = cpu_oracle_time_to_tol(cfg, data, alpha, M, iters_to_tol or n_iter, x0=args.x0)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -387,13 +401,18 @@ def kkt_rms_hu(ct, G, g, y, w, x, beta, delta, potential, hu):
 
 
 def _source_digest():
+    """Digest of the code of the profiled projector kernels: projectors.cu and the device-arithmetic
+    section of ct_internal.cuh (the footprint, CDF and traversal functions they inline)."""
     import hashlib
 
-    h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1512_04564_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, fn), "rb") as f:
-            h.update(fn.encode() + f.read())
+    h = hashlib.sha256()
+    with open(os.path.join(csrc, "projectors.cu"), "rb") as f:
+        h.update(f.read())
+    hdr = open(os.path.join(csrc, "ct_internal.cuh")).read()
+    a = hdr.index("// ---------------------------------------------------------------- device arithmetic")
+    b = hdr.index("// ---------------------------------------------------------------- launchers")
+    h.update(hdr[a:b].encode())
     return h.hexdigest()[:16]
 
 

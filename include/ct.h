@@ -135,6 +135,19 @@ ct_status ct_sqs_diag(const ct_geom *g, const float *w, float *d_l, void *stream
  * current.  Errors: CT_EINVAL, CT_ECUDA. */
 ct_status ct_sqs_diag_noalloc(const ct_geom *g, const float *w, float *d_l, void *stream);
 
+enum { CT_FBP_RAMP = 0, CT_FBP_HANN = 1 };
+
+/* Filtered back-projection of a full 360-degree equiangular fan-beam scan,
+ * the initial image of Algorithm 1 ("an initial (FBP) image", Sec. III-A;
+ * the paper does not specify it).  Textbook equiangular fan-beam FBP:
+ * D cos(gamma) pre-weighting, band-limited ramp filter in the fan angle
+ * (window CT_FBP_RAMP, or CT_FBP_HANN for its Hann-apodised version),
+ * distance-weighted back-projection with linear interpolation.  y: device
+ * [na][ns] line integrals; x: device [ny][nx] output (same units per mm).
+ * Uses the geometry's sinogram workspace.  Errors: CT_EINVAL, CT_ENOTSUP
+ * (orbit other than 360 degrees, or ns > 19,000), CT_ECUDA. */
+ct_status ct_fbp(const ct_geom *g, const float *y, float *x, int window, void *stream);
+
 enum { CT_POT_HYPERBOLA = 0, CT_POT_FAIR = 1, CT_POT_QUADRATIC = 2 };
 enum { CT_ALG_PROPOSED = 0, CT_ALG_SIMPLE = 1 };
 
@@ -162,6 +175,7 @@ typedef struct {
     float hu_per_unit;  /* HU per unit of x, for RMSD reporting */
     float fov_radius;   /* RMSD mask radius in mm; <= 0 selects the scan's full field of view */
     float stop_rmsd_hu; /* > 0: stop after the first iteration with RMSD <= this (needs x_ref) */
+    int init_fbp;       /* 1: overwrite x_inout with the Hann-windowed FBP of y first (timed with the solve) */
 } ct_solve_params;
 
 /* Report filled by ct_relaxed_oslalm_solve.  The two array pointers are
@@ -184,7 +198,8 @@ typedef struct {
  *   zeta = M grad L_m(x+); g+ = rho/(rho+1)(alpha zeta + (1-alpha) g) + g/(rho+1);
  *   h+ = alpha (D_L x+ - zeta) + (1-alpha) h; rho <- rho_{k}(alpha).
  * y, w: device [na][ns] sinogram and weights (w >= 0).  x_inout: device
- * [ny][nx], the initial image on entry and the result on return.  The solve
+ * [ny][nx], the initial image on entry (or the FBP of y when init_fbp = 1,
+ * which needs a 360-degree scan) and the result on return.  The solve
  * runs on `stream` as CUDA-graph replays of one outer iteration and
  * synchronises the stream before returning.  Errors: CT_EINVAL, CT_ENOMEM,
  * CT_ECUDA. */

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <string>
 
 #include "../../include/ct.h"
@@ -311,6 +312,8 @@ cudaError_t launch_reg_update(const FanDev &G, const SolveDev &S, float beta, fl
                               cudaStream_t st);
 
 cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t st, bool *too_big);
+cudaError_t launch_fbp(const ct_geom *g, const float *y, float *x, int window, cudaStream_t st);
+ct_status validate_fbp(const ct_geom *g, int window);
 
 ct_status validate_views(const ct_geom *g, const int *views, int nviews);
 ct_status stage_views(const ct_geom *g, const int *views, int nviews, const int **dev_views, cudaStream_t st);

@@ -150,6 +150,11 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
     if (!p->continuation && !(p->rho_fixed > 0.0f)) { set_error("rho_fixed must be > 0"); return CT_EINVAL; }
     if (p->stop_rmsd_hu > 0.0f && !p->x_ref) { set_error("stop_rmsd_hu needs x_ref"); return CT_EINVAL; }
     if ((long)p->n_iter * p->M > 200000000L) { set_error("n_iter * M too large"); return CT_EINVAL; }
+    if (p->init_fbp != 0 && p->init_fbp != 1) { set_error("init_fbp must be 0 or 1"); return CT_EINVAL; }
+    if (p->init_fbp) {
+        ct_status sf = validate_fbp(g, CT_FBP_HANN);
+        if (sf != CT_OK) return sf;
+    }
 
     const int M = p->M;
     // interleaved subsets, stored contiguously: perm = [S_0 | S_1 | ... | S_{M-1}]
@@ -241,6 +246,7 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
     } eguard{exec};
 
     CT_CUDA_TRY(cudaEventRecord(ev_start, ws), "event");
+    if (p->init_fbp) CT_CUDA_TRY(launch_fbp(g, y, x, CT_FBP_HANN, ws), "initial FBP image");
     // D_L = diag(A' W A 1) over all views
     CT_CUDA_TRY(launch_fp(G, FP_ONES_W, nullptr, g->d_views_all, na, g->d_sino_ws, nullptr, w, ws), "D_L forward");
     CT_CUDA_TRY(launch_bp(G, BP_PLAIN, g->d_sino_ws, g->d_views_all, na, W.d_l, 1.0f, 0, nullptr, ws), "D_L back");

@@ -19,6 +19,7 @@ CT_OK, CT_EINVAL, CT_ENOMEM, CT_ECUDA, CT_ETIMEOUT, CT_ENOTSUP = range(6)
 CT_FAN_ARC_2D = 1
 CT_POT_HYPERBOLA, CT_POT_FAIR, CT_POT_QUADRATIC = 0, 1, 2
 CT_ALG_PROPOSED, CT_ALG_SIMPLE = 0, 1
+CT_FBP_RAMP, CT_FBP_HANN = 0, 1
 POTENTIALS = {"hyperbola": CT_POT_HYPERBOLA, "fair": CT_POT_FAIR, "quadratic": CT_POT_QUADRATIC}
 ALGORITHMS = {"proposed": CT_ALG_PROPOSED, "simple": CT_ALG_SIMPLE}
 
@@ -45,7 +46,7 @@ class ct_solve_params(ctypes.Structure):
         ("potential", ctypes.c_int), ("algorithm", ctypes.c_int), ("nonneg", ctypes.c_int),
         ("continuation", ctypes.c_int), ("rho_fixed", ctypes.c_float),
         ("x_ref", ctypes.c_void_p), ("hu_per_unit", ctypes.c_float), ("fov_radius", ctypes.c_float),
-        ("stop_rmsd_hu", ctypes.c_float),
+        ("stop_rmsd_hu", ctypes.c_float), ("init_fbp", ctypes.c_int),
     ]
 
 
@@ -70,6 +71,7 @@ def _load():
         "ct_back": [vp, vp, vp, ip, cint, cfl, cint, vp],
         "ct_sqs_diag": [vp, vp, vp, vp],
         "ct_sqs_diag_noalloc": [vp, vp, vp, vp],
+        "ct_fbp": [vp, vp, vp, cint, vp],
         "ct_geom_precompute": [vp, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong), vp],
         "ct_reg_gradient": [vp, vp, cfl, cfl, cint, vp, vp, vp],
         "ct_relaxed_oslalm_solve": [vp, vp, vp, ctypes.POINTER(ct_solve_params), vp,
@@ -89,7 +91,7 @@ def _load():
 
 _lib = _load()
 EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_geom_precompute", "ct_forward", "ct_back", "ct_sqs_diag",
-            "ct_sqs_diag_noalloc", "ct_reg_gradient", "ct_relaxed_oslalm_solve", "ct_last_error", "ct_version")
+            "ct_sqs_diag_noalloc", "ct_fbp", "ct_reg_gradient", "ct_relaxed_oslalm_solve", "ct_last_error", "ct_version")
 
 
 class CTError(RuntimeError):
@@ -199,6 +201,14 @@ def ct_sqs_diag_noalloc(geom: Geometry, w: torch.Tensor, d_l: torch.Tensor, stre
     return d_l
 
 
+def ct_fbp(geom: Geometry, y: torch.Tensor, x: torch.Tensor, window: str = "hann", stream=None) -> torch.Tensor:
+    """Full-scan equiangular fan-beam FBP (initial image of Algorithm 1)."""
+    win = {"ramp": CT_FBP_RAMP, "hann": CT_FBP_HANN}[window] if isinstance(window, str) else int(window)
+    _check(_lib.ct_fbp(geom.handle, _ptr(y, "y", geom.na * geom.ns), _ptr(x, "x", geom.nx * geom.ny), win,
+                       _stream(stream)))
+    return x
+
+
 def ct_reg_gradient(geom: Geometry, x: torch.Tensor, beta: float, delta: float, potential: str | int,
                     grad: torch.Tensor, curv: torch.Tensor | None = None, stream=None):
     pot = POTENTIALS[potential] if isinstance(potential, str) else int(potential)
@@ -212,7 +222,7 @@ def ct_relaxed_oslalm_solve(geom: Geometry, y: torch.Tensor, w: torch.Tensor, x:
                             n_iter: int, alpha: float, beta: float, delta: float, potential="hyperbola",
                             algorithm="proposed", nonneg=True, continuation=True, rho_fixed=0.0,
                             x_ref: torch.Tensor | None = None, hu_per_unit=1.0, fov_radius=0.0,
-                            stop_rmsd_hu=0.0, stream=None) -> dict:
+                            stop_rmsd_hu=0.0, init_fbp=False, stream=None) -> dict:
     """Relaxed OS-LALM (Algorithm 1 / 2); x is updated in place.  Returns the report as a dict."""
     n = geom.nx * geom.ny
     p = ct_solve_params()
@@ -222,6 +232,7 @@ def ct_relaxed_oslalm_solve(geom: Geometry, y: torch.Tensor, w: torch.Tensor, x:
     p.nonneg, p.continuation, p.rho_fixed = int(bool(nonneg)), int(bool(continuation)), float(rho_fixed)
     p.x_ref = _ptr(x_ref, "x_ref", n)
     p.hu_per_unit, p.fov_radius, p.stop_rmsd_hu = hu_per_unit, fov_radius, stop_rmsd_hu
+    p.init_fbp = int(bool(init_fbp))
     r = ct_solve_report()
     trace = (ctypes.c_float * max(n_iter, 1))()
     its = (ctypes.c_double * max(n_iter, 1))()
