@@ -102,6 +102,17 @@ void ct_geom_destroy(ct_geom *g);
  * CT_ENOMEM, CT_ECUDA. */
 ct_status ct_geom_precompute(ct_geom *g, unsigned long long max_bytes, unsigned long long *bytes_out, void *stream);
 
+/* Projector autotuner (an implementation choice; the paper has no
+ * counterpart).  Times, on a subset of views_per_launch evenly spread views
+ * (<= 0: 24), every forward-projector decomposition available for g
+ * (1 = resident-matrix rows, 2 = 32-cell bundles, 3 = 8 lanes per ray) and
+ * every back-projector (1 = stored footprints, 2 = footprints on the fly),
+ * and keeps the fastest for all later calls on g.  Run it after
+ * ct_geom_precompute if the matrix is wanted among the candidates.
+ * fp_choice, bp_choice: optional host outputs.  Allocates two temporary
+ * buffers; synchronises the stream.  Errors: CT_EINVAL, CT_ENOMEM, CT_ECUDA. */
+ct_status ct_geom_autotune(ct_geom *g, int views_per_launch, int *fp_choice, int *bp_choice, void *stream);
+
 /* Forward projection y = A_V x (Sec. III, Eq. (ct_problem); SF footprints,
  * ray-driven).  x: device [ny][nx]; y: device [nviews][ns], row k is view
  * views[k].  views: host array of nviews indices in [0, na), or NULL for all
@@ -205,6 +216,26 @@ typedef struct {
  * CT_ECUDA. */
 ct_status ct_relaxed_oslalm_solve(const ct_geom *g, const float *y, const float *w, const ct_solve_params *p,
                                   float *x_inout, ct_solve_report *report, void *stream);
+
+/* Batched relaxed OS-LALM: nslices independent problems (Algorithm 1 or 2
+ * each, with its own geometry, sinogram, weights and parameters) solved in
+ * one persistent cooperative launch, after per-slice setup launches (D_L,
+ * initial gradient, optional FBP).  Slice i runs n_iter_i * M_i
+ * subiterations; all slices advance in lockstep super-steps, and each
+ * super-step's regularizer, forward-projection and back-projection work of
+ * every active slice is spread over all SMs.  geoms, y, w, x_inout: host
+ * arrays of nslices pointers (device data as in ct_relaxed_oslalm_solve;
+ * slices may share a geometry); params: host array of nslices parameter
+ * sets (stop_rmsd_hu is ignored: every slice runs n_iter iterations);
+ * reports: optional host array of nslices reports, whose per-iteration times
+ * come from the device clock at each slice's iteration ends.  Allocates one
+ * device arena for the batch per call.  1 <= nslices <= 1024.  Synchronises
+ * the stream.  Errors: CT_EINVAL, CT_ENOTSUP, CT_ENOMEM, CT_ECUDA,
+ * CT_ETIMEOUT (a bounded grid-barrier wait gave up; the results are then
+ * undefined). */
+ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms, const float *const *y, const float *const *w,
+                                          const ct_solve_params *params, float *const *x_inout, int nslices,
+                                          ct_solve_report *reports, void *stream);
 
 /* Message describing the last failure on this thread ("" if none). */
 const char *ct_last_error(void);

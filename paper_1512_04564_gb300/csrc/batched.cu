@@ -1,0 +1,564 @@
+// Batched relaxed OS-LALM: many 2-D slices of uneven size, view count and
+// subset count solved in ONE persistent cooperative launch (Algorithm 1 per
+// slice, Sec. III-A).
+//
+// All slices advance in lockstep super-steps t = 0, 1, ...: slice i runs its
+// subiteration t while t < n_iter * M_i.  Each super-step has three phases,
+// separated by a grid barrier, and the work units of every active slice are
+// spread over all CTAs:
+//   A. regularizer + x-update (256-pixel chunks); also, for slices that just
+//      finished an outer iteration, the RMSD to x_ref and a %globaltimer stamp;
+//   B. subset forward projection + weighted residual (units of 8 rays, one
+//      warp per ray: resident-matrix rows, or the footprints on the fly);
+//   C. subset back-projection + g/h update (16x16 tiles, one pixel per thread).
+// The grid barrier is a generation counter with a bounded spin: if a wait
+// gives up, the kernel records an error status and every CTA returns.
+// Setup (D_L, initial gradient, optional FBP) uses the single-slice kernels.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "ct_internal.cuh"
+
+namespace ct {
+namespace {
+
+constexpr int kMaxSlices = 1024;
+constexpr int kThreads = 256;
+constexpr long long kMaxSpins = 1ll << 24;  // x ~100 ns sleep: ~2 s per barrier at most
+
+struct BatchSlice {
+    FanDev G;
+    float *x, *x_new, *g, *h, *d_l, *resid;
+    const float *y, *w, *x_ref;
+    const int *perm;     // views in subset order
+    const int *sub_off;  // [M+1] offsets into perm
+    const float *rho;    // [T]
+    double *rmsd_acc;    // [n_iter][2]: sum of squares, count (FOV)
+    unsigned long long *stamp;  // [n_iter] %globaltimer at the end of each outer iteration
+    Pot P;
+    float alpha, beta, r2max;
+    int M, T, n_iter, nonneg, algorithm;
+};
+
+struct BatchCtl {
+    unsigned int count;
+    unsigned int gen;
+    int error;
+    int pad;
+    unsigned long long t_start;
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier with a bounded wait; returns false (for every thread of
+// the CTA) once any CTA has given up.
+__device__ bool grid_barrier(BatchCtl *ctl)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = &ctl->gen;
+        volatile int *verr = &ctl->error;
+        const unsigned int g0 = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&ctl->count, 1u) + 1u;
+        int ok = 1;
+        if (arrived == gridDim.x) {
+            atomicExch(&ctl->count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == g0) {
+                if (*verr) { ok = 0; break; }
+                if (++spins > kMaxSpins) {
+                    atomicExch(&ctl->error, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        s_ok = ok && (*verr == 0);
+    }
+    __syncthreads();
+    __threadfence();  // every thread: order its later loads after the barrier
+    return s_ok != 0;
+}
+
+// Exclusive prefix over slices of their work units in this phase (shared memory).
+template <class Units>
+__device__ int build_prefix(int *s_pre, int nsl, Units units)
+{
+    __shared__ int s_part[kThreads / 32];
+    // each thread sums a contiguous block of slices
+    const int per = (nsl + kThreads - 1) / kThreads;
+    const int a0 = threadIdx.x * per;
+    int run = 0;
+    for (int i = 0; i < per; i++) {
+        const int s = a0 + i;
+        if (s < nsl) {
+            const int u = units(s);
+            s_pre[s] = u;
+            run += u;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_part[warp] = incl;
+    __syncthreads();
+    int base = 0;
+    for (int q = 0; q < warp; q++) base += s_part[q];
+    int pos = base + incl - run;
+    for (int i = 0; i < per; i++) {
+        const int s = a0 + i;
+        if (s < nsl) {
+            const int u = s_pre[s];
+            s_pre[s] = pos;
+            pos += u;
+        }
+    }
+    if (threadIdx.x == kThreads - 1) s_pre[nsl] = pos;
+    __syncthreads();
+    return s_pre[nsl];
+}
+
+// slice owning unit u: largest s with s_pre[s] <= u
+__device__ __forceinline__ int find_slice(const int *s_pre, int nsl, int u)
+{
+    int lo = 0, hi = nsl - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_pre[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ void rmsd_units(const BatchSlice &B, int iter, int chunk)
+{
+    const int j = chunk * kThreads + threadIdx.x;
+    const int npix = B.G.nx * B.G.ny;
+    double s = 0.0, c = 0.0;
+    if (j < npix) {
+        const int ix = j % B.G.nx, iy = j / B.G.nx;
+        const float X = ((float)ix - B.G.cxo) * B.G.dx, Y = ((float)iy - B.G.cyo) * B.G.dy;
+        if (fmaf(X, X, Y * Y) <= B.r2max) {
+            const double d = (double)__ldcg(&B.x[j]) - (double)B.x_ref[j];
+            s = d * d;
+            c = 1.0;
+        }
+    }
+    // warp sums, then one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0 && c > 0.0) {
+        atomicAdd(&B.rmsd_acc[2 * iter], s);
+        atomicAdd(&B.rmsd_acc[2 * iter + 1], c);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) batched_kernel(const BatchSlice *__restrict__ SL, int nsl, int Tmax,
+                                                          BatchCtl *ctl)
+{
+    __shared__ int s_pre[kMaxSlices + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_start = global_ns();
+    for (int t = 0; t <= Tmax; t++) {
+        // ---- phase A: iteration-end bookkeeping (RMSD, stamps) and K1 (regularizer + x-update)
+        {
+            // slices whose outer iteration ended with subiteration t-1
+            auto ended = [&](int s) {
+                const BatchSlice &B = SL[s];
+                return t > 0 && t <= B.T && (t % B.M) == 0;
+            };
+            if (blockIdx.x == 0 && threadIdx.x < 32) {
+                for (int s = lane; s < nsl; s += 32)
+                    if (ended(s)) SL[s].stamp[t / SL[s].M - 1] = global_ns();
+            }
+            const int total = build_prefix(s_pre, nsl, [&](int s) {
+                const BatchSlice &B = SL[s];
+                const int chunks = (B.G.nx * B.G.ny + kThreads - 1) / kThreads;
+                const int rm = (ended(s) && B.x_ref) ? chunks : 0;
+                const int k1 = (t < B.T) ? chunks : 0;
+                return rm + k1;
+            });
+            for (int u = blockIdx.x; u < total; u += gridDim.x) {
+                const int s = find_slice(s_pre, nsl, u);
+                const BatchSlice &B = SL[s];
+                const int chunks = (B.G.nx * B.G.ny + kThreads - 1) / kThreads;
+                int local = u - s_pre[s];
+                const bool do_rmsd = ended(s) && B.x_ref;
+                if (do_rmsd && local < chunks) {
+                    rmsd_units(B, t / B.M - 1, local);
+                    continue;
+                }
+                if (do_rmsd) local -= chunks;
+                const int j = local * kThreads + threadIdx.x;
+                if (j >= B.G.nx * B.G.ny) continue;
+                const int ix = j % B.G.nx, iy = j / B.G.nx;
+                const float rho = B.rho[t];
+                float gr, cv;
+                reg_terms<true>(B.G, B.x, ix, iy, B.beta, B.P, gr, cv);
+                const float xj = __ldcg(&B.x[j]), dl = __ldcg(&B.d_l[j]), g = __ldcg(&B.g[j]), h = __ldcg(&B.h[j]);
+                const float sv = (B.algorithm == CT_ALG_PROPOSED) ? fmaf(rho, fmaf(dl, xj, -h), (1.0f - rho) * g)
+                                                                  : fmaf(rho, h, (1.0f - rho) * g);
+                const float den = fmaf(rho, dl, cv);
+                float xn = den > 0.0f ? xj - (sv + gr) / den : xj;
+                if (B.nonneg) xn = fmaxf(xn, 0.0f);
+                B.x_new[j] = xn;
+            }
+        }
+        if (t == Tmax) break;
+        if (!grid_barrier(ctl)) return;
+        // ---- phase B: subset forward projection with the weighted residual (one warp per ray)
+        {
+            const int total = build_prefix(s_pre, nsl, [&](int s) {
+                const BatchSlice &B = SL[s];
+                if (t >= B.T) return 0;
+                const int m = t % B.M;
+                const int rays = (B.sub_off[m + 1] - B.sub_off[m]) * B.G.ns;
+                return (rays + 7) / 8;
+            });
+            for (int u = blockIdx.x; u < total; u += gridDim.x) {
+                const int s = find_slice(s_pre, nsl, u);
+                const BatchSlice &B = SL[s];
+                const int m = t % B.M;
+                const int nv = B.sub_off[m + 1] - B.sub_off[m];
+                const int r = (u - s_pre[s]) * 8 + warp;
+                if (r >= nv * B.G.ns) continue;  // whole warp
+                const int k = r / B.G.ns, sc = r - k * B.G.ns;
+                const int v = B.perm[B.sub_off[m] + k];
+                const size_t ri = (size_t)v * B.G.ns + sc;
+                float acc = 0.0f;
+                if (B.G.row_ptr) {
+                    const long long b0 = B.G.row_ptr[ri], e0 = B.G.row_ptr[ri + 1];
+                    float a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+                    long long i = b0 + lane;
+                    for (; i + 96 < e0; i += 128) {  // four loads in flight per lane
+                        const int2 q0 = __ldcs(&B.G.row_ent[i]), q1 = __ldcs(&B.G.row_ent[i + 32]);
+                        const int2 q2 = __ldcs(&B.G.row_ent[i + 64]), q3 = __ldcs(&B.G.row_ent[i + 96]);
+                        acc = fmaf(__int_as_float(q0.y), __ldcg(&B.x_new[q0.x]), acc);
+                        a1 = fmaf(__int_as_float(q1.y), __ldcg(&B.x_new[q1.x]), a1);
+                        a2 = fmaf(__int_as_float(q2.y), __ldcg(&B.x_new[q2.x]), a2);
+                        a3 = fmaf(__int_as_float(q3.y), __ldcg(&B.x_new[q3.x]), a3);
+                    }
+                    for (; i < e0; i += 32) {
+                        const int2 q = __ldcs(&B.G.row_ent[i]);
+                        acc = fmaf(__int_as_float(q.y), __ldcg(&B.x_new[q.x]), acc);
+                    }
+                    acc = (acc + a1) + (a2 + a3);
+                } else {
+                    const float2 cs = __ldg(&B.G.view_cs[v]);
+                    ray_visit(B.G, v, sc, lane, 32, [&](int ix, int iy) {
+                        const float xv = __ldcg(&B.x_new[(size_t)iy * B.G.nx + ix]);
+                        if (xv == 0.0f) return;
+                        const Footprint F = pixel_footprint(B.G, v, cs.x, cs.y, ix, iy);
+                        acc = fmaf(cell_weight(F, sc), xv, acc);
+                    });
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) B.resid[(size_t)k * B.G.ns + sc] = __ldg(&B.w[ri]) * (acc - __ldg(&B.y[ri]));
+            }
+        }
+        if (!grid_barrier(ctl)) return;
+        // ---- phase C: subset back-projection + g/h update (16x16 tiles, one pixel per thread)
+        {
+            const int total = build_prefix(s_pre, nsl, [&](int s) {
+                const BatchSlice &B = SL[s];
+                return (t < B.T) ? B.G.ntx * B.G.nty : 0;
+            });
+            for (int u = blockIdx.x; u < total; u += gridDim.x) {
+                const int s = find_slice(s_pre, nsl, u);
+                const BatchSlice &B = SL[s];
+                const int tile = u - s_pre[s];
+                const int ty = tile / B.G.ntx, tx = tile - ty * B.G.ntx;
+                const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+                const int ix = tx * kTile + lx, iy = ty * kTile + ly;
+                const int m = t % B.M;
+                const int v0 = B.sub_off[m], nv = B.sub_off[m + 1] - v0;
+                const int ntiles = B.G.ntx * B.G.nty;
+                const float ox = ((float)lx - kTileHalf) * B.G.dx, oy = ((float)ly - kTileHalf) * B.G.dy;
+                float acc = 0.0f;
+                if (B.G.foot_t) {  // stored footprints, next view's prefetched
+                    const size_t vstride = (size_t)ntiles * (kTile * kTile);
+                    const size_t base = (size_t)tile * (kTile * kTile) + threadIdx.x;
+                    float4 tn = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float2 an = make_float2(0.f, 0.f);
+                    if (nv > 0) {
+                        const size_t i = (size_t)B.perm[v0] * vstride + base;
+                        tn = __ldcs(&B.G.foot_t[i]);
+                        an = __ldcs(&B.G.foot_an[i]);
+                    }
+                    for (int k = 0; k < nv; k++) {
+                        const Footprint F = footprint_from(tn, an);
+                        if (k + 1 < nv) {
+                            const size_t i = (size_t)B.perm[v0 + k + 1] * vstride + base;
+                            tn = __ldcs(&B.G.foot_t[i]);
+                            an = __ldcs(&B.G.foot_an[i]);
+                        }
+                        acc += footprint_dot_coherent(F, B.resid + (size_t)k * B.G.ns, B.G.ns);
+                    }
+                } else {
+                    for (int k = 0; k < nv; k++) {
+                        const int v = B.perm[v0 + k];
+                        const float2 cs = __ldg(&B.G.view_cs[v]);
+                        const float4 A = __ldg(&B.G.anchor[(size_t)v * ntiles + tile]);
+                        const Footprint F = sf_footprint(B.G, cs.x, cs.y, A, ox, oy);
+                        acc += footprint_dot_coherent(F, B.resid + (size_t)k * B.G.ns, B.G.ns);
+                    }
+                }
+                if (ix >= B.G.nx || iy >= B.G.ny) continue;
+                const size_t j = (size_t)iy * B.G.nx + ix;
+                const float rho = B.rho[t];
+                const float zeta = (float)B.M * acc;
+                const float g = __ldcg(&B.g[j]), xp = __ldcg(&B.x_new[j]), a = B.alpha;
+                const float ir = 1.0f / (rho + 1.0f);
+                B.g[j] = fmaf(rho * ir, fmaf(a, zeta, (1.0f - a) * g), g * ir);
+                if (B.algorithm == CT_ALG_PROPOSED)
+                    B.h[j] = fmaf(a, fmaf(__ldcg(&B.d_l[j]), xp, -zeta), (1.0f - a) * __ldcg(&B.h[j]));
+                else
+                    B.h[j] = zeta;
+                B.x[j] = xp;
+            }
+        }
+        if (!grid_barrier(ctl)) return;
+    }
+}
+
+double rho_cont(long k, double alpha)
+{
+    if (k == 0) return 1.0;
+    const double q = M_PI / (alpha * (double)(k + 1));
+    return q * std::sqrt(1.0 - 0.25 * q * q);
+}
+
+size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace ct
+
+using namespace ct;
+
+extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms, const float *const *y,
+                                                     const float *const *w, const ct_solve_params *params,
+                                                     float *const *x_inout, int nslices, ct_solve_report *reports,
+                                                     void *stream)
+{
+    if (!geoms || !y || !w || !params || !x_inout || nslices < 1 || nslices > kMaxSlices) {
+        set_error("ct_relaxed_oslalm_solve_batched: null argument or nslices outside [1, %d]", kMaxSlices);
+        return CT_EINVAL;
+    }
+    int dev = 0;
+    CT_CUDA_TRY(cudaGetDevice(&dev), "current device");
+    // validate and size the arena
+    std::vector<size_t> off(nslices);
+    size_t total = 0;
+    int Tmax = 0;
+    for (int i = 0; i < nslices; i++) {
+        const ct_geom *g = geoms[i];
+        const ct_solve_params *p = &params[i];
+        if (!g || !y[i] || !w[i] || !x_inout[i]) { set_error("slice %d: null argument", i); return CT_EINVAL; }
+        if (g->device != dev) { set_error("slice %d: geometry on device %d, current %d", i, g->device, dev); return CT_EINVAL; }
+        if (p->M < 1 || p->M > g->fan.na || p->n_iter < 1 || p->n_iter > 100000 || !(p->alpha >= 1.0f && p->alpha < 2.0f) ||
+            !(p->beta >= 0.0f) || p->potential < CT_POT_HYPERBOLA || p->potential > CT_POT_QUADRATIC ||
+            (p->potential != CT_POT_QUADRATIC && !(p->delta > 0.0f)) ||
+            (p->algorithm != CT_ALG_PROPOSED && p->algorithm != CT_ALG_SIMPLE) ||
+            (!p->continuation && !(p->rho_fixed > 0.0f))) {
+            set_error("slice %d: invalid solver parameters", i);
+            return CT_EINVAL;
+        }
+        if (p->init_fbp) {
+            ct_status sf = validate_fbp(g, CT_FBP_HANN);
+            if (sf != CT_OK) return sf;
+        }
+        if ((long)p->n_iter * p->M > 50000000L) { set_error("slice %d: n_iter * M too large", i); return CT_EINVAL; }
+        const int T = p->n_iter * p->M;
+        Tmax = std::max(Tmax, T);
+        int max_sub = (g->fan.na + p->M - 1) / p->M;
+        const size_t npix = (size_t)g->fan.nx * g->fan.ny;
+        off[i] = total;
+        total += al256(npix * 4) * 4 + al256((size_t)max_sub * g->fan.ns * 4) + al256((size_t)g->fan.na * 4) +
+                 al256((size_t)(p->M + 1) * 4) + al256((size_t)T * 4) + al256((size_t)p->n_iter * 16) +
+                 al256((size_t)p->n_iter * 8);
+    }
+    const size_t desc_off = total;
+    total += al256(sizeof(BatchSlice) * nslices) + al256(sizeof(BatchCtl));
+    char *arena = nullptr;
+    CT_CUDA_TRY(cudaMalloc(&arena, total), "allocating the batch arena");
+    struct ArenaGuard {
+        char *p;
+        ~ArenaGuard() { cudaFree(p); }
+    } aguard{arena};
+
+    cudaStream_t user = (cudaStream_t)stream, ws = nullptr;
+    CT_CUDA_TRY(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking), "creating batch stream");
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamDestroy(s); }
+    } sguard{ws};
+    cudaEvent_t ev_in, ev0, ev1, ev2;
+    CT_CUDA_TRY(cudaEventCreate(&ev_in), "event");
+    CT_CUDA_TRY(cudaEventCreate(&ev0), "event");
+    CT_CUDA_TRY(cudaEventCreate(&ev1), "event");
+    CT_CUDA_TRY(cudaEventCreate(&ev2), "event");
+    struct EvGuard {
+        cudaEvent_t a, b, c, d;
+        ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); cudaEventDestroy(c); cudaEventDestroy(d); }
+    } eguard{ev_in, ev0, ev1, ev2};
+    CT_CUDA_TRY(cudaEventRecord(ev_in, user), "event");
+    CT_CUDA_TRY(cudaStreamWaitEvent(ws, ev_in, 0), "ordering after caller's stream");
+
+    std::vector<BatchSlice> hs(nslices);
+    CT_CUDA_TRY(cudaMemsetAsync(arena, 0, total, ws), "clearing the batch arena");
+    for (int i = 0; i < nslices; i++) {
+        const ct_geom *g = geoms[i];
+        const ct_solve_params *p = &params[i];
+        const int M = p->M, T = p->n_iter * M;
+        const int max_sub = (g->fan.na + M - 1) / M;
+        const size_t npix = (size_t)g->fan.nx * g->fan.ny;
+        char *b = arena + off[i];
+        BatchSlice &B = hs[i];
+        B.G = g->fan;
+        B.x = x_inout[i];
+        B.x_new = (float *)b; b += al256(npix * 4);
+        B.g = (float *)b; b += al256(npix * 4);
+        B.h = (float *)b; b += al256(npix * 4);
+        B.d_l = (float *)b; b += al256(npix * 4);
+        B.resid = (float *)b; b += al256((size_t)max_sub * g->fan.ns * 4);
+        int *perm = (int *)b; b += al256((size_t)g->fan.na * 4);
+        int *sub = (int *)b; b += al256((size_t)(M + 1) * 4);
+        float *rho = (float *)b; b += al256((size_t)T * 4);
+        B.rmsd_acc = (double *)b; b += al256((size_t)p->n_iter * 16);
+        B.stamp = (unsigned long long *)b;
+        B.y = y[i];
+        B.w = w[i];
+        B.x_ref = p->x_ref;
+        B.perm = perm;
+        B.sub_off = sub;
+        B.rho = rho;
+        B.P = Pot{p->potential, p->potential == CT_POT_QUADRATIC ? 0.0f : 1.0f / p->delta};
+        B.alpha = p->alpha;
+        B.beta = p->beta;
+        const double R = p->fov_radius > 0.0f ? (double)p->fov_radius : g->fov_radius;
+        B.r2max = (float)(R * R);
+        B.M = M;
+        B.T = T;
+        B.n_iter = p->n_iter;
+        B.nonneg = p->nonneg;
+        B.algorithm = p->algorithm;
+        std::vector<int> hp;
+        std::vector<int> ho(M + 1);
+        for (int m = 0; m < M; m++) {
+            ho[m] = (int)hp.size();
+            for (int v = m; v < g->fan.na; v += M) hp.push_back(v);
+        }
+        ho[M] = g->fan.na;
+        std::vector<float> hr(T);
+        for (int k = 0; k < T; k++) hr[k] = (float)(p->continuation ? rho_cont(k, p->alpha) : (double)p->rho_fixed);
+        CT_CUDA_TRY(cudaMemcpyAsync(perm, hp.data(), sizeof(int) * hp.size(), cudaMemcpyHostToDevice, ws), "upload");
+        CT_CUDA_TRY(cudaMemcpyAsync(sub, ho.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice, ws), "upload");
+        CT_CUDA_TRY(cudaMemcpyAsync(rho, hr.data(), sizeof(float) * T, cudaMemcpyHostToDevice, ws), "upload");
+        CT_CUDA_TRY(cudaStreamSynchronize(ws), "upload");  // host vectors go out of scope
+    }
+    BatchSlice *dsl = (BatchSlice *)(arena + desc_off);
+    BatchCtl *ctl = (BatchCtl *)(arena + desc_off + al256(sizeof(BatchSlice) * nslices));
+    CT_CUDA_TRY(cudaMemcpyAsync(dsl, hs.data(), sizeof(BatchSlice) * nslices, cudaMemcpyHostToDevice, ws), "upload");
+
+    // persistent grid: every CTA co-resident (cooperative launch)
+    int nsm = 0, per_sm = 0;
+    CT_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    CT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, kThreads, 0), "occupancy");
+    if (per_sm < 1) { set_error("batched kernel cannot be resident"); return CT_ECUDA; }
+    const int grid = nsm * per_sm;
+
+    CT_CUDA_TRY(cudaEventRecord(ev0, ws), "event");
+    for (int i = 0; i < nslices; i++) {
+        const ct_geom *g = geoms[i];
+        const ct_solve_params *p = &params[i];
+        BatchSlice &B = hs[i];
+        if (p->init_fbp) CT_CUDA_TRY(launch_fbp(g, y[i], x_inout[i], CT_FBP_HANN, ws), "initial FBP");
+        CT_CUDA_TRY(launch_fp(g->fan, FP_ONES_W, nullptr, g->d_views_all, g->fan.na, g->d_sino_ws, nullptr, w[i], ws),
+                    "D_L forward");
+        CT_CUDA_TRY(launch_bp(g->fan, BP_PLAIN, g->d_sino_ws, g->d_views_all, g->fan.na, B.d_l, 1.0f, 0, nullptr, ws),
+                    "D_L back");
+        // rho = 1, zeta = g = M grad L_M(x), h = D_L x - zeta (last subset)
+        const int M = p->M;
+        const int vlast = (g->fan.na - (M - 1) + M - 1) / M;  // views in subset M-1
+        const int off_last = g->fan.na - vlast;
+        SolveDev S{};
+        S.x = x_inout[i];
+        S.g = B.g;
+        S.h = B.h;
+        S.d_l = B.d_l;
+        S.M_scale = (float)M;
+        S.algorithm = p->algorithm;
+        CT_CUDA_TRY(launch_fp(g->fan, FP_RESID, x_inout[i], B.perm + off_last, vlast, B.resid, y[i], w[i], ws),
+                    "init forward");
+        CT_CUDA_TRY(launch_bp(g->fan, BP_SOLVE_INIT, B.resid, B.perm + off_last, vlast, nullptr, 1.0f, 0, &S, ws),
+                    "init back");
+    }
+    CT_CUDA_TRY(cudaEventRecord(ev1, ws), "event");
+    int nsl = nslices;
+    void *args[] = {(void *)&dsl, (void *)&nsl, (void *)&Tmax, (void *)&ctl};
+    CT_CUDA_TRY(cudaLaunchCooperativeKernel((void *)batched_kernel, dim3(grid), dim3(kThreads), args, 0, ws),
+                "persistent batched launch");
+    CT_CUDA_TRY(cudaEventRecord(ev2, ws), "event");
+    CT_CUDA_TRY(cudaEventRecord(ev_in, ws), "event");
+    CT_CUDA_TRY(cudaStreamWaitEvent(user, ev_in, 0), "ordering caller's stream");
+    CT_CUDA_TRY(cudaStreamSynchronize(ws), "batched solve");
+
+    BatchCtl hctl;
+    CT_CUDA_TRY(cudaMemcpy(&hctl, ctl, sizeof(hctl), cudaMemcpyDeviceToHost), "read status");
+    if (hctl.error) {
+        set_error("batched solve: a grid barrier wait gave up");
+        return CT_ETIMEOUT;
+    }
+    float ms_setup = 0.0f, ms_all = 0.0f;
+    cudaEventElapsedTime(&ms_setup, ev0, ev1);
+    cudaEventElapsedTime(&ms_all, ev0, ev2);
+    if (reports) {
+        for (int i = 0; i < nslices; i++) {
+            const ct_solve_params *p = &params[i];
+            const int n = p->n_iter;
+            std::vector<double> acc(2 * (size_t)n);
+            std::vector<unsigned long long> st(n);
+            CT_CUDA_TRY(cudaMemcpy(acc.data(), hs[i].rmsd_acc, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost), "read");
+            CT_CUDA_TRY(cudaMemcpy(st.data(), hs[i].stamp, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost),
+                        "read");
+            ct_solve_report *r = &reports[i];
+            r->iters_done = n;
+            r->seconds = ms_all * 1e-3;
+            r->seconds_to_tol = -1.0;
+            r->rmsd_hu_last = -1.0f;
+            const float tol = p->stop_rmsd_hu > 0.0f ? p->stop_rmsd_hu : 1.0f;
+            for (int k = 0; k < n; k++) {
+                const double tk = ms_setup * 1e-3 + (double)(st[k] - hctl.t_start) * 1e-9;
+                if (r->iter_seconds) r->iter_seconds[k] = tk;
+                if (p->x_ref) {
+                    const float v = acc[2 * k + 1] > 0 ? (float)(std::sqrt(acc[2 * k] / acc[2 * k + 1]) * p->hu_per_unit)
+                                                       : 0.0f;
+                    if (r->rmsd_trace_hu) r->rmsd_trace_hu[k] = v;
+                    r->rmsd_hu_last = v;
+                    if (r->seconds_to_tol < 0.0 && v <= tol) r->seconds_to_tol = tk;
+                }
+            }
+        }
+    }
+    return CT_OK;
+}

@@ -38,6 +38,8 @@ struct FanDev {
     const float2 *foot_an;    // [na][ntiles][256]: amplitude, n (int bits)
     const long long *row_ptr; // [na*ns + 1]: start of each ray's entries
     const int2 *row_ent;      // (pixel index, a_ij bits), ray-major, march order within a ray
+    int fp_variant;           // forward projector chosen by ct_geom_autotune (FP_AUTO: default order)
+    int bp_variant;           // back-projector chosen by ct_geom_autotune (BP_AUTO)
 };
 
 // Solver state shared by the kernels of one subiteration (device pointers).
@@ -299,6 +301,8 @@ __device__ __forceinline__ Footprint footprint_from(float4 t, float2 an)
 // ---------------------------------------------------------------- launchers (projectors.cu)
 
 enum FpMode { FP_PLAIN = 0, FP_RESID = 1, FP_ONES_W = 2 };
+enum FpVariant { FP_AUTO = 0, FP_VAR_CSR = 1, FP_VAR_BUNDLE = 2, FP_VAR_RAY = 3 };
+enum BpVariant { BP_AUTO = 0, BP_VAR_STORED = 1, BP_VAR_FLY = 2 };
 enum BpMode { BP_PLAIN = 0, BP_SOLVE_INIT = 1, BP_SOLVE_UPDATE = 2 };
 
 // out rows follow `views` (device list of nviews view indices).
@@ -317,5 +321,81 @@ ct_status validate_fbp(const ct_geom *g, int window);
 
 ct_status validate_views(const ct_geom *g, const int *views, int nviews);
 ct_status stage_views(const ct_geom *g, const int *views, int nviews, const int **dev_views, cudaStream_t st);
+
+// ---------------------------------------------------------------- regularizer (Eq. (def_reg))
+
+struct Pot {
+    int kind;
+    float inv_delta;
+    // phi'(t) and omega(t) = phi'(t)/t
+    __device__ __forceinline__ void eval(float t, float &dphi, float &omega) const
+    {
+        if (kind == CT_POT_HYPERBOLA) {
+            const float q = t * inv_delta;
+            omega = rsqrtf(fmaf(q, q, 1.0f));
+        } else if (kind == CT_POT_FAIR) {
+            omega = 1.0f / fmaf(fabsf(t), inv_delta, 1.0f);
+        } else {
+            omega = 1.0f;
+        }
+        dphi = t * omega;
+    }
+};
+
+// COHERENT loads bypass L1 and the read-only path: needed when x is rewritten
+// by other CTAs of the same (persistent) kernel.
+template <bool COHERENT = false>
+__device__ __forceinline__ float ld_img(const float *p)
+{
+    return COHERENT ? __ldcg(p) : __ldg(p);
+}
+
+template <bool COHERENT = false>
+__device__ __forceinline__ void reg_terms(const FanDev &G, const float *__restrict__ x, int ix, int iy, float beta,
+                                          Pot P, float &grad, float &curv)
+{
+    const float xj = ld_img<COHERENT>(&x[(size_t)iy * G.nx + ix]);
+    const int ddx[4] = {1, 0, 1, 1};
+    const int ddy[4] = {0, 1, 1, -1};
+    const float bd = beta * 0.70710678118654752f;
+    grad = 0.0f;
+    curv = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const float bi = (i < 2) ? beta : bd;
+        const int fx = ix + ddx[i], fy = iy + ddy[i];
+        if (fx >= 0 && fx < G.nx && fy >= 0 && fy < G.ny) {
+            float d, o;
+            P.eval(xj - ld_img<COHERENT>(&x[(size_t)fy * G.nx + fx]), d, o);
+            grad = fmaf(bi, d, grad);
+            curv = fmaf(2.0f * bi, o, curv);
+        }
+        const int bx = ix - ddx[i], by = iy - ddy[i];
+        if (bx >= 0 && bx < G.nx && by >= 0 && by < G.ny) {
+            float d, o;
+            P.eval(ld_img<COHERENT>(&x[(size_t)by * G.nx + bx]) - xj, d, o);
+            grad = fmaf(-bi, d, grad);
+            curv = fmaf(2.0f * bi, o, curv);
+        }
+    }
+}
+
+// footprint_dot with L1-bypassing loads of the detector row (rows rewritten by
+// other CTAs of a persistent kernel); same arithmetic.
+__device__ __forceinline__ float footprint_dot_coherent(const Footprint &F, const float *row, int ns)
+{
+    const int j0 = (int)floorf(F.t0 - 0.5f) + 1;
+    const int jl = (int)ceilf(F.t3 + 0.5f) - 1;
+    int s = F.n + j0;
+    float rp = ((unsigned)s < (unsigned)ns) ? __ldcg(&row[s]) : 0.0f;
+    float acc = 0.0f;
+    for (int j = j0; j < jl; j++) {
+        s++;
+        const float rn = ((unsigned)s < (unsigned)ns) ? __ldcg(&row[s]) : 0.0f;
+        acc = fmaf(trap_cdf(F, (float)j + 0.5f), rp - rn, acc);
+        rp = rn;
+    }
+    return F.amp * fmaf(trap_area(F), rp, acc);
+}
 
 }  // namespace ct

@@ -425,7 +425,12 @@ cudaError_t launch_fp(const FanDev &G, int mode, const float *x, const int *view
                       const float *y, const float *w, cudaStream_t st)
 {
     if (nviews <= 0) return cudaSuccess;
-    if (G.row_ptr) {
+    const bool bundle_ok = G.max_span <= kMaxSpan && G.nx <= kMaxMarch && G.ny <= kMaxMarch;
+    int var = G.fp_variant;
+    if (var == FP_VAR_CSR && !G.row_ptr) var = FP_AUTO;
+    if (var == FP_VAR_BUNDLE && !bundle_ok) var = FP_AUTO;
+    if (var == FP_AUTO) var = G.row_ptr ? FP_VAR_CSR : (bundle_ok ? FP_VAR_BUNDLE : FP_VAR_RAY);
+    if (var == FP_VAR_CSR) {
         const unsigned blocks = (unsigned)(((long)nviews * G.ns + 7) / 8);
         switch (mode) {
         case FP_PLAIN: fp_csr_kernel<FP_PLAIN><<<blocks, 256, 0, st>>>(G, x, views, nviews, out, y, w); break;
@@ -434,7 +439,7 @@ cudaError_t launch_fp(const FanDev &G, int mode, const float *x, const int *view
         }
         return cudaGetLastError();
     }
-    if (G.max_span <= kMaxSpan && G.nx <= kMaxMarch && G.ny <= kMaxMarch) {
+    if (var == FP_VAR_BUNDLE) {
         const unsigned blocks = (unsigned)nviews * (unsigned)((G.ns + 31) / 32);
         switch (mode) {
         case FP_PLAIN: fp_bundle_kernel<FP_PLAIN><<<blocks, kBundleWarps * 32, 0, st>>>(G, x, views, nviews, out, y, w); break;
@@ -460,7 +465,8 @@ cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *v
     dim3 grid(G.ntx, G.nty);
     SolveDev s0{};
     const SolveDev &SS = S ? *S : s0;
-    if (G.foot_t) {
+    const bool stored = G.foot_t && G.bp_variant != BP_VAR_FLY;
+    if (stored) {
         switch (mode) {
         case BP_PLAIN: bp_fan2d_kernel<BP_PLAIN, true><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
         case BP_SOLVE_INIT: bp_fan2d_kernel<BP_SOLVE_INIT, true><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;

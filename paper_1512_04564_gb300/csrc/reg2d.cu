@@ -17,53 +17,6 @@ namespace ct {
 
 namespace {
 
-struct Pot {
-    int kind;
-    float inv_delta;
-    // phi'(t) and omega(t) = phi'(t)/t
-    __device__ __forceinline__ void eval(float t, float &dphi, float &omega) const
-    {
-        if (kind == CT_POT_HYPERBOLA) {
-            const float q = t * inv_delta;
-            omega = rsqrtf(fmaf(q, q, 1.0f));
-        } else if (kind == CT_POT_FAIR) {
-            omega = 1.0f / fmaf(fabsf(t), inv_delta, 1.0f);
-        } else {
-            omega = 1.0f;
-        }
-        dphi = t * omega;
-    }
-};
-
-__device__ __forceinline__ void reg_terms(const FanDev &G, const float *__restrict__ x, int ix, int iy, float beta,
-                                          Pot P, float &grad, float &curv)
-{
-    const float xj = __ldg(&x[(size_t)iy * G.nx + ix]);
-    const int ddx[4] = {1, 0, 1, 1};
-    const int ddy[4] = {0, 1, 1, -1};
-    const float bd = beta * 0.70710678118654752f;
-    grad = 0.0f;
-    curv = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        const float bi = (i < 2) ? beta : bd;
-        const int fx = ix + ddx[i], fy = iy + ddy[i];
-        if (fx >= 0 && fx < G.nx && fy >= 0 && fy < G.ny) {
-            float d, o;
-            P.eval(xj - __ldg(&x[(size_t)fy * G.nx + fx]), d, o);
-            grad = fmaf(bi, d, grad);
-            curv = fmaf(2.0f * bi, o, curv);
-        }
-        const int bx = ix - ddx[i], by = iy - ddy[i];
-        if (bx >= 0 && bx < G.nx && by >= 0 && by < G.ny) {
-            float d, o;
-            P.eval(__ldg(&x[(size_t)by * G.nx + bx]) - xj, d, o);
-            grad = fmaf(-bi, d, grad);
-            curv = fmaf(2.0f * bi, o, curv);
-        }
-    }
-}
-
 __global__ void __launch_bounds__(256) reg_gradient_kernel(FanDev G, const float *__restrict__ x, float beta, Pot P,
                                                            float *__restrict__ grad, float *__restrict__ curv)
 {

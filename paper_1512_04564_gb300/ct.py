@@ -73,9 +73,13 @@ def _load():
         "ct_sqs_diag_noalloc": [vp, vp, vp, vp],
         "ct_fbp": [vp, vp, vp, cint, vp],
         "ct_geom_precompute": [vp, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong), vp],
+        "ct_geom_autotune": [vp, cint, ip, ip, vp],
         "ct_reg_gradient": [vp, vp, cfl, cfl, cint, vp, vp, vp],
         "ct_relaxed_oslalm_solve": [vp, vp, vp, ctypes.POINTER(ct_solve_params), vp,
                                     ctypes.POINTER(ct_solve_report), vp],
+        "ct_relaxed_oslalm_solve_batched": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                            ctypes.POINTER(ct_solve_params), ctypes.POINTER(vp), cint,
+                                            ctypes.POINTER(ct_solve_report), vp],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -90,8 +94,9 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_geom_precompute", "ct_forward", "ct_back", "ct_sqs_diag",
-            "ct_sqs_diag_noalloc", "ct_fbp", "ct_reg_gradient", "ct_relaxed_oslalm_solve", "ct_last_error", "ct_version")
+EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_geom_precompute", "ct_geom_autotune", "ct_forward", "ct_back", "ct_sqs_diag",
+            "ct_sqs_diag_noalloc", "ct_fbp", "ct_reg_gradient", "ct_relaxed_oslalm_solve",
+            "ct_relaxed_oslalm_solve_batched", "ct_last_error", "ct_version")
 
 
 class CTError(RuntimeError):
@@ -173,6 +178,18 @@ def ct_geom_precompute(geom: Geometry, max_bytes: int = 0, stream=None) -> int:
     return int(b.value)
 
 
+FP_VARIANTS = {1: "resident rows", 2: "bundle", 3: "ray"}
+BP_VARIANTS = {1: "stored footprints", 2: "on the fly"}
+
+
+def ct_geom_autotune(geom: Geometry, views_per_launch: int = 0, stream=None) -> tuple[str, str]:
+    """Time the projector decompositions available for this geometry and keep the fastest."""
+    f, b = ctypes.c_int(0), ctypes.c_int(0)
+    _check(_lib.ct_geom_autotune(geom.handle, int(views_per_launch), ctypes.byref(f), ctypes.byref(b),
+                                 _stream(stream)))
+    return FP_VARIANTS[f.value], BP_VARIANTS[b.value]
+
+
 def ct_forward(geom: Geometry, x: torch.Tensor, y: torch.Tensor, views=None, stream=None) -> torch.Tensor:
     arr, nv = _views(views, geom.na)
     _check(_lib.ct_forward(geom.handle, _ptr(x, "x", geom.nx * geom.ny), _ptr(y, "y", nv * geom.ns), arr, nv,
@@ -225,6 +242,19 @@ def ct_relaxed_oslalm_solve(geom: Geometry, y: torch.Tensor, w: torch.Tensor, x:
                             stop_rmsd_hu=0.0, init_fbp=False, stream=None) -> dict:
     """Relaxed OS-LALM (Algorithm 1 / 2); x is updated in place.  Returns the report as a dict."""
     n = geom.nx * geom.ny
+    p = _params(geom, M=M, n_iter=n_iter, alpha=alpha, beta=beta, delta=delta, potential=potential,
+                algorithm=algorithm, nonneg=nonneg, continuation=continuation, rho_fixed=rho_fixed, x_ref=x_ref,
+                hu_per_unit=hu_per_unit, fov_radius=fov_radius, stop_rmsd_hu=stop_rmsd_hu, init_fbp=init_fbp)
+    r, trace, its = _report(n_iter)
+    _check(_lib.ct_relaxed_oslalm_solve(geom.handle, _ptr(y, "y", geom.na * geom.ns), _ptr(w, "w", geom.na * geom.ns),
+                                        ctypes.byref(p), _ptr(x, "x", n), ctypes.byref(r), _stream(stream)))
+    return _report_dict(r, trace, its, x_ref is not None)
+
+
+def _params(geom, *, M, n_iter, alpha, beta, delta, potential="hyperbola", algorithm="proposed", nonneg=True,
+            continuation=True, rho_fixed=0.0, x_ref=None, hu_per_unit=1.0, fov_radius=0.0, stop_rmsd_hu=0.0,
+            init_fbp=False):
+    n = geom.nx * geom.ny
     p = ct_solve_params()
     p.M, p.n_iter, p.alpha, p.beta, p.delta = M, n_iter, alpha, beta, delta
     p.potential = POTENTIALS[potential] if isinstance(potential, str) else int(potential)
@@ -233,22 +263,50 @@ def ct_relaxed_oslalm_solve(geom: Geometry, y: torch.Tensor, w: torch.Tensor, x:
     p.x_ref = _ptr(x_ref, "x_ref", n)
     p.hu_per_unit, p.fov_radius, p.stop_rmsd_hu = hu_per_unit, fov_radius, stop_rmsd_hu
     p.init_fbp = int(bool(init_fbp))
+    return p
+
+
+def _report(n_iter):
     r = ct_solve_report()
     trace = (ctypes.c_float * max(n_iter, 1))()
     its = (ctypes.c_double * max(n_iter, 1))()
     r.rmsd_trace_hu = ctypes.cast(trace, ctypes.POINTER(ctypes.c_float))
     r.iter_seconds = ctypes.cast(its, ctypes.POINTER(ctypes.c_double))
-    _check(_lib.ct_relaxed_oslalm_solve(geom.handle, _ptr(y, "y", geom.na * geom.ns), _ptr(w, "w", geom.na * geom.ns),
-                                        ctypes.byref(p), _ptr(x, "x", n), ctypes.byref(r), _stream(stream)))
+    return r, trace, its
+
+
+def _report_dict(r, trace, its, has_ref):
     k = r.iters_done
     return {
         "iters_done": k,
         "seconds": r.seconds,
         "seconds_to_tol": r.seconds_to_tol,
         "rmsd_hu_last": r.rmsd_hu_last,
-        "rmsd_trace_hu": list(trace[:k]) if x_ref is not None else [],
+        "rmsd_trace_hu": list(trace[:k]) if has_ref else [],
         "iter_seconds": list(its[:k]),
     }
+
+
+def ct_relaxed_oslalm_solve_batched(geoms, ys, ws, xs, params: list[dict], stream=None) -> list[dict]:
+    """Batched relaxed OS-LALM in one persistent launch; params[i] holds the keyword arguments of
+    ct_relaxed_oslalm_solve for slice i.  Every x is updated in place.  Returns the per-slice reports."""
+    n = len(geoms)
+    if not (len(ys) == len(ws) == len(xs) == len(params) == n):
+        raise ValueError("geoms, ys, ws, xs and params must have one entry per slice")
+    VP = ctypes.c_void_p * n
+    gh = VP(*[g.handle.value for g in geoms])
+    yp = VP(*[_ptr(ys[i], "y", geoms[i].na * geoms[i].ns).value for i in range(n)])
+    wp = VP(*[_ptr(ws[i], "w", geoms[i].na * geoms[i].ns).value for i in range(n)])
+    xp = VP(*[_ptr(xs[i], "x", geoms[i].nx * geoms[i].ny).value for i in range(n)])
+    P = (ct_solve_params * n)(*[_params(geoms[i], **params[i]) for i in range(n)])
+    reps = [_report(params[i]["n_iter"]) for i in range(n)]
+    R = (ct_solve_report * n)(*[r for r, _, _ in reps])
+    _check(_lib.ct_relaxed_oslalm_solve_batched(ctypes.cast(gh, ctypes.POINTER(ctypes.c_void_p)),
+                                                ctypes.cast(yp, ctypes.POINTER(ctypes.c_void_p)),
+                                                ctypes.cast(wp, ctypes.POINTER(ctypes.c_void_p)), P,
+                                                ctypes.cast(xp, ctypes.POINTER(ctypes.c_void_p)), n, R,
+                                                _stream(stream)))
+    return [_report_dict(R[i], reps[i][1], reps[i][2], params[i].get("x_ref") is not None) for i in range(n)]
 
 
 def version() -> int:

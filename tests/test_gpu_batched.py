@@ -1,0 +1,133 @@
+"""Batched relaxed OS-LALM (one persistent launch) against the single-slice solver and the oracle.
+
+A batch mixes image sizes, detector sizes, view counts and subset counts;
+some slices use the resident system matrix and some the on-the-fly
+footprints; two slices share one geometry.  Each slice must match the
+single-slice solve (RMSD <= 0.01 HU: the same arithmetic with a different
+summation order in the projectors) and one slice the FP64 oracle
+(<= 0.1 HU, the solver parity bar).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import solver as osolver
+from oracle.projector import FanProjector
+
+pytestmark = pytest.mark.gpu
+
+MU_W = 0.02
+BETA = 2.0 ** 14 / MU_W ** 2
+DELTA = 10 * MU_W / 1000
+HU = 1000 / MU_W
+
+
+def _problem(seed, nx, ns, na, dx):
+    g = synth.FanArcGeometry(nx=nx, ny=nx, dx=dx, dy=dx, ns=ns, ds=1.0239 * 128 / ns * nx * dx / 128, na=na,
+                             dso=541.0, dsd=949.0)
+    r = 0.4 * nx * dx
+    E = [synth.Ellipse(0.0, 0.0, r, 0.8 * r, 0.2 + seed, 0.018), synth.Ellipse(0.2 * r, -0.1 * r, 0.2 * r, 0.15 * r, 0.0, -0.01),
+         synth.Ellipse(-0.3 * r, 0.2 * r, 0.1 * r, 0.1 * r, 0.0, 0.006)]
+    y, w = synth.transmission_data(synth.fan_arc_line_integrals(E, g), 1e5, 5.0, seed)
+    return g, y.astype(np.float32), w.astype(np.float32)
+
+
+CASES = [  # (seed, nx, ns, na, dx, M, resident)
+    (1, 64, 96, 90, 2.0, 5, True),
+    (2, 96, 128, 120, 1.4, 12, False),
+    (3, 128, 160, 180, 1.0, 10, True),
+    (4, 64, 96, 90, 2.0, 9, True),     # shares the first slice's geometry
+    (5, 80, 112, 60, 1.6, 7, False),   # uneven subsets (60 = 7 * 8 + 4)
+]
+
+
+def _hu_rmsd(a, b, g):
+    return osolver.rmsd_hu(a.astype(np.float64), b.astype(np.float64), osolver.fov_mask(g), HU)
+
+
+def test_batched_matches_single_slice_solves():
+    from paper_1512_04564_gb300 import ct
+
+    geoms, ys, ws, xs, params, probs = {}, [], [], [], [], []
+    for seed, nx, ns, na, dx, M, resident in CASES:
+        key = (nx, ns, na, dx)
+        g, y, w = _problem(seed, nx, ns, na, dx)
+        if key not in geoms:
+            G = ct.Geometry.from_fan(g)
+            if resident:
+                ct.ct_geom_precompute(G)
+            geoms[key] = G
+        probs.append((g, geoms[key], y, w, M))
+        ys.append(torch.from_numpy(y).cuda())
+        ws.append(torch.from_numpy(w).cuda())
+        xs.append(torch.zeros(g.ny, g.nx, device="cuda"))
+        params.append(dict(M=M, n_iter=4, alpha=1.999, beta=BETA, delta=DELTA))
+    G_list = [p[1] for p in probs]
+    # references: one single-slice solve per slice, also its x* for the trace
+    singles, refs = [], []
+    for i, (g, G, y, w, M) in enumerate(probs):
+        xr = torch.zeros(g.ny, g.nx, device="cuda")
+        ct.ct_relaxed_oslalm_solve(G, ys[i], ws[i], xr, M=1, n_iter=30, alpha=1.999, beta=BETA, delta=DELTA)
+        refs.append(xr)
+        xsng = torch.zeros(g.ny, g.nx, device="cuda")
+        rep = ct.ct_relaxed_oslalm_solve(G, ys[i], ws[i], xsng, x_ref=xr, hu_per_unit=HU, **params[i])
+        singles.append((xsng, rep))
+        params[i]["x_ref"] = xr
+        params[i]["hu_per_unit"] = HU
+    reps = ct.ct_relaxed_oslalm_solve_batched(G_list, ys, ws, xs, params)
+    torch.cuda.synchronize()
+    for i, (g, G, y, w, M) in enumerate(probs):
+        d = _hu_rmsd(xs[i].cpu().numpy(), singles[i][0].cpu().numpy(), g)
+        assert d <= 0.01, (i, d)
+        tb, ts = reps[i]["rmsd_trace_hu"], singles[i][1]["rmsd_trace_hu"]
+        assert len(tb) == 4 and np.allclose(tb, ts, rtol=1e-3, atol=1e-2), (i, tb, ts)
+        assert all(b > a for a, b in zip(reps[i]["iter_seconds"], reps[i]["iter_seconds"][1:]))
+
+
+def test_batched_slice_matches_oracle():
+    from paper_1512_04564_gb300 import ct
+
+    seed, nx, ns, na, dx, M, _ = CASES[2]
+    g, y, w = _problem(seed, nx, ns, na, dx)
+    G = ct.Geometry.from_fan(g)
+    seed2, nx2, ns2, na2, dx2, M2, _ = CASES[0]
+    g2, y2, w2 = _problem(seed2, nx2, ns2, na2, dx2)
+    G2 = ct.Geometry.from_fan(g2)
+    x1 = torch.zeros(g.ny, g.nx, device="cuda")
+    x2 = torch.zeros(g2.ny, g2.nx, device="cuda")
+    p = dict(n_iter=3, alpha=1.999, beta=BETA, delta=DELTA)
+    ct.ct_relaxed_oslalm_solve_batched([G, G2], [torch.from_numpy(y).cuda(), torch.from_numpy(y2).cuda()],
+                                       [torch.from_numpy(w).cuda(), torch.from_numpy(w2).cuda()], [x1, x2],
+                                       [dict(M=M, **p), dict(M=M2, **p)])
+    prob = osolver.PWLSProblem(FanProjector(g), y.astype(np.float64), w.astype(np.float64), BETA, DELTA)
+    xo = osolver.relaxed_os_lalm(prob, np.zeros((g.ny, g.nx)), M, 1.999, 3)
+    assert _hu_rmsd(x1.cpu().numpy(), xo, g) <= 0.1
+
+
+def test_batched_rejects_bad_arguments():
+    from paper_1512_04564_gb300 import ct
+
+    g, y, w = _problem(*CASES[0][:5])
+    G = ct.Geometry.from_fan(g)
+    with pytest.raises(ct.CTError):
+        ct.ct_relaxed_oslalm_solve_batched([G], [torch.from_numpy(y).cuda()], [torch.from_numpy(w).cuda()],
+                                           [torch.zeros(g.ny, g.nx, device="cuda")],
+                                           [dict(M=0, n_iter=2, alpha=1.999, beta=BETA, delta=DELTA)])
+
+
+def test_autotune_choice_keeps_parity():
+    from paper_1512_04564_gb300 import ct
+
+    g, y, w = _problem(*CASES[2][:5])
+    G = ct.Geometry.from_fan(g)
+    ct.ct_geom_precompute(G)
+    fp, bp = ct.ct_geom_autotune(G, 20)
+    assert fp in ("resident rows", "bundle", "ray") and bp in ("stored footprints", "on the fly")
+    x = torch.from_numpy(np.random.default_rng(0).random((g.ny, g.nx)).astype(np.float32)).cuda()
+    yy = torch.empty(g.na, g.ns, device="cuda")
+    ct.ct_forward(G, x, yy)
+    ref = FanProjector(g).forward(x.cpu().numpy().astype(np.float64))
+    den = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+    assert np.max(np.abs(yy.cpu().numpy() - ref) / den) <= 3e-5
