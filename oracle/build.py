@@ -15,7 +15,7 @@ import tempfile
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["sf_fan_oracle.c"]
+SOURCES = ["sf_fan_oracle.c", "sf_helical_oracle.c"]
 LIB = os.path.join(BUILD_DIR, "liboracle_ct.so")
 
 

@@ -5,9 +5,12 @@ ORACLE -- test infrastructure only.
 R(x) = sum_i beta_i sum_n kappa_n kappa_{n+s_i} phi([C_i x]_n)      (Sec. III, Eq. (def_reg))
 
 with [C_i x]_n = x_n - x_{n+s_i}, counted for pairs whose both pixels lie in
-the image, kappa = 1, and beta_i = beta / ||s_i|| (axis neighbours beta,
-diagonal neighbours beta/sqrt(2)).  In 2-D the four directions
-(1,0), (0,1), (1,1), (1,-1) cover all 8 neighbours.
+the image, kappa = 1, and beta_i = beta / ||s_i|| with ||s_i|| in index units
+(axis neighbours beta, face diagonals beta/sqrt(2), body diagonals
+beta/sqrt(3)).  In 2-D the four directions (1,0), (0,1), (1,1), (1,-1) cover
+all 8 neighbours; in 3-D thirteen directions cover all 26 (the paper's 3-D
+experiments use the 26 neighbours).  Offsets are (step in ix, step in iy[, step in iz])
+and arrays are [iy][ix] or [iz][iy][ix].
 
 The SQS diagonal uses Huber's curvature omega(t) = phi'(t)/t (Sec. III-A: the
 iteration-dependent curvature used "for faster convergence"):
@@ -23,6 +26,13 @@ import math
 import numpy as np
 
 DIRECTIONS_2D = ((1, 0), (0, 1), (1, 1), (1, -1))  # (step in ix, step in iy)
+# one offset of each +-pair of the 26 neighbours: the first nonzero step is positive
+DIRECTIONS_3D = tuple(d for d in ((i, j, k) for k in (-1, 0, 1) for j in (-1, 0, 1) for i in (-1, 0, 1))
+                      if d != (0, 0, 0) and next(c for c in d if c != 0) > 0)
+
+
+def directions(ndim: int):
+    return DIRECTIONS_2D if ndim == 2 else DIRECTIONS_3D
 
 
 def potential(kind: str, delta: float):
@@ -49,22 +59,25 @@ def direction_weights(beta: float, dirs=DIRECTIONS_2D):
 
 
 def _pair_slices(shape, d):
-    """Slices (a, b) so that x[a] and x[b] are the pixel pairs n, n + s (both in the image)."""
-    ny, nx = shape
-    sx, sy = d
+    """Slices (a, b) so that x[a] and x[b] are the pairs n, n + s (both inside the array).
+
+    ``d`` lists steps along (ix, iy[, iz]); ``shape`` is (ny, nx) or (nz, ny, nx).
+    """
 
     def one(step, n):
         return (slice(0, n - step), slice(step, n)) if step >= 0 else (slice(-step, n), slice(0, n + step))
 
-    ax, bx = one(sx, nx)
-    ay, by = one(sy, ny)
-    return (ay, ax), (by, bx)
+    axes = [one(step, n) for step, n in zip(d, shape[::-1])]  # along x, y[, z]
+    a = tuple(p[0] for p in axes[::-1])
+    b = tuple(p[1] for p in axes[::-1])
+    return a, b
 
 
 def value(x: np.ndarray, beta: float, delta: float, kind: str) -> float:
     phi, _, _ = potential(kind, delta)
+    dirs = directions(x.ndim)
     tot = 0.0
-    for d, bi in zip(DIRECTIONS_2D, direction_weights(beta)):
+    for d, bi in zip(dirs, direction_weights(beta, dirs)):
         a, b = _pair_slices(x.shape, d)
         tot += bi * float(np.sum(phi(x[a] - x[b])))
     return tot
@@ -72,8 +85,9 @@ def value(x: np.ndarray, beta: float, delta: float, kind: str) -> float:
 
 def gradient(x: np.ndarray, beta: float, delta: float, kind: str) -> np.ndarray:
     _, dphi, _ = potential(kind, delta)
+    dirs = directions(x.ndim)
     g = np.zeros_like(x, dtype=np.float64)
-    for d, bi in zip(DIRECTIONS_2D, direction_weights(beta)):
+    for d, bi in zip(dirs, direction_weights(beta, dirs)):
         a, b = _pair_slices(x.shape, d)
         f = bi * dphi(x[a] - x[b])
         g[a] += f
@@ -84,8 +98,9 @@ def gradient(x: np.ndarray, beta: float, delta: float, kind: str) -> np.ndarray:
 def curvature(x: np.ndarray, beta: float, delta: float, kind: str) -> np.ndarray:
     """Huber-curvature SQS diagonal D_R(x)."""
     _, _, omega = potential(kind, delta)
+    dirs = directions(x.ndim)
     D = np.zeros_like(x, dtype=np.float64)
-    for d, bi in zip(DIRECTIONS_2D, direction_weights(beta)):
+    for d, bi in zip(dirs, direction_weights(beta, dirs)):
         a, b = _pair_slices(x.shape, d)
         c = 2.0 * bi * omega(x[a] - x[b])
         D[a] += c

@@ -50,16 +50,17 @@ def interleaved_subsets(na: int, M: int) -> list[np.ndarray]:
 class PWLSProblem:
     """PWLS CT problem with an FP64 projector (oracle)."""
 
-    proj: object  # oracle.projector.FanProjector
-    y: np.ndarray  # [na][ns]
-    w: np.ndarray  # [na][ns]
+    proj: object  # oracle.projector.FanProjector or oracle.helical.HelicalProjector
+    y: np.ndarray  # [na][ns] (helical: [na][nt][ns])
+    w: np.ndarray  # same shape as y
     beta: float
     delta: float
     potential: str = "hyperbola"
 
     @property
     def shape(self):
-        return (self.proj.geom.ny, self.proj.geom.nx)
+        g = self.proj.geom
+        return (g.nz, g.ny, g.nx) if hasattr(g, "nz") else (g.ny, g.nx)
 
     def grad_L_subset(self, x: np.ndarray, views: np.ndarray) -> np.ndarray:
         """grad L_m(x) = A_m' W_m (A_m x - y_m)."""
@@ -140,10 +141,11 @@ def relaxed_os_lalm(problem: PWLSProblem, x0: np.ndarray, M: int, alpha: float, 
 
 
 def fov_mask(geom) -> np.ndarray:
-    """Pixels whose centres lie inside the disk every view sees."""
+    """Pixels whose centres lie inside the disk every view sees (3-D: that disk in every slice)."""
     xc = (np.arange(geom.nx) - (geom.nx - 1) / 2.0 + geom.offset_x) * geom.dx
     yc = (np.arange(geom.ny) - (geom.ny - 1) / 2.0 + geom.offset_y) * geom.dy
-    return (xc[None, :] ** 2 + yc[:, None] ** 2) <= geom.fov_radius() ** 2
+    m = (xc[None, :] ** 2 + yc[:, None] ** 2) <= geom.fov_radius() ** 2
+    return np.broadcast_to(m, (geom.nz,) + m.shape) if hasattr(geom, "nz") else m
 
 
 def rmsd_hu(x: np.ndarray, x_ref: np.ndarray, mask: np.ndarray, hu_per_unit: float) -> float:

@@ -11,7 +11,8 @@ al., "Parallel random numbers: as easy as 1, 2, 3", SC 2011), keyed by the
 caller's seed.
 """
 
-from .configs import FanArcGeometry, ScanConfig, fan2d_128, fan2d_512, config_by_name
+from .configs import (FanArcGeometry, HelicalConeGeometry, ScanConfig, fan2d_128, fan2d_512, helix3d_64,
+                      helix3d_512, config_by_name)
 from .phantom import (
     Ellipse,
     random_ellipses_cfg1,
@@ -20,12 +21,32 @@ from .phantom import (
     fan_arc_line_integrals,
     fan_arc_line_integrals_sampled,
 )
-from .noise import transmission_data, make_scan, SinoData
+from .phantom3d import (
+    Ellipsoid,
+    EllipticCylinder,
+    random_solids,
+    anthropomorphic_solids,
+    rasterize_solids,
+    helical_line_integrals,
+    helical_line_integrals_sampled,
+)
+from .noise import transmission_data, make_scan, phantom_of, SinoData
 from .rng import philox
 
 __all__ = [
     "FanArcGeometry",
+    "HelicalConeGeometry",
     "ScanConfig",
+    "helix3d_64",
+    "helix3d_512",
+    "Ellipsoid",
+    "EllipticCylinder",
+    "random_solids",
+    "anthropomorphic_solids",
+    "rasterize_solids",
+    "helical_line_integrals",
+    "helical_line_integrals_sampled",
+    "phantom_of",
     "fan2d_128",
     "fan2d_512",
     "config_by_name",

@@ -134,5 +134,111 @@ def fan2d_512(seed: int = 0) -> ScanConfig:
     )
 
 
+
+
+@dataclasses.dataclass(frozen=True)
+class HelicalConeGeometry:
+    """3-D helical cone-beam scan with a cylindrical (arc) detector.
+
+    * Volume: ``nx x ny x nz`` voxels of ``dx x dy x dz`` (mm), stored
+      ``[iz][iy][ix]``; voxel (ix, iy, iz) is centred at
+      ``((ix-(nx-1)/2+offset_x) dx, (iy-(ny-1)/2+offset_y) dy, (iz-(nz-1)/2+offset_z) dz)``.
+    * View v: transaxial angle ``beta_v = orbit_start + v * orbit / na`` (the
+      orbit spans ``orbit_deg / 360`` turns); the source is at
+      ``(-dso cos b, -dso sin b, z_src(b))`` with
+      ``z_src = pitch * (nt dt dso / dsd) * (b - b_mid) / (2 pi)``: the table
+      advances ``pitch`` times the detector's axial coverage at the
+      isocentre per turn, centred on the volume at mid-scan.
+    * Detector: ``ns`` cells of arc length ``ds`` at ``dsd`` (fan angle
+      ``(s-(ns-1)/2+offset_s) ds/dsd``) by ``nt`` rows of height ``dt``
+      (row t at height ``(t-(nt-1)/2+offset_t) dt`` on the cylinder);
+      sinograms are stored ``[view][row][cell]``.
+    """
+
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    dz: float
+    ns: int
+    ds: float
+    nt: int
+    dt: float
+    na: int
+    dso: float
+    dsd: float
+    pitch: float
+    orbit_deg: float
+    orbit_start_deg: float = 0.0
+    offset_x: float = 0.0
+    offset_y: float = 0.0
+    offset_z: float = 0.0
+    offset_s: float = 0.0
+    offset_t: float = 0.0
+
+    @property
+    def dgamma(self) -> float:
+        return self.ds / self.dsd
+
+    def betas(self):
+        import numpy as np
+
+        v = np.arange(self.na, dtype=np.float64)
+        return np.deg2rad(self.orbit_start_deg + v * self.orbit_deg / self.na)
+
+    def gammas(self):
+        import numpy as np
+
+        s = np.arange(self.ns, dtype=np.float64)
+        return (s - (self.ns - 1) / 2.0 + self.offset_s) * self.dgamma
+
+    def row_heights(self):
+        import numpy as np
+
+        t = np.arange(self.nt, dtype=np.float64)
+        return (t - (self.nt - 1) / 2.0 + self.offset_t) * self.dt
+
+    def source_z(self, beta):
+        mid = math.radians(self.orbit_start_deg + 0.5 * self.orbit_deg)
+        cover = self.nt * self.dt * self.dso / self.dsd
+        return self.pitch * cover * (beta - mid) / (2.0 * math.pi)
+
+    def transaxial(self) -> FanArcGeometry:
+        """The fan-arc geometry of the transaxial plane (same views and cells)."""
+        return FanArcGeometry(nx=self.nx, ny=self.ny, dx=self.dx, dy=self.dy, ns=self.ns, ds=self.ds, na=self.na,
+                              dso=self.dso, dsd=self.dsd, offset_x=self.offset_x, offset_y=self.offset_y,
+                              offset_s=self.offset_s, orbit_deg=self.orbit_deg, orbit_start_deg=self.orbit_start_deg)
+
+    def fov_radius(self) -> float:
+        return self.transaxial().fov_radius()
+
+    def with_(self, **kw) -> "HelicalConeGeometry":
+        return dataclasses.replace(self, **kw)
+
+
+def helix3d_512(seed: int = 0) -> ScanConfig:
+    """512x512x64 voxels of 0.98x0.98x0.625 mm; 888x32 cells of 1.0239x1.0964 mm; pitch 1;
+    984 views per turn over 3 turns; 26-neighbour hyperbola regularizer; M=24, alpha=1.999, 20 iterations."""
+    g = HelicalConeGeometry(nx=512, ny=512, nz=64, dx=0.98, dy=0.98, dz=0.625, ns=888, ds=1.0239, nt=32, dt=1.0964,
+                            na=3 * 984, dso=541.0, dsd=949.0, pitch=1.0, orbit_deg=3 * 360.0)
+    return ScanConfig(
+        name="helix3d_512", geom=g, phantom="anthro3d", i0=1e5, sigma_e=5.0,
+        beta=2.0 ** 14, delta_hu=10.0, potential="hyperbola", M=24, alpha=1.999, n_iter=20, seed=seed,
+    )
+
+
+def helix3d_64(seed: int = 0) -> ScanConfig:
+    """Small helical case the oracle finishes in seconds: 64x64x16 voxels of 2x2x1.25 mm, 96x8 cells,
+    pitch 1, 120 views per turn over 2 turns, M=8."""
+    g = HelicalConeGeometry(nx=64, ny=64, nz=16, dx=2.0, dy=2.0, dz=1.25, ns=96, ds=2.0, nt=8, dt=2.2,
+                            na=240, dso=541.0, dsd=949.0, pitch=1.0, orbit_deg=720.0)
+    return ScanConfig(
+        name="helix3d_64", geom=g, phantom="random3d", i0=1e5, sigma_e=5.0,
+        beta=2.0 ** 14, delta_hu=10.0, potential="hyperbola", M=8, alpha=1.999, n_iter=10, seed=seed,
+    )
+
+
 def config_by_name(name: str, seed: int = 0) -> ScanConfig:
-    return {"fan2d_128": fan2d_128, "fan2d_512": fan2d_512}[name](seed)
+    return {"fan2d_128": fan2d_128, "fan2d_512": fan2d_512, "helix3d_64": helix3d_64,
+            "helix3d_512": helix3d_512}[name](seed)
