@@ -54,7 +54,7 @@ typedef enum {
     CT_ENOTSUP = 5   /* geometry kind or option not supported */
 } ct_status;
 
-enum { CT_FAN_ARC_2D = 1 };
+enum { CT_FAN_ARC_2D = 1, CT_HELICAL_CONE_ARC = 2 };
 
 typedef struct ct_geom ct_geom; /* opaque; owns device geometry tables and workspace */
 

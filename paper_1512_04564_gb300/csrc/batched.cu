@@ -375,6 +375,7 @@ extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms
         const ct_solve_params *p = &params[i];
         if (!g || !y[i] || !w[i] || !x_inout[i]) { set_error("slice %d: null argument", i); return CT_EINVAL; }
         if (g->device != dev) { set_error("slice %d: geometry on device %d, current %d", i, g->device, dev); return CT_EINVAL; }
+        if (g->helical) { set_error("slice %d: batched solves take 2-D fan-beam slices", i); return CT_ENOTSUP; }
         if (p->M < 1 || p->M > g->fan.na || p->n_iter < 1 || p->n_iter > 100000 || !(p->alpha >= 1.0f && p->alpha < 2.0f) ||
             !(p->beta >= 0.0f) || p->potential < CT_POT_HYPERBOLA || p->potential > CT_POT_QUADRATIC ||
             (p->potential != CT_POT_QUADRATIC && !(p->delta > 0.0f)) ||

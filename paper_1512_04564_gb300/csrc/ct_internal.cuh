@@ -56,18 +56,41 @@ struct SolveDev {
     int nonneg;
 };
 
+// Axial part of a helical cone-beam geometry (the transaxial part is a FanDev
+// whose views run over all turns).  Volumes inside the library are stored
+// column-major, [iy][ix][iz] (z fastest); the C ABI's [iz][iy][ix] is
+// transposed on entry and exit.
+struct HelixDev {
+    int nz, nt;
+    float ct0;               // row coordinate of detector height 0: (nt-1)/2 - offset_t = ct0i - ofr
+    float ct0i;              // (nt-1)/2 - round(offset_t): an integer or half-integer, exact in FP32
+    float ofr;               // offset_t - round(offset_t), in [-1/2, 1/2]
+    float kA, inv_kA;        // dz * dsd / dt (rows spanned by one voxel times its source distance), 1 / kA
+    const float2 *view_zb;   // [na]: (z of the volume's lower face - z_src(view)) / dz = zbi + zbf, zbi integer
+    const float *row_c;      // [nt]: 1 / cos(cone angle of row t) = sqrt(1 + (v_t / dsd)^2)
+    const float4 *tile_ax;   // [na][ntiles]: at each anchor tile's centre, voxels per row 1/a = L/kA and
+                             // rows per voxel a = kA/L, each as hi + lo floats (FP64-derived)
+};
+
 }  // namespace ct
 
 // The opaque handle of the C ABI.
 struct ct_geom {
     ct_geom_desc desc;
     ct::FanDev fan;
+    int helical = 0;               // desc.kind == CT_HELICAL_CONE_ARC
+    ct::HelixDev hx{};
+    float2 *d_view_zb = nullptr;   // helical tables
+    float *d_row_c = nullptr;
+    float4 *d_tile_ax = nullptr;
+    float *d_vol_ws = nullptr;     // helical: one column-major volume for the ABI's layout changes
+    int hx_zc = 0;                 // helical: voxels per back-projector thread (chunk along z)
     float4 *d_anchor = nullptr;
     float2 *d_view_cs = nullptr;
     float *d_view_beta = nullptr;
     int *d_views_all = nullptr;   // identity list [0, na)
     int *d_views_stage = nullptr; // caller view lists are staged here [na]
-    float *d_sino_ws = nullptr;   // [na][ns] sinogram workspace (D_L)
+    float *d_sino_ws = nullptr;   // [na][nt][ns] sinogram workspace (D_L; nt = 1 in 2-D)
     // solver workspace (allocated at the first solve)
     size_t solve_bytes = 0;
     void *d_solve = nullptr;
@@ -320,6 +343,32 @@ cudaError_t launch_fbp(const ct_geom *g, const float *y, float *x, int window, c
 ct_status validate_fbp(const ct_geom *g, int window);
 
 ct_status validate_views(const ct_geom *g, const int *views, int nviews);
+
+// helical cone-beam (helical.cu); volumes column-major [iy][ix][iz]
+cudaError_t launch_fp_helix(const ct_geom *g, int mode, const float *x, const int *views, int nviews, float *out,
+                            const float *y, const float *w, cudaStream_t st);
+cudaError_t launch_bp_helix(const ct_geom *g, int mode, const float *sino, const int *views, int nviews, float *x,
+                            float scale, int accumulate, const SolveDev *S, cudaStream_t st);
+cudaError_t launch_reg_gradient_helix(const ct_geom *g, const float *x, float beta, float delta, int potential,
+                                      float *grad, float *curv, cudaStream_t st);
+cudaError_t launch_reg_update_helix(const ct_geom *g, const SolveDev &S, float beta, float delta, int potential,
+                                    cudaStream_t st);
+cudaError_t launch_rmsd_helix(const ct_geom *g, const float *x, const float *xr, float r2max, double *partial,
+                              int *counter, float *trace, int M, float hu, cudaStream_t st);
+int helix_chunk_voxels(double a_max);  // largest chunk whose magnified extent fits the row buffer, 0 if none
+int helix_max_rows();
+int helix_max_span();
+int helix_max_march();
+// [iz][iy][ix] -> column-major, and back (dst = scale * src (+ dst if accumulate))
+cudaError_t launch_to_columns(const ct_geom *g, const float *src, float *dst, cudaStream_t st);
+cudaError_t launch_to_slices(const ct_geom *g, const float *src, float *dst, float scale, int accumulate,
+                             cudaStream_t st);
+ct_status helix_forward(const ct_geom *g, const float *x, float *y, const int *views, int nviews, cudaStream_t st);
+ct_status helix_back(const ct_geom *g, const float *y, float *x, const int *views, int nviews, float scale,
+                     int accumulate, cudaStream_t st);
+ct_status helix_sqs_diag(const ct_geom *g, const float *w, float *d_l, cudaStream_t st);
+ct_status helix_reg_gradient(const ct_geom *g, const float *x, float beta, float delta, int potential, float *grad,
+                             float *curv, cudaStream_t st);
 ct_status stage_views(const ct_geom *g, const int *views, int nviews, const int **dev_views, cudaStream_t st);
 
 // ---------------------------------------------------------------- regularizer (Eq. (def_reg))

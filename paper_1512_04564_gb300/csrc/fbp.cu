@@ -108,6 +108,10 @@ ct_status validate_fbp(const ct_geom *g, int window)
         set_error("unknown FBP window %d", window);
         return CT_EINVAL;
     }
+    if (g->helical) {
+        set_error("FBP is implemented for 2-D fan-beam scans only");
+        return CT_ENOTSUP;
+    }
     if (std::fabs(g->desc.orbit_deg - 360.0) > 1e-9) {
         set_error("FBP needs a full 360-degree scan (orbit %g)", g->desc.orbit_deg);
         return CT_ENOTSUP;

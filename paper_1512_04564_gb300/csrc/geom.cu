@@ -82,6 +82,10 @@ static void free_geom(ct_geom *g)
     cudaFree(g->d_row_ent);
     cudaFree(g->d_foot_t);
     cudaFree(g->d_foot_an);
+    cudaFree(g->d_view_zb);
+    cudaFree(g->d_row_c);
+    cudaFree(g->d_tile_ax);
+    cudaFree(g->d_vol_ws);
     delete g;
 }
 
@@ -89,9 +93,23 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
 {
     if (!d || !out) { set_error("ct_geom_create: null argument"); return CT_EINVAL; }
     *out = nullptr;
-    if (d->kind != CT_FAN_ARC_2D) {
-        set_error("geometry kind %d is not supported (CT_FAN_ARC_2D=%d)", d->kind, CT_FAN_ARC_2D);
+    const bool helical = d->kind == CT_HELICAL_CONE_ARC;
+    if (d->kind != CT_FAN_ARC_2D && !helical) {
+        set_error("geometry kind %d is not supported (CT_FAN_ARC_2D=%d, CT_HELICAL_CONE_ARC=%d)", d->kind,
+                  CT_FAN_ARC_2D, CT_HELICAL_CONE_ARC);
         return CT_ENOTSUP;
+    }
+    if (helical) {
+        if (d->nz < 1 || d->nt < 1 || d->nz > 4096 || !(d->dz > 0) || !(d->dt > 0) || !std::isfinite(d->pitch) ||
+            !std::isfinite(d->offset_z) || !std::isfinite(d->offset_t)) {
+            set_error("bad helical sizes nz=%d nt=%d or lengths", d->nz, d->nt);
+            return CT_EINVAL;
+        }
+        if (d->nt > helix_max_rows() || d->nx > helix_max_march() || d->ny > helix_max_march()) {
+            set_error("helical scans support up to %d detector rows and %d pixels per side", helix_max_rows(),
+                      helix_max_march());
+            return CT_ENOTSUP;
+        }
     }
     if (d->nx < 1 || d->ny < 1 || d->ns < 1 || d->na < 1 || d->nx > 65536 || d->ny > 65536 || d->ns > (1 << 20) ||
         d->na > (1 << 20)) {
@@ -128,8 +146,26 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         return CT_EINVAL;
     }
 
+    // helical: widest axial shadow of one voxel, in rows (closest column to the source)
+    int zc = 0;
+    if (helical) {
+        const int span = (int)std::ceil(std::sqrt(d->dx * d->dx + d->dy * d->dy) / ((d->dso - r_img) * dg)) + 2;
+        if (span > helix_max_span()) {
+            set_error("detector cells too fine for the voxels: a column's footprint spans %d cells (max %d)", span,
+                      helix_max_span());
+            return CT_ENOTSUP;
+        }
+        zc = helix_chunk_voxels(d->dz * d->dsd / d->dt / (d->dso - r_img));
+        if (zc == 0) {
+            set_error("voxels too tall for the detector rows: one voxel's shadow exceeds the row buffer");
+            return CT_ENOTSUP;
+        }
+    }
+
     ct_geom *g = new ct_geom();
     g->desc = *d;
+    g->helical = helical ? 1 : 0;
+    g->hx_zc = zc;
     cudaGetDevice(&g->device);
     FanDev &F = g->fan;
     F.nx = d->nx; F.ny = d->ny; F.ns = d->ns; F.na = d->na;
@@ -181,7 +217,8 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     if (e == cudaSuccess) e = cudaMalloc(&g->d_view_beta, sizeof(float) * na);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_views_all, sizeof(int) * na);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_views_stage, sizeof(int) * na);
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_sino_ws, sizeof(float) * (size_t)na * d->ns);
+    const size_t rows = helical ? (size_t)d->nt : 1;
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_sino_ws, sizeof(float) * (size_t)na * d->ns * rows);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_anchor, anc.data(), sizeof(float4) * anc.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_view_cs, cs.data(), sizeof(float2) * na, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_view_beta, bet.data(), sizeof(float) * na, cudaMemcpyHostToDevice);
@@ -190,6 +227,64 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         ct_status st = cuda_fail(e, "ct_geom_create");
         free_geom(g);
         return st;
+    }
+    if (e == cudaSuccess && helical) {
+        // axial tables (FP64 on the host): per view, the volume's lower face relative to the source
+        // height in voxel units (hi + lo floats); per row, 1/cos of its cone angle
+        std::vector<float2> zbv(na);
+        std::vector<float> rc(d->nt);
+        std::vector<float4> tax((size_t)na * ntiles);
+        const double face0 = (-d->nz / 2.0 + d->offset_z) * d->dz;
+        const double mid = (d->orbit_start_deg + 0.5 * d->orbit_deg) * M_PI / 180.0;
+        const double cover = d->nt * d->dt * d->dso / d->dsd;
+        const double kA = d->dz * d->dsd / d->dt;
+        for (int v = 0; v < na; v++) {
+            const double b = (d->orbit_start_deg + (double)v * d->orbit_deg / na) * M_PI / 180.0;
+            const double zsrc = d->pitch * cover * (b - mid) / (2.0 * M_PI);
+            const double zb = (face0 - zsrc) / d->dz;
+            const double zbi = std::nearbyint(zb);
+            zbv[v] = make_float2((float)zbi, (float)(zb - zbi));
+            const double cb = std::cos(b), sb = std::sin(b);
+            for (int ty = 0; ty < F.nty; ty++)
+                for (int tx = 0; tx < F.ntx; tx++) {
+                    const double X = (tx * kTile + (double)kTileHalf - cxo) * d->dx;
+                    const double Y = (ty * kTile + (double)kTileHalf - cyo) * d->dy;
+                    const double tpar = d->dso + X * cb + Y * sb, tperp = -X * sb + Y * cb;
+                    const double L = std::sqrt(tpar * tpar + tperp * tperp);
+                    const double ia = L / kA, a = kA / L;
+                    const float iah = (float)ia, ah = (float)a;
+                    tax[(size_t)v * ntiles + ty * F.ntx + tx] =
+                        make_float4(iah, (float)(ia - (double)iah), ah, (float)(a - (double)ah));
+                }
+        }
+        for (int t = 0; t < d->nt; t++) {
+            const double vt = (t - (d->nt - 1) / 2.0 + d->offset_t) * d->dt;
+            rc[t] = (float)std::sqrt(1.0 + (vt / d->dsd) * (vt / d->dsd));
+        }
+        e = cudaMalloc(&g->d_view_zb, sizeof(float2) * na);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_row_c, sizeof(float) * d->nt);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_vol_ws, sizeof(float) * (size_t)d->nx * d->ny * d->nz);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_tile_ax, sizeof(float4) * tax.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g->d_tile_ax, tax.data(), sizeof(float4) * tax.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_view_zb, zbv.data(), sizeof(float2) * na, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_row_c, rc.data(), sizeof(float) * d->nt, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            ct_status st = cuda_fail(e, "ct_geom_create (helical tables)");
+            free_geom(g);
+            return st;
+        }
+        g->hx.nz = d->nz;
+        g->hx.nt = d->nt;
+        const double ofr = d->offset_t - std::nearbyint(d->offset_t);
+        g->hx.ct0 = (float)((d->nt - 1) / 2.0 - d->offset_t);
+        g->hx.ct0i = (float)((d->nt - 1) / 2.0 - std::nearbyint(d->offset_t));
+        g->hx.ofr = (float)ofr;
+        g->hx.kA = (float)kA;
+        g->hx.inv_kA = (float)(1.0 / kA);
+        g->hx.view_zb = g->d_view_zb;
+        g->hx.row_c = g->d_row_c;
+        g->hx.tile_ax = g->d_tile_ax;
     }
     F.anchor = g->d_anchor;
     F.view_cs = g->d_view_cs;

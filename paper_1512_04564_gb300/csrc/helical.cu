@@ -1,0 +1,810 @@
+// Helical cone-beam CT (3-D) on sm_103a: the separable-footprint projector
+// pair with a trapezoid transaxial and a rectangle axial footprint (SF-TR),
+// the 26-neighbour regularizer (Eq. (def_reg), 13 directions) with the fused
+// x-update of Algorithm 1/2, the RMSD reduction, and the changes between the
+// C ABI's [iz][iy][ix] volumes and the column-major [iy][ix][iz] volumes the
+// kernels use (a voxel column is contiguous, so the forward projector reads a
+// column's z-range as one run and the back-projector writes its chunk as one).
+//
+//   a_{(v,t,s),j} = l_xy(j) * c_t * T_j(s) * R_j(t)
+//
+//   T_j(s): cell integral of the column's transaxial trapezoid (sf_footprint,
+//           with the per-(view, 16x16 tile) FP64-derived anchors of the 2-D path);
+//   l_xy:   the column's transaxial chord (the footprint amplitude);
+//   R_j(t): overlap, in rows, of row t with the voxel's z-extent magnified by
+//           dsd / L (L: transaxial source-to-column distance); voxel boundary k
+//           falls at row coordinate u_k = a (k + zb_v) + ct0, a = dz dsd / (dt L);
+//   c_t:    1 / cos(cone angle of row t).
+//
+// Forward projector (ray-driven, cell-owned outputs, no atomics): one CTA per
+// (view, 32 adjacent cells); its warps split the image columns of the
+// bundle's transaxial fan wedge.  Per round a warp stages 32 columns, one per
+// lane: the lane evaluates the column's footprint once (cell weights) and its
+// axial profile p_t = sum_k x_k R_k(t) over all rows; then each lane, as the
+// owner of one cell, adds weight x profile for every staged column its own
+// wedge crosses, for all rows at once.  Partial sums of the warps are added in
+// a fixed order.
+//
+// Back-projector (voxel-driven, no atomics): one thread per (column, chunk of
+// ZC voxels); per view it evaluates the column's footprint, forms the row
+// sums q_t = c_t sum_s w_s y[t][s] over the rows its chunk reaches, and
+// integrates them over each voxel's magnified extent through their running
+// sum.  Fused epilogues as in 2-D (plain, and the g/h updates of Algorithm 1/2).
+#include <cmath>
+
+#include "ct_internal.cuh"
+
+namespace ct {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kHxWarps = 4;         // warps per forward-projector CTA
+constexpr int kHxMaxSpan = 12;      // cells per staged transaxial footprint
+constexpr int kHxMaxMarch = 2048;   // longest march axis of a wedge
+constexpr int kHxBpCols = 128;      // back-projector CTA: 16 x 8 columns
+constexpr int kHxQMax = 64;         // rows one back-projector chunk may reach
+constexpr int kHxMaxRows = 64;      // detector rows supported
+
+// Marching frame of a bundle wedge: "march" is the axis walked along (x for
+// shallow bundles, y for steep ones), "cross" the other.
+struct March {
+    float m_edge0, m_d;
+    float c_edge0, c_invd;
+    float Sm, Sc;
+    int n_march, n_cross;
+    bool col;
+};
+
+// Cross-axis column range [lo, hi] of the wedge between the lines of slopes T1,
+// T2 (cross = Sc + (march - Sm) T) inside the march slab of index a.
+__device__ __forceinline__ void wedge_range(const March &M, int a, float T1, float T2, int &lo, int &hi)
+{
+    const float ml = fmaf((float)a, M.m_d, M.m_edge0) - M.Sm, mr = ml + M.m_d;
+    const float c1 = fmaf(ml, T1, M.Sc), c2 = fmaf(mr, T1, M.Sc);
+    const float c3 = fmaf(ml, T2, M.Sc), c4 = fmaf(mr, T2, M.Sc);
+    const float clo = (fminf(fminf(c1, c2), fminf(c3, c4)) - M.c_edge0) * M.c_invd - kRangePad;
+    const float chi = (fmaxf(fmaxf(c1, c2), fmaxf(c3, c4)) - M.c_edge0) * M.c_invd + kRangePad;
+    lo = max(0, (int)floorf(fmaxf(clo, -1.0f)));
+    hi = min(M.n_cross - 1, (int)floorf(fminf(chi, (float)M.n_cross)));
+}
+
+__device__ __forceinline__ float march_slope(const March &M, float ang)
+{
+    float sn, cn;
+    sincosf(ang, &sn, &cn);
+    return M.col ? sn / cn : cn / sn;
+}
+
+// Number of entries of the warp-wide nondecreasing array `incl` that are <= key.
+__device__ __forceinline__ int count_le(int incl, int key)
+{
+    int pos = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const int v = __shfl_sync(kFull, incl, pos + step - 1);
+        if (v <= key) pos += step;
+    }
+    return pos;
+}
+
+// Axial scale of column (ix, iy) in one view: voxels per row ia = L/kA and rows
+// per voxel a = kA/L, L the transaxial source-to-column distance, each as hi +
+// lo floats.  L = L_A + (L - L_A) with L_A the tile centre's FP64-derived
+// distance and L - L_A = (2 A.d + |d|^2) / (L + L_A) (A: anchor vector, d:
+// column offset), which is small and so accurate in FP32; the rounding of A
+// cancels between |A + d| and |A| to first order.
+struct ColumnAxial {
+    float ia_hi, ia_lo, a_hi, a_lo;
+};
+
+__device__ __forceinline__ ColumnAxial column_axial(const HelixDev &H, float4 A, float4 X, float cb, float sb,
+                                                    float ox, float oy)
+{
+    const float dpar = fmaf(ox, cb, oy * sb), dperp = fmaf(oy, cb, -ox * sb);
+    const float cpar = A.x + dpar, cperp = A.y + dperp;
+    const float L = sqrtf(fmaf(cpar, cpar, cperp * cperp));
+    const float LA = X.x * H.kA;
+    const float num = fmaf(2.0f, fmaf(A.x, dpar, A.y * dperp), fmaf(dpar, dpar, dperp * dperp));
+    const float dL = __fdividef(num, L + LA);
+    ColumnAxial C;
+    C.ia_hi = X.x;
+    C.ia_lo = fmaf(dL, H.inv_kA, X.y);
+    C.a_hi = X.z;
+    C.a_lo = fmaf(-X.z, __fdividef(dL, L), X.w);
+    return C;
+}
+
+// Detector-row boundary b (row coordinate b - 1/2) of a column, in voxel
+// coordinates z = K + f (voxel K spans [K, K+1], 0 <= f < 1):
+//   z = (b - 1/2 - ct0i + ofr) ia - zbi - zbf.
+// The integer parts are exact, so f is formed by one fma at magnitude ~1 and
+// resolves the boundary to ~1e-7 voxel (a thin sliver of a voxel keeps its
+// relative accuracy).  cz = ofr * ia - zbf.
+__device__ __forceinline__ void row_boundary(float b_minus_c, float ia_hi, float ia_lo, float zbi, float cz, int nz,
+                                             int &K, float &f)
+{
+    const float sm = fmaf(b_minus_c, ia_lo, cz);
+    const float approx = fmaf(b_minus_c, ia_hi, sm - zbi);
+    K = (int)floorf(fminf(fmaxf(approx, -2.0f), (float)nz + 1.0f));
+    f = fmaf(b_minus_c, ia_hi, -(zbi + (float)K)) + sm;
+    if (f < 0.0f) { K -= 1; f += 1.0f; }
+    else if (f >= 1.0f) { K += 1; f -= 1.0f; }
+}
+
+template <int MODE, int NT>
+__global__ void __launch_bounds__(kHxWarps * 32) fp_helix_kernel(FanDev G, HelixDev H, const float *__restrict__ x,
+                                                                const int *__restrict__ views, int nviews,
+                                                                float *__restrict__ out, const float *__restrict__ y,
+                                                                const float *__restrict__ w)
+{
+    constexpr int PS = NT + 4;  // stride of a staged axial profile (floats; float4-aligned)
+    __shared__ int s_pre[kHxMaxMarch + 1];
+    __shared__ int s_lo[kHxMaxMarch];
+    __shared__ float s_w[kHxWarps][32][kHxMaxSpan + 1];
+    __shared__ int s_c[kHxWarps][32];
+    __shared__ int s_n[kHxWarps][32];
+    __shared__ int s_part[kHxWarps];
+    __shared__ float s_rc[NT];
+    extern __shared__ float4 s_dyn4[];
+    float *s_p = reinterpret_cast<float *>(s_dyn4);  // [warp][32][PS] profiles; later [warp][NT][32] partial sums
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = (G.ns + 31) >> 5;
+    const int k = blockIdx.x / nb;
+    const int s0 = (blockIdx.x - k * nb) * 32;
+    const int v = __ldg(&views[k]);
+    const float2 cs = __ldg(&G.view_cs[v]);
+    const float beta = __ldg(&G.view_beta[v]);
+    const float2 zb = __ldg(&H.view_zb[v]);
+    if (threadIdx.x < NT) s_rc[threadIdx.x] = threadIdx.x < H.nt ? __ldg(&H.row_c[threadIdx.x]) : 0.0f;
+    const int s_last = min(s0 + 31, G.ns - 1);
+    const float a_lo = beta + fmaf((float)s0 - 0.5f, G.dgamma, G.gamma0);
+    const float a_hi = beta + fmaf((float)s_last + 0.5f, G.dgamma, G.gamma0);
+    float sn, cn;
+    sincosf(0.5f * (a_lo + a_hi), &sn, &cn);
+    March M;
+    M.col = fabsf(cn) >= fabsf(sn);
+    const float Sx = -G.dso * cs.x, Sy = -G.dso * cs.y;
+    if (M.col) {
+        M.m_edge0 = G.x_edge0; M.m_d = G.dx; M.c_edge0 = G.y_edge0; M.c_invd = G.inv_dy;
+        M.Sm = Sx; M.Sc = Sy; M.n_march = G.nx; M.n_cross = G.ny;
+    } else {
+        M.m_edge0 = G.y_edge0; M.m_d = G.dy; M.c_edge0 = G.x_edge0; M.c_invd = G.inv_dx;
+        M.Sm = Sy; M.Sc = Sx; M.n_march = G.ny; M.n_cross = G.nx;
+    }
+    const int nm = M.n_march;
+    {   // wedge columns per march index, then an exclusive scan over the CTA
+        const float TB1 = march_slope(M, a_lo), TB2 = march_slope(M, a_hi);
+        const int per = (nm + kHxWarps * 32 - 1) / (kHxWarps * 32);
+        const int a0 = threadIdx.x * per;
+        int run = 0;
+        for (int i = 0; i < per; i++) {
+            const int a = a0 + i;
+            if (a < nm) {
+                int lo, hi;
+                wedge_range(M, a, TB1, TB2, lo, hi);
+                s_lo[a] = lo;
+                const int c = max(hi - lo + 1, 0);
+                s_pre[a] = c;
+                run += c;
+            }
+        }
+        int incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_part[warp] = incl;
+        __syncthreads();
+        int base = 0;
+        for (int q = 0; q < warp; q++) base += s_part[q];
+        int pos = base + incl - run;
+        for (int i = 0; i < per; i++) {
+            const int a = a0 + i;
+            if (a < nm) {
+                const int c = s_pre[a];
+                s_pre[a] = pos;
+                pos += c;
+            }
+        }
+        if (threadIdx.x == kHxWarps * 32 - 1) s_pre[nm] = pos;
+        __syncthreads();
+    }
+    const int T = s_pre[nm];
+    const int s_mine = s0 + lane;
+    const float my_a = beta + fmaf((float)s_mine, G.dgamma, G.gamma0);
+    const float t1 = march_slope(M, my_a - 0.5f * G.dgamma), t2 = march_slope(M, my_a + 0.5f * G.dgamma);
+    float(*sw)[kHxMaxSpan + 1] = s_w[warp];
+    int *scf = s_c[warp];
+    int *sns = s_n[warp];
+    float *sp = s_p + (size_t)warp * 32 * PS;
+    const int nt = H.nt, nz = H.nz;
+    float acc[NT];
+#pragma unroll
+    for (int t = 0; t < NT; t++) acc[t] = 0.0f;
+    const int t_end = (int)(((long)(warp + 1) * T) / kHxWarps);
+    int t0 = (int)(((long)warp * T) / kHxWarps);
+    int col = 0;
+    while (t0 < t_end) {
+        while (s_pre[col + 1] <= t0) col++;
+        const int e = s_pre[min(col + lane + 1, nm)];
+        const int n = min(min(32, t_end - t0), __shfl_sync(kFull, e, 31) - t0);
+        const int t = t0 + lane;
+        const int ls = min(count_le(e, t), 31);
+        const int c = col + ls;
+        int cf = 1 << 20, cnt = 0;
+        if (lane < n) {  // column role: footprint weights and axial profile of one column
+            const int bc = s_lo[c] + (t - s_pre[c]);
+            const int ix = M.col ? c : bc, iy = M.col ? bc : c;
+            const int tx = ix / kTile, ty = iy / kTile;
+            const float4 A = __ldg(&G.anchor[(size_t)v * (G.ntx * G.nty) + ty * G.ntx + tx]);
+            const float ox = ((float)(ix - tx * kTile) - kTileHalf) * G.dx;
+            const float oy = ((float)(iy - ty * kTile) - kTileHalf) * G.dy;
+            const Footprint F = sf_footprint(G, cs.x, cs.y, A, ox, oy);
+            const int j0 = (int)floorf(F.t0 - 0.5f) + 1;
+            cnt = max(min((int)ceilf(F.t3 + 0.5f) - j0, kHxMaxSpan), 0);
+            float Fp = trap_cdf(F, (float)j0 - 0.5f);
+            for (int i = 0; i < cnt; i++) {
+                const float Fn = trap_cdf(F, (float)(j0 + i) + 0.5f);
+                sw[lane][i] = (Fn - Fp) * F.amp;
+                Fp = Fn;
+            }
+            cf = F.n + j0 - s0;
+            // axial profile: row r covers voxel coordinates between its two boundaries
+            const float4 X = __ldg(&H.tile_ax[(size_t)v * (G.ntx * G.nty) + ty * G.ntx + tx]);
+            const ColumnAxial C = column_axial(H, A, X, cs.x, cs.y, ox, oy);
+            const float a = C.a_hi + C.a_lo;
+            const float cz = fmaf(H.ofr, C.ia_hi + C.ia_lo, -zb.y);
+            const float *xc = (MODE == FP_ONES_W) ? x : x + ((size_t)iy * G.nx + ix) * nz;
+            int Kl;
+            float fl;
+            row_boundary(-0.5f - H.ct0i, C.ia_hi, C.ia_lo, zb.x, cz, nz, Kl, fl);
+            float *pl = sp + lane * PS;
+#pragma unroll 2
+            for (int r = 0; r < NT; r++) {
+                if (r < nt) {
+                    int Kh;
+                    float fh;
+                    row_boundary((float)r + 0.5f - H.ct0i, C.ia_hi, C.ia_lo, zb.x, cz, nz, Kh, fh);
+                    float sacc = 0.0f;
+                    if (Kh >= 0 && Kl < nz) {
+                        const int k0 = Kl < 0 ? 0 : Kl, k1 = Kh >= nz ? nz - 1 : Kh;
+                        const float f0 = Kl < 0 ? 0.0f : fl, f1 = Kh >= nz ? 1.0f : fh;
+                        if (MODE == FP_ONES_W) {
+                            sacc = (float)(k1 - k0) + (f1 - f0);
+                        } else if (k0 == k1) {
+                            sacc = __ldg(&xc[k0]) * (f1 - f0);
+                        } else {
+                            sacc = __ldg(&xc[k0]) * (1.0f - f0);
+                            for (int kk = k0 + 1; kk < k1; kk++) sacc += __ldg(&xc[kk]);
+                            sacc = fmaf(__ldg(&xc[k1]), f1, sacc);
+                        }
+                    }
+                    pl[r] = a * sacc;
+                    Kl = Kh;
+                    fl = fh;
+                } else {
+                    pl[r] = 0.0f;
+                }
+            }
+        }
+        scf[lane] = cf;
+        sns[lane] = cnt;
+        __syncwarp();
+        // cell role: add weight x profile of every staged column this lane's wedge crosses
+        const int lmax = __shfl_sync(kFull, ls, n - 1);
+        for (int l = 0; l <= lmax; l++) {
+            const int cc = col + l;
+            const int pre_c = s_pre[cc];
+            const int task_lo = max(pre_c, t0), task_hi = min(__shfl_sync(kFull, e, l), t0 + n);
+            const int row0 = s_lo[cc] - pre_c;
+            int q_lo, q_hi;
+            wedge_range(M, cc, t1, t2, q_lo, q_hi);
+            q_lo = max(q_lo, row0 + task_lo);
+            q_hi = min(q_hi, row0 + task_hi - 1);
+            for (int q = q_lo; q <= q_hi; q++) {
+                const int slot = q - row0 - t0;
+                const int i = lane - scf[slot];
+                if ((unsigned)i < (unsigned)sns[slot]) {
+                    const float wt = sw[slot][i];
+                    const float4 *p4 = reinterpret_cast<const float4 *>(sp + slot * PS);
+#pragma unroll
+                    for (int r4 = 0; r4 < NT / 4; r4++) {
+                        const float4 p = p4[r4];
+                        acc[4 * r4 + 0] = fmaf(wt, p.x, acc[4 * r4 + 0]);
+                        acc[4 * r4 + 1] = fmaf(wt, p.y, acc[4 * r4 + 1]);
+                        acc[4 * r4 + 2] = fmaf(wt, p.z, acc[4 * r4 + 2]);
+                        acc[4 * r4 + 3] = fmaf(wt, p.w, acc[4 * r4 + 3]);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        t0 += n;
+    }
+    // warps' partial sums, added in a fixed order
+    __syncthreads();
+    float *red = s_p;  // [warp][NT][32]
+#pragma unroll
+    for (int r = 0; r < NT; r++) red[(warp * NT + r) * 32 + lane] = acc[r];
+    __syncthreads();
+    for (int q = threadIdx.x; q < NT * 32; q += kHxWarps * 32) {
+        const int r = q >> 5, l = q & 31, s = s0 + l;
+        if (r >= nt || s >= G.ns) continue;
+        float sum = 0.0f;
+#pragma unroll
+        for (int wq = 0; wq < kHxWarps; wq++) sum += red[(wq * NT + r) * 32 + l];
+        sum *= s_rc[r];
+        const size_t ri = ((size_t)v * nt + r) * G.ns + s;
+        const size_t oi = ((size_t)k * nt + r) * G.ns + s;
+        if (MODE == FP_PLAIN) out[oi] = sum;
+        else if (MODE == FP_RESID) out[oi] = __ldg(&w[ri]) * (sum - __ldg(&y[ri]));
+        else out[ri] = __ldg(&w[ri]) * sum;
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void bp_helix_epilogue(const SolveDev &S, float *__restrict__ xo, size_t j, float acc,
+                                                  float rho, float scale, int accumulate)
+{
+    if (MODE == BP_PLAIN) {
+        xo[j] = accumulate ? fmaf(scale, acc, xo[j]) : scale * acc;
+        return;
+    }
+    const float zeta = S.M_scale * acc;  // M grad L_m
+    if (MODE == BP_SOLVE_INIT) {
+        S.g[j] = zeta;
+        S.h[j] = (S.algorithm == CT_ALG_PROPOSED) ? fmaf(S.d_l[j], S.x[j], -zeta) : zeta;
+    } else {
+        const float g = S.g[j];
+        const float xp = S.x_new[j];
+        const float a = S.alpha;
+        const float ir = 1.0f / (rho + 1.0f);
+        S.g[j] = fmaf(rho * ir, fmaf(a, zeta, (1.0f - a) * g), g * ir);
+        if (S.algorithm == CT_ALG_PROPOSED)
+            S.h[j] = fmaf(a, fmaf(S.d_l[j], xp, -zeta), (1.0f - a) * S.h[j]);
+        else
+            S.h[j] = zeta;
+        S.x[j] = xp;
+    }
+}
+
+// Running sum of the row sums at voxel boundary k of a column, over rows
+// [t_lo, t_lo + nr): qb[i] = sum of q over the first i rows, linear inside a
+// row.  The boundary's row coordinate is u + 1/2 = (k + zbi)(a_hi + a_lo) +
+// zbf a + ct0i + 1/2 - ofr = r + fr (row r, 0 <= fr < 1); with k + zbi and
+// ct0i + 1/2 - r exact, fr comes from one fma at magnitude ~1.  cb0 = zbf a - ofr.
+__device__ __forceinline__ float row_cdf(const float *qb, int k, float zbi, float a_hi, float a_lo, float cb0,
+                                         float c_half, int t_lo, int nr, int nt)
+{
+    const float Z = (float)k + zbi;
+    const float sm = fmaf(Z, a_lo, cb0);
+    const float approx = fmaf(Z, a_hi, sm + c_half);
+    int r = (int)floorf(fminf(fmaxf(approx, -2.0f), (float)nt + 1.0f));
+    float fr = fmaf(Z, a_hi, c_half - (float)r) + sm;
+    if (fr < 0.0f) { r -= 1; fr += 1.0f; }
+    else if (fr >= 1.0f) { r += 1; fr -= 1.0f; }
+    const int rel = r - t_lo;
+    if (rel < 0) return 0.0f;
+    if (rel >= nr) return qb[nr * kHxBpCols];
+    const float lo = qb[rel * kHxBpCols], hi = qb[(rel + 1) * kHxBpCols];
+    return fmaf(fr, hi - lo, lo);
+}
+
+template <int MODE, int ZC>
+__global__ void __launch_bounds__(kHxBpCols) bp_helix_kernel(FanDev G, HelixDev H, const float *__restrict__ sino,
+                                                             const int *__restrict__ views, int nviews,
+                                                             float *__restrict__ xo, float scale, int accumulate,
+                                                             SolveDev S)
+{
+    __shared__ float s_qb[(kHxQMax + 1) * kHxBpCols];
+    __shared__ float s_w[kHxMaxSpan * kHxBpCols];
+    __shared__ float s_rc[kHxMaxRows];
+    const int tid = threadIdx.x;
+    const int ix = blockIdx.x * 16 + (tid & 15), iy = blockIdx.y * 8 + (tid >> 4);
+    const int z0 = blockIdx.z * ZC;
+    if (tid < kHxMaxRows) s_rc[tid] = tid < H.nt ? __ldg(&H.row_c[tid]) : 0.0f;
+    __syncthreads();
+    const bool inside = ix < G.nx && iy < G.ny;
+    const int tx = min(ix, G.nx - 1) / kTile, ty = min(iy, G.ny - 1) / kTile;
+    const int tile = ty * G.ntx + tx;
+    const int ntiles = G.ntx * G.nty;
+    const float ox = ((float)(ix - tx * kTile) - kTileHalf) * G.dx;
+    const float oy = ((float)(iy - ty * kTile) - kTileHalf) * G.dy;
+    float *qb = s_qb + tid;
+    float *wq = s_w + tid;
+    float rho = 1.0f;
+    if (MODE == BP_SOLVE_UPDATE) rho = __ldcg(&S.rho_tab[__ldcg(&S.counter[0])]);
+    float acc[ZC];
+#pragma unroll
+    for (int i = 0; i < ZC; i++) acc[i] = 0.0f;
+    const int nt = H.nt;
+    if (inside) {
+        for (int k = 0; k < nviews; k++) {
+            const int v = __ldg(&views[k]);
+            const float2 cs = __ldg(&G.view_cs[v]);
+            const float4 A = __ldg(&G.anchor[(size_t)v * ntiles + tile]);
+            const float2 zb = __ldg(&H.view_zb[v]);
+            const ColumnAxial Cx = column_axial(H, A, __ldg(&H.tile_ax[(size_t)v * ntiles + tile]), cs.x, cs.y, ox, oy);
+            const float a = Cx.a_hi + Cx.a_lo;
+            // rows the chunk's shadow reaches (approximate ends, widened by 1e-3 row)
+            const float uA = fmaf(a, (float)z0 + zb.x + zb.y, H.ct0);
+            const float uB = fmaf(a, (float)ZC, uA);
+            const int t_lo = (int)fmaxf(floorf(uA + 0.499f), 0.0f);
+            const int t_hi = (int)fminf(floorf(uB + 0.501f), (float)(nt - 1));
+            if (t_lo > t_hi) continue;  // the chunk's shadow misses the detector in this view
+            const Footprint F = sf_footprint(G, cs.x, cs.y, A, ox, oy);
+            const int j0 = (int)floorf(F.t0 - 0.5f) + 1;
+            const int cnt = max(min((int)ceilf(F.t3 + 0.5f) - j0, kHxMaxSpan), 0);
+            const int sfirst = F.n + j0;
+            float Fp = trap_cdf(F, (float)j0 - 0.5f);
+            for (int i = 0; i < cnt; i++) {
+                const float Fn = trap_cdf(F, (float)(j0 + i) + 0.5f);
+                const int s = sfirst + i;
+                wq[i * kHxBpCols] = ((unsigned)s < (unsigned)G.ns) ? (Fn - Fp) * F.amp : 0.0f;
+                Fp = Fn;
+            }
+            const int i0 = max(-sfirst, 0);
+            const int i1 = min(cnt, G.ns - sfirst);
+            // running sums of q_t = c_t sum_s w_s y[t][s] over rows t_lo..t_hi
+            float Q = 0.0f;
+            qb[0] = 0.0f;
+            for (int t = t_lo; t <= t_hi; t++) {
+                const float *row = sino + ((size_t)k * nt + t) * G.ns;
+                float d = 0.0f;
+                for (int i = i0; i < i1; i++) d = fmaf(wq[i * kHxBpCols], __ldg(&row[sfirst + i]), d);
+                Q = fmaf(s_rc[t], d, Q);
+                qb[(t - t_lo + 1) * kHxBpCols] = Q;
+            }
+            const int nr = t_hi - t_lo + 1;
+            const float cb0 = fmaf(zb.y, a, -H.ofr);
+            const float c_half = H.ct0i + 0.5f;
+            float Cp = row_cdf(qb, z0, zb.x, Cx.a_hi, Cx.a_lo, cb0, c_half, t_lo, nr, nt);
+#pragma unroll
+            for (int i = 0; i < ZC; i++) {
+                const float C = row_cdf(qb, z0 + i + 1, zb.x, Cx.a_hi, Cx.a_lo, cb0, c_half, t_lo, nr, nt);
+                acc[i] += C - Cp;
+                Cp = C;
+            }
+        }
+        const size_t jc = ((size_t)iy * G.nx + ix) * H.nz;
+#pragma unroll
+        for (int i = 0; i < ZC; i++)
+            if (z0 + i < H.nz) bp_helix_epilogue<MODE>(S, xo, jc + z0 + i, acc[i], rho, scale, accumulate);
+    }
+    if (MODE == BP_SOLVE_UPDATE) {
+        // the last block to finish advances the subiteration counter (rho for the next one)
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            const int done = atomicAdd(&S.counter[1], 1);
+            if (done == (int)(gridDim.x * gridDim.y * gridDim.z) - 1) {
+                S.counter[1] = 0;
+                S.counter[0] += 1;
+                __threadfence();
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- regularizer (13 directions, 26 neighbours)
+
+struct VolDims {
+    int nx, ny, nz;
+    long long sx, sy, sz;  // element strides along x, y, z
+};
+
+// grad R_j = sum over the 26 neighbours n of beta/||s|| phi'(x_j - x_n);
+// D_R,j = sum 2 beta/||s|| omega(x_j - x_n) (pairs outside the volume absent).
+__device__ __forceinline__ void reg_terms3(const float *__restrict__ x, const VolDims &D, int ix, int iy, int iz,
+                                           long long j, float beta, Pot P, float &grad, float &curv)
+{
+    const float xj = __ldg(&x[j]);
+    const float b1 = beta, b2 = beta * 0.70710678118654752f, b3 = beta * 0.57735026918962576f;
+    grad = 0.0f;
+    curv = 0.0f;
+#pragma unroll
+    for (int dz = -1; dz <= 1; dz++)
+#pragma unroll
+        for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+            for (int dx = -1; dx <= 1; dx++) {
+                const int n2 = dx * dx + dy * dy + dz * dz;
+                if (n2 == 0) continue;
+                const int fx = ix + dx, fy = iy + dy, fz = iz + dz;
+                if (fx < 0 || fx >= D.nx || fy < 0 || fy >= D.ny || fz < 0 || fz >= D.nz) continue;
+                const float bi = n2 == 1 ? b1 : (n2 == 2 ? b2 : b3);
+                float d, o;
+                P.eval(xj - __ldg(&x[j + dx * D.sx + dy * D.sy + dz * D.sz]), d, o);
+                grad = fmaf(bi, d, grad);
+                curv = fmaf(2.0f * bi, o, curv);
+            }
+}
+
+// One thread per voxel in memory order of a volume with strides D.
+__global__ void __launch_bounds__(256) reg_gradient3_kernel(VolDims D, int zfast, const float *__restrict__ x,
+                                                           float beta, Pot P, float *__restrict__ grad,
+                                                           float *__restrict__ curv)
+{
+    const long long n = (long long)D.nx * D.ny * D.nz;
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int ix, iy, iz;
+    if (zfast) {
+        iz = (int)(j % D.nz);
+        const long long c = j / D.nz;
+        ix = (int)(c % D.nx);
+        iy = (int)(c / D.nx);
+    } else {
+        ix = (int)(j % D.nx);
+        const long long c = j / D.nx;
+        iy = (int)(c % D.ny);
+        iz = (int)(c / D.ny);
+    }
+    float gr, cv;
+    reg_terms3(x, D, ix, iy, iz, j, beta, P, gr, cv);
+    grad[j] = gr;
+    if (curv) curv[j] = cv;
+}
+
+// Fused x-update of Algorithm 1/2 on a column-major volume.
+__global__ void __launch_bounds__(256) reg_update3_kernel(VolDims D, SolveDev S, float beta, Pot P)
+{
+    const long long n = (long long)D.nx * D.ny * D.nz;
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int iz = (int)(j % D.nz);
+    const long long c = j / D.nz;
+    const int ix = (int)(c % D.nx), iy = (int)(c / D.nx);
+    const float rho = __ldcg(&S.rho_tab[__ldcg(&S.counter[0])]);
+    float gr, cv;
+    reg_terms3(S.x, D, ix, iy, iz, j, beta, P, gr, cv);
+    const float xj = S.x[j], dl = S.d_l[j], g = S.g[j], h = S.h[j];
+    const float s = (S.algorithm == CT_ALG_PROPOSED) ? fmaf(rho, fmaf(dl, xj, -h), (1.0f - rho) * g)
+                                                     : fmaf(rho, h, (1.0f - rho) * g);
+    const float den = fmaf(rho, dl, cv);
+    float xn = den > 0.0f ? xj - (s + gr) / den : xj;
+    if (S.nonneg) xn = fmaxf(xn, 0.0f);
+    S.x_new[j] = xn;
+}
+
+// RMSD over the field-of-view cylinder of a column-major volume (see the 2-D
+// rmsd kernel: per-block partial sums, the last block writes the trace entry).
+__global__ void __launch_bounds__(256) rmsd3_kernel(FanDev G, int nz, const float *__restrict__ x,
+                                                    const float *__restrict__ xr, float r2max,
+                                                    double *__restrict__ partial, int *__restrict__ counter,
+                                                    float *__restrict__ trace, int M, float hu)
+{
+    __shared__ double ss[256];
+    __shared__ double sc[256];
+    double s = 0.0, c = 0.0;
+    const long long n = (long long)G.nx * G.ny * nz;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        const long long col = j / nz;
+        const int ix = (int)(col % G.nx), iy = (int)(col / G.nx);
+        const float X = ((float)ix - G.cxo) * G.dx, Y = ((float)iy - G.cyo) * G.dy;
+        if (fmaf(X, X, Y * Y) <= r2max) {
+            const double d = (double)x[j] - (double)xr[j];
+            s += d * d;
+            c += 1.0;
+        }
+    }
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+            sc[threadIdx.x] += sc[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = ss[0];
+        partial[2 * blockIdx.x + 1] = sc[0];
+        __threadfence();
+        const int done = atomicAdd(&counter[2], 1);
+        if (done == (int)gridDim.x - 1) {
+            __threadfence();
+            double S = 0.0, C = 0.0;
+            for (int b = 0; b < (int)gridDim.x; b++) {
+                S += __ldcg(&partial[2 * b]);
+                C += __ldcg(&partial[2 * b + 1]);
+            }
+            const int it = __ldcg(&counter[0]) / M - 1;
+            trace[it] = C > 0 ? (float)(sqrt(S / C) * hu) : 0.0f;
+            counter[2] = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- layout changes
+
+// dst[c][r] = src[r][c] for an R x C matrix (tiles of 32 x 32 through shared memory).
+__global__ void __launch_bounds__(256) transpose_kernel(const float *__restrict__ src, float *__restrict__ dst,
+                                                        long long R, long long C, float scale, int accumulate)
+{
+    __shared__ float tile[32][33];
+    const long long tiles_c = (C + 31) / 32;
+    const long long c0 = ((long long)blockIdx.x % tiles_c) * 32, r0 = ((long long)blockIdx.x / tiles_c) * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const long long r = r0 + i, c = c0 + threadIdx.x;
+        if (r < R && c < C) tile[i][threadIdx.x] = __ldg(&src[r * C + c]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const long long c = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && c < C) {
+            const float v = scale * tile[threadIdx.x][i];
+            dst[c * R + r] = accumulate ? dst[c * R + r] + v : v;
+        }
+    }
+}
+
+cudaError_t transpose(const float *src, float *dst, long long R, long long C, float scale, int accumulate,
+                      cudaStream_t st)
+{
+    const long long tiles = ((C + 31) / 32) * ((R + 31) / 32);
+    transpose_kernel<<<(unsigned)tiles, dim3(32, 8), 0, st>>>(src, dst, R, C, scale, accumulate);
+    return cudaGetLastError();
+}
+
+Pot make_pot(int potential, float delta) { return Pot{potential, potential == CT_POT_QUADRATIC ? 0.0f : 1.0f / delta}; }
+
+template <int MODE>
+cudaError_t fp_helix_dispatch(const ct_geom *g, const float *x, const int *views, int nviews, float *out,
+                              const float *y, const float *w, cudaStream_t st)
+{
+    const FanDev &G = g->fan;
+    const HelixDev &H = g->hx;
+    const unsigned blocks = (unsigned)nviews * (unsigned)((G.ns + 31) / 32);
+    const int nt = H.nt;
+#define CT_FP_HX(NTV)                                                                                   \
+    fp_helix_kernel<MODE, NTV><<<blocks, kHxWarps * 32, sizeof(float) * kHxWarps * 32 * (NTV + 4), st>>>( \
+        G, H, x, views, nviews, out, y, w)
+    if (nt <= 8) CT_FP_HX(8);
+    else if (nt <= 16) CT_FP_HX(16);
+    else if (nt <= 32) CT_FP_HX(32);
+    else CT_FP_HX(64);
+#undef CT_FP_HX
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t bp_helix_dispatch(const ct_geom *g, const float *sino, const int *views, int nviews, float *x,
+                              float scale, int accumulate, const SolveDev &S, cudaStream_t st)
+{
+    const FanDev &G = g->fan;
+    const HelixDev &H = g->hx;
+    const int zc = g->hx_zc;
+    dim3 grid((G.nx + 15) / 16, (G.ny + 7) / 8, (H.nz + zc - 1) / zc);
+    switch (zc) {
+    case 16: bp_helix_kernel<MODE, 16><<<grid, kHxBpCols, 0, st>>>(G, H, sino, views, nviews, x, scale, accumulate, S); break;
+    case 8: bp_helix_kernel<MODE, 8><<<grid, kHxBpCols, 0, st>>>(G, H, sino, views, nviews, x, scale, accumulate, S); break;
+    case 4: bp_helix_kernel<MODE, 4><<<grid, kHxBpCols, 0, st>>>(G, H, sino, views, nviews, x, scale, accumulate, S); break;
+    case 2: bp_helix_kernel<MODE, 2><<<grid, kHxBpCols, 0, st>>>(G, H, sino, views, nviews, x, scale, accumulate, S); break;
+    default: bp_helix_kernel<MODE, 1><<<grid, kHxBpCols, 0, st>>>(G, H, sino, views, nviews, x, scale, accumulate, S); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int helix_chunk_voxels(double a_max)
+{
+    for (int zc = 16; zc >= 1; zc >>= 1)
+        if (std::ceil(zc * a_max) + 2.0 <= (double)kHxQMax) return zc;
+    return 0;
+}
+
+int helix_max_rows() { return kHxMaxRows; }
+int helix_max_span() { return kHxMaxSpan; }
+int helix_max_march() { return kHxMaxMarch; }
+
+cudaError_t launch_fp_helix(const ct_geom *g, int mode, const float *x, const int *views, int nviews, float *out,
+                            const float *y, const float *w, cudaStream_t st)
+{
+    switch (mode) {
+    case FP_PLAIN: return fp_helix_dispatch<FP_PLAIN>(g, x, views, nviews, out, y, w, st);
+    case FP_RESID: return fp_helix_dispatch<FP_RESID>(g, x, views, nviews, out, y, w, st);
+    default: return fp_helix_dispatch<FP_ONES_W>(g, x, views, nviews, out, y, w, st);
+    }
+}
+
+cudaError_t launch_bp_helix(const ct_geom *g, int mode, const float *sino, const int *views, int nviews, float *x,
+                            float scale, int accumulate, const SolveDev *S, cudaStream_t st)
+{
+    SolveDev s0{};
+    const SolveDev &SS = S ? *S : s0;
+    switch (mode) {
+    case BP_PLAIN: return bp_helix_dispatch<BP_PLAIN>(g, sino, views, nviews, x, scale, accumulate, SS, st);
+    case BP_SOLVE_INIT: return bp_helix_dispatch<BP_SOLVE_INIT>(g, sino, views, nviews, x, scale, accumulate, SS, st);
+    default: return bp_helix_dispatch<BP_SOLVE_UPDATE>(g, sino, views, nviews, x, scale, accumulate, SS, st);
+    }
+}
+
+static VolDims column_dims(const ct_geom *g)
+{
+    const int nx = g->fan.nx, ny = g->fan.ny, nz = g->hx.nz;
+    return VolDims{nx, ny, nz, (long long)nz, (long long)nx * nz, 1};
+}
+
+cudaError_t launch_reg_gradient_helix(const ct_geom *g, const float *x, float beta, float delta, int potential,
+                                      float *grad, float *curv, cudaStream_t st)
+{
+    // the C ABI's layout, [iz][iy][ix]
+    const int nx = g->fan.nx, ny = g->fan.ny, nz = g->hx.nz;
+    const VolDims D{nx, ny, nz, 1, (long long)nx, (long long)nx * ny};
+    const long long n = (long long)nx * ny * nz;
+    reg_gradient3_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(D, 0, x, beta, make_pot(potential, delta),
+                                                                      grad, curv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reg_update_helix(const ct_geom *g, const SolveDev &S, float beta, float delta, int potential,
+                                    cudaStream_t st)
+{
+    const VolDims D = column_dims(g);
+    const long long n = (long long)D.nx * D.ny * D.nz;
+    reg_update3_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(D, S, beta, make_pot(potential, delta));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rmsd_helix(const ct_geom *g, const float *x, const float *xr, float r2max, double *partial,
+                              int *counter, float *trace, int M, float hu, cudaStream_t st)
+{
+    rmsd3_kernel<<<152, 256, 0, st>>>(g->fan, g->hx.nz, x, xr, r2max, partial, counter, trace, M, hu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_columns(const ct_geom *g, const float *src, float *dst, cudaStream_t st)
+{
+    return transpose(src, dst, g->hx.nz, (long long)g->fan.nx * g->fan.ny, 1.0f, 0, st);
+}
+
+cudaError_t launch_to_slices(const ct_geom *g, const float *src, float *dst, float scale, int accumulate,
+                             cudaStream_t st)
+{
+    return transpose(src, dst, (long long)g->fan.nx * g->fan.ny, g->hx.nz, scale, accumulate, st);
+}
+
+ct_status helix_forward(const ct_geom *g, const float *x, float *y, const int *views, int nviews, cudaStream_t st)
+{
+    const int *dv = nullptr;
+    ct_status s = stage_views(g, views, nviews, &dv, st);
+    if (s != CT_OK) return s;
+    CT_CUDA_TRY(launch_to_columns(g, x, g->d_vol_ws, st), "ct_forward layout");
+    CT_CUDA_TRY(launch_fp_helix(g, FP_PLAIN, g->d_vol_ws, dv, nviews, y, nullptr, nullptr, st), "ct_forward launch");
+    return CT_OK;
+}
+
+ct_status helix_back(const ct_geom *g, const float *y, float *x, const int *views, int nviews, float scale,
+                     int accumulate, cudaStream_t st)
+{
+    const int *dv = nullptr;
+    ct_status s = stage_views(g, views, nviews, &dv, st);
+    if (s != CT_OK) return s;
+    CT_CUDA_TRY(launch_bp_helix(g, BP_PLAIN, y, dv, nviews, g->d_vol_ws, 1.0f, 0, nullptr, st), "ct_back launch");
+    CT_CUDA_TRY(launch_to_slices(g, g->d_vol_ws, x, scale, accumulate, st), "ct_back layout");
+    return CT_OK;
+}
+
+ct_status helix_sqs_diag(const ct_geom *g, const float *w, float *d_l, cudaStream_t st)
+{
+    const int na = g->fan.na;
+    CT_CUDA_TRY(launch_fp_helix(g, FP_ONES_W, nullptr, g->d_views_all, na, g->d_sino_ws, nullptr, w, st),
+                "ct_sqs_diag forward");
+    CT_CUDA_TRY(launch_bp_helix(g, BP_PLAIN, g->d_sino_ws, g->d_views_all, na, g->d_vol_ws, 1.0f, 0, nullptr, st),
+                "ct_sqs_diag back");
+    CT_CUDA_TRY(launch_to_slices(g, g->d_vol_ws, d_l, 1.0f, 0, st), "ct_sqs_diag layout");
+    return CT_OK;
+}
+
+ct_status helix_reg_gradient(const ct_geom *g, const float *x, float beta, float delta, int potential, float *grad,
+                             float *curv, cudaStream_t st)
+{
+    CT_CUDA_TRY(launch_reg_gradient_helix(g, x, beta, delta, potential, grad, curv, st), "ct_reg_gradient launch");
+    return CT_OK;
+}
+
+}  // namespace ct

@@ -183,6 +183,10 @@ extern "C" ct_status ct_geom_precompute(ct_geom *g, unsigned long long max_bytes
                                         void *stream)
 {
     if (!g) { set_error("ct_geom_precompute: null geometry"); return CT_EINVAL; }
+    if (g->helical) {
+        set_error("ct_geom_precompute: the resident matrix is built for 2-D fan-beam geometries only");
+        return CT_ENOTSUP;
+    }
     if (!g->d_row_ptr) {
         bool too_big = false;
         cudaError_t e = build_matrix(g, max_bytes, (cudaStream_t)stream, &too_big);

@@ -40,6 +40,7 @@ using namespace ct;
 extern "C" ct_status ct_sqs_diag_noalloc(const ct_geom *g, const float *w, float *d_l, void *stream)
 {
     if (!g || !w || !d_l) { set_error("ct_sqs_diag_noalloc: null argument"); return CT_EINVAL; }
+    if (g->helical) { set_error("ct_sqs_diag_noalloc: 2-D fan-beam geometries only"); return CT_ENOTSUP; }
     const long long cells = (long long)g->fan.na * g->fan.ns;
     if (cells > kNoAllocMaxCells) {
         set_error("ct_sqs_diag_noalloc: the sinogram has %lld cells (na * ns); the allocation-free scratch holds "

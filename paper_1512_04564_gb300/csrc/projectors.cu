@@ -495,6 +495,7 @@ extern "C" ct_status ct_forward(const ct_geom *g, const float *x, float *y, cons
     ct_status st = validate_views(g, views, nviews);
     if (st != CT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    if (g->helical) return helix_forward(g, x, y, views, nviews, s);
     const int *dv = nullptr;
     if ((st = stage_views(g, views, nviews, &dv, s)) != CT_OK) return st;
     CT_CUDA_TRY(launch_fp(g->fan, FP_PLAIN, x, dv, nviews, y, nullptr, nullptr, s), "ct_forward launch");
@@ -508,6 +509,7 @@ extern "C" ct_status ct_back(const ct_geom *g, const float *y, float *x, const i
     ct_status st = validate_views(g, views, nviews);
     if (st != CT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    if (g->helical) return helix_back(g, y, x, views, nviews, scale, accumulate, s);
     const int *dv = nullptr;
     if ((st = stage_views(g, views, nviews, &dv, s)) != CT_OK) return st;
     CT_CUDA_TRY(launch_bp(g->fan, BP_PLAIN, y, dv, nviews, x, scale, accumulate, nullptr, s), "ct_back launch");
@@ -518,6 +520,7 @@ extern "C" ct_status ct_sqs_diag(const ct_geom *g, const float *w, float *d_l, v
 {
     if (!g || !w || !d_l) { set_error("ct_sqs_diag: null argument"); return CT_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
+    if (g->helical) return helix_sqs_diag(g, w, d_l, s);
     // q = w (A 1) over all views, then D_L = A' q
     CT_CUDA_TRY(launch_fp(g->fan, FP_ONES_W, nullptr, g->d_views_all, g->fan.na, g->d_sino_ws, nullptr, w, s),
                 "ct_sqs_diag forward");

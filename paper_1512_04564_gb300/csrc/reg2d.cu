@@ -82,6 +82,7 @@ extern "C" ct_status ct_reg_gradient(const ct_geom *g, const float *x, float bet
         set_error("need beta >= 0 and delta > 0");
         return CT_EINVAL;
     }
+    if (g->helical) return helix_reg_gradient(g, x, beta, delta, potential, grad, curv, (cudaStream_t)stream);
     CT_CUDA_TRY(launch_reg_gradient(g->fan, x, beta, delta, potential, grad, curv, (cudaStream_t)stream),
                 "ct_reg_gradient launch");
     return CT_OK;

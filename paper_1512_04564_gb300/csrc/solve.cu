@@ -74,16 +74,19 @@ struct Workspace {
     float *x_new, *g, *h, *d_l, *resid, *rho_tab, *trace;
     int *perm, *counter;
     double *partial;
+    float *x_col, *xref_col;  // helical: column-major copies of x and x_ref
 };
 
 ct_status ensure_workspace(ct_geom *g, int max_sub, int T, int n_iter, Workspace &W)
 {
-    const size_t npix = (size_t)g->fan.nx * g->fan.ny;
-    size_t off[10], sz = 0;
-    const size_t sizes[10] = {npix * 4, npix * 4, npix * 4, npix * 4, (size_t)max_sub * g->fan.ns * 4,
+    const size_t npix = (size_t)g->fan.nx * g->fan.ny * (g->helical ? g->hx.nz : 1);
+    const size_t view_len = (size_t)g->fan.ns * (g->helical ? g->hx.nt : 1);
+    const size_t vol_h = g->helical ? npix * 4 : 0;
+    size_t off[12], sz = 0;
+    const size_t sizes[12] = {npix * 4, npix * 4, npix * 4, npix * 4, (size_t)max_sub * view_len * 4,
                               (size_t)T * 4, (size_t)(n_iter > 0 ? n_iter : 1) * 4, (size_t)g->fan.na * 4, 16 * 4,
-                              (size_t)kRmsdBlocks * 2 * 8};
-    for (int i = 0; i < 10; i++) {
+                              (size_t)kRmsdBlocks * 2 * 8, vol_h, vol_h};
+    for (int i = 0; i < 12; i++) {
         off[i] = sz;
         sz += align_up(sizes[i]);
     }
@@ -105,6 +108,8 @@ ct_status ensure_workspace(ct_geom *g, int max_sub, int T, int n_iter, Workspace
     W.perm = (int *)(b + off[7]);
     W.counter = (int *)(b + off[8]);
     W.partial = (double *)(b + off[9]);
+    W.x_col = g->helical ? (float *)(b + off[10]) : nullptr;
+    W.xref_col = g->helical ? (float *)(b + off[11]) : nullptr;
     return CT_OK;
 }
 
@@ -113,6 +118,27 @@ double rho_continuation(long k, double alpha)
     if (k == 0) return 1.0;
     const double q = M_PI / (alpha * (double)(k + 1));
     return q * std::sqrt(1.0 - 0.25 * q * q);
+}
+
+// The launches of one subiteration step, for either geometry kind.
+cudaError_t step_update(const ct_geom *g, const SolveDev &S, const ct_solve_params *p, cudaStream_t st)
+{
+    return g->helical ? launch_reg_update_helix(g, S, p->beta, p->delta, p->potential, st)
+                      : launch_reg_update(g->fan, S, p->beta, p->delta, p->potential, st);
+}
+
+cudaError_t step_fp(const ct_geom *g, int mode, const float *x, const int *views, int nviews, float *out,
+                    const float *y, const float *w, cudaStream_t st)
+{
+    return g->helical ? launch_fp_helix(g, mode, x, views, nviews, out, y, w, st)
+                      : launch_fp(g->fan, mode, x, views, nviews, out, y, w, st);
+}
+
+cudaError_t step_bp(const ct_geom *g, int mode, const float *sino, const int *views, int nviews, float *x,
+                    const SolveDev *S, cudaStream_t st)
+{
+    return g->helical ? launch_bp_helix(g, mode, sino, views, nviews, x, 1.0f, 0, S, st)
+                      : launch_bp(g->fan, mode, sino, views, nviews, x, 1.0f, 0, S, st);
 }
 
 struct Events {
@@ -198,7 +224,7 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
     CT_CUDA_TRY(cudaMemsetAsync(W.counter, 0, 16 * sizeof(int), ws), "reset counters");
 
     SolveDev S;
-    S.x = x;
+    S.x = g->helical ? W.x_col : x;
     S.x_new = W.x_new;
     S.g = W.g;
     S.h = W.h;
@@ -221,15 +247,18 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
         CT_CUDA_TRY(cudaStreamBeginCapture(ws, cudaStreamCaptureModeThreadLocal), "begin capture");
         cudaError_t e = cudaSuccess;
         for (int m = 0; m < M && e == cudaSuccess; m++) {
-            e = launch_reg_update(G, S, p->beta, p->delta, p->potential, ws);
-            if (e == cudaSuccess)
-                e = launch_fp(G, FP_RESID, W.x_new, W.perm + off[m], cnt[m], W.resid, y, w, ws);
-            if (e == cudaSuccess) e = launch_bp(G, BP_SOLVE_UPDATE, W.resid, W.perm + off[m], cnt[m], nullptr, 1.0f, 0, &S, ws);
+            e = step_update(g, S, p, ws);
+            if (e == cudaSuccess) e = step_fp(g, FP_RESID, W.x_new, W.perm + off[m], cnt[m], W.resid, y, w, ws);
+            if (e == cudaSuccess) e = step_bp(g, BP_SOLVE_UPDATE, W.resid, W.perm + off[m], cnt[m], nullptr, &S, ws);
         }
         if (e == cudaSuccess && p->x_ref) {
-            rmsd_kernel<<<kRmsdBlocks, 256, 0, ws>>>(G, x, p->x_ref, r2max, W.partial, W.counter, W.trace, M,
-                                                     p->hu_per_unit);
-            e = cudaGetLastError();
+            if (g->helical) {
+                e = launch_rmsd_helix(g, S.x, W.xref_col, r2max, W.partial, W.counter, W.trace, M, p->hu_per_unit, ws);
+            } else {
+                rmsd_kernel<<<kRmsdBlocks, 256, 0, ws>>>(G, x, p->x_ref, r2max, W.partial, W.counter, W.trace, M,
+                                                         p->hu_per_unit);
+                e = cudaGetLastError();
+            }
         }
         cudaError_t e2 = cudaStreamEndCapture(ws, &graph);
         if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e, "capturing iteration"); }
@@ -247,13 +276,16 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
 
     CT_CUDA_TRY(cudaEventRecord(ev_start, ws), "event");
     if (p->init_fbp) CT_CUDA_TRY(launch_fbp(g, y, x, CT_FBP_HANN, ws), "initial FBP image");
+    if (g->helical) {  // the kernels work on column-major volumes
+        CT_CUDA_TRY(launch_to_columns(g, x, W.x_col, ws), "x layout");
+        if (p->x_ref) CT_CUDA_TRY(launch_to_columns(g, p->x_ref, W.xref_col, ws), "x_ref layout");
+    }
     // D_L = diag(A' W A 1) over all views
-    CT_CUDA_TRY(launch_fp(G, FP_ONES_W, nullptr, g->d_views_all, na, g->d_sino_ws, nullptr, w, ws), "D_L forward");
-    CT_CUDA_TRY(launch_bp(G, BP_PLAIN, g->d_sino_ws, g->d_views_all, na, W.d_l, 1.0f, 0, nullptr, ws), "D_L back");
+    CT_CUDA_TRY(step_fp(g, FP_ONES_W, nullptr, g->d_views_all, na, g->d_sino_ws, nullptr, w, ws), "D_L forward");
+    CT_CUDA_TRY(step_bp(g, BP_PLAIN, g->d_sino_ws, g->d_views_all, na, W.d_l, nullptr, ws), "D_L back");
     // rho = 1, zeta = g = M grad L_M(x), h = D_L x - zeta  (last subset)
-    CT_CUDA_TRY(launch_fp(G, FP_RESID, x, W.perm + off[M - 1], cnt[M - 1], W.resid, y, w, ws), "init forward");
-    CT_CUDA_TRY(launch_bp(G, BP_SOLVE_INIT, W.resid, W.perm + off[M - 1], cnt[M - 1], nullptr, 1.0f, 0, &S, ws),
-                "init back");
+    CT_CUDA_TRY(step_fp(g, FP_RESID, S.x, W.perm + off[M - 1], cnt[M - 1], W.resid, y, w, ws), "init forward");
+    CT_CUDA_TRY(step_bp(g, BP_SOLVE_INIT, W.resid, W.perm + off[M - 1], cnt[M - 1], nullptr, &S, ws), "init back");
 
     const float tol = p->stop_rmsd_hu > 0.0f ? p->stop_rmsd_hu : 1.0f;
     int done = 0;
@@ -268,6 +300,7 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
             if (r <= tol) break;
         }
     }
+    if (g->helical) CT_CUDA_TRY(launch_to_slices(g, W.x_col, x, 1.0f, 0, ws), "x layout");
     CT_CUDA_TRY(cudaEventRecord(ev_end, ws), "event");
     CT_CUDA_TRY(cudaEventRecord(ev_in, ws), "event");
     CT_CUDA_TRY(cudaStreamWaitEvent(user, ev_in, 0), "ordering caller's stream");

@@ -24,6 +24,7 @@ using namespace ct;
 extern "C" ct_status ct_geom_autotune(ct_geom *g, int views_per_launch, int *fp_choice, int *bp_choice, void *stream)
 {
     if (!g) { set_error("ct_geom_autotune: null geometry"); return CT_EINVAL; }
+    if (g->helical) { set_error("ct_geom_autotune: 2-D fan-beam geometries only"); return CT_ENOTSUP; }
     const int na = g->fan.na, ns = g->fan.ns;
     int nv = views_per_launch > 0 ? views_per_launch : (na < 24 ? na : 24);
     if (nv > na) nv = na;

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libct.so")
 
 CT_OK, CT_EINVAL, CT_ENOMEM, CT_ECUDA, CT_ETIMEOUT, CT_ENOTSUP = range(6)
 CT_FAN_ARC_2D = 1
+CT_HELICAL_CONE_ARC = 2
 CT_POT_HYPERBOLA, CT_POT_FAIR, CT_POT_QUADRATIC = 0, 1, 2
 CT_ALG_PROPOSED, CT_ALG_SIMPLE = 0, 1
 CT_FBP_RAMP, CT_FBP_HANN = 0, 1
@@ -134,30 +135,69 @@ def _views(views, na):
 
 
 class Geometry:
-    """Owner of a ``ct_geom`` handle (``ct_geom_create`` / ``ct_geom_destroy``)."""
+    """Owner of a ``ct_geom`` handle (``ct_geom_create`` / ``ct_geom_destroy``).
+
+    2-D fan-beam scans (``kind=CT_FAN_ARC_2D``) use images ``[ny][nx]`` and
+    sinograms ``[view][ns]``; helical cone-beam scans (``CT_HELICAL_CONE_ARC``)
+    volumes ``[nz][ny][nx]`` and sinograms ``[view][nt][ns]``.
+    """
 
     def __init__(self, *, nx, ny, dx, dy, ns, ds, na, dso, dsd, offset_x=0.0, offset_y=0.0, offset_s=0.0,
-                 orbit_deg=360.0, orbit_start_deg=0.0, kind=CT_FAN_ARC_2D):
+                 orbit_deg=360.0, orbit_start_deg=0.0, kind=CT_FAN_ARC_2D, nz=1, dz=1.0, offset_z=0.0, nt=1,
+                 dt=1.0, offset_t=0.0, pitch=0.0):
         d = ct_geom_desc()
         d.kind = kind
-        d.nx, d.ny, d.nz = nx, ny, 1
-        d.dx, d.dy, d.dz = dx, dy, 1.0
-        d.offset_x, d.offset_y = offset_x, offset_y
-        d.ns, d.nt, d.na = ns, 1, na
-        d.ds, d.dt, d.offset_s = ds, 1.0, offset_s
+        d.nx, d.ny, d.nz = nx, ny, nz
+        d.dx, d.dy, d.dz = dx, dy, dz
+        d.offset_x, d.offset_y, d.offset_z = offset_x, offset_y, offset_z
+        d.ns, d.nt, d.na = ns, nt, na
+        d.ds, d.dt, d.offset_s, d.offset_t = ds, dt, offset_s, offset_t
         d.dso, d.dsd = dso, dsd
         d.orbit_deg, d.orbit_start_deg = orbit_deg, orbit_start_deg
+        d.pitch = pitch
         self.desc = d
+        self.kind = kind
         self.nx, self.ny, self.ns, self.na = nx, ny, ns, na
+        self.nz, self.nt = (nz, nt) if kind == CT_HELICAL_CONE_ARC else (1, 1)
         h = ctypes.c_void_p()
         _check(_lib.ct_geom_create(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
+
+    @property
+    def nvox(self) -> int:
+        """Pixels (2-D) or voxels (3-D) of the image."""
+        return self.nx * self.ny * self.nz
+
+    @property
+    def view_len(self) -> int:
+        """Detector cells per view."""
+        return self.ns * self.nt
+
+    @property
+    def image_shape(self) -> tuple:
+        return (self.nz, self.ny, self.nx) if self.kind == CT_HELICAL_CONE_ARC else (self.ny, self.nx)
+
+    @property
+    def view_shape(self) -> tuple:
+        return (self.nt, self.ns) if self.kind == CT_HELICAL_CONE_ARC else (self.ns,)
 
     @classmethod
     def from_fan(cls, g) -> "Geometry":
         return cls(nx=g.nx, ny=g.ny, dx=g.dx, dy=g.dy, ns=g.ns, ds=g.ds, na=g.na, dso=g.dso, dsd=g.dsd,
                    offset_x=g.offset_x, offset_y=g.offset_y, offset_s=g.offset_s, orbit_deg=g.orbit_deg,
                    orbit_start_deg=g.orbit_start_deg)
+
+    @classmethod
+    def from_helix(cls, g) -> "Geometry":
+        return cls(nx=g.nx, ny=g.ny, dx=g.dx, dy=g.dy, ns=g.ns, ds=g.ds, na=g.na, dso=g.dso, dsd=g.dsd,
+                   offset_x=g.offset_x, offset_y=g.offset_y, offset_s=g.offset_s, orbit_deg=g.orbit_deg,
+                   orbit_start_deg=g.orbit_start_deg, kind=CT_HELICAL_CONE_ARC, nz=g.nz, dz=g.dz,
+                   offset_z=g.offset_z, nt=g.nt, dt=g.dt, offset_t=g.offset_t, pitch=g.pitch)
+
+    @classmethod
+    def from_scan(cls, g) -> "Geometry":
+        """From a fan-beam or helical scan description (anything with the same fields)."""
+        return cls.from_helix(g) if hasattr(g, "nz") else cls.from_fan(g)
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
@@ -192,7 +232,7 @@ def ct_geom_autotune(geom: Geometry, views_per_launch: int = 0, stream=None) -> 
 
 def ct_forward(geom: Geometry, x: torch.Tensor, y: torch.Tensor, views=None, stream=None) -> torch.Tensor:
     arr, nv = _views(views, geom.na)
-    _check(_lib.ct_forward(geom.handle, _ptr(x, "x", geom.nx * geom.ny), _ptr(y, "y", nv * geom.ns), arr, nv,
+    _check(_lib.ct_forward(geom.handle, _ptr(x, "x", geom.nvox), _ptr(y, "y", nv * geom.view_len), arr, nv,
                            _stream(stream)))
     return y
 
@@ -200,28 +240,28 @@ def ct_forward(geom: Geometry, x: torch.Tensor, y: torch.Tensor, views=None, str
 def ct_back(geom: Geometry, y: torch.Tensor, x: torch.Tensor, views=None, scale=1.0, accumulate=False,
             stream=None) -> torch.Tensor:
     arr, nv = _views(views, geom.na)
-    _check(_lib.ct_back(geom.handle, _ptr(y, "y", nv * geom.ns), _ptr(x, "x", geom.nx * geom.ny), arr, nv,
+    _check(_lib.ct_back(geom.handle, _ptr(y, "y", nv * geom.view_len), _ptr(x, "x", geom.nvox), arr, nv,
                         float(scale), int(bool(accumulate)), _stream(stream)))
     return x
 
 
 def ct_sqs_diag(geom: Geometry, w: torch.Tensor, d_l: torch.Tensor, stream=None) -> torch.Tensor:
-    _check(_lib.ct_sqs_diag(geom.handle, _ptr(w, "w", geom.na * geom.ns), _ptr(d_l, "d_l", geom.nx * geom.ny),
+    _check(_lib.ct_sqs_diag(geom.handle, _ptr(w, "w", geom.na * geom.view_len), _ptr(d_l, "d_l", geom.nvox),
                             _stream(stream)))
     return d_l
 
 
 def ct_sqs_diag_noalloc(geom: Geometry, w: torch.Tensor, d_l: torch.Tensor, stream=None) -> torch.Tensor:
     """ct_sqs_diag without device allocation (scratch in a fixed 4 MiB library array; na*ns <= 2^20)."""
-    _check(_lib.ct_sqs_diag_noalloc(geom.handle, _ptr(w, "w", geom.na * geom.ns),
-                                    _ptr(d_l, "d_l", geom.nx * geom.ny), _stream(stream)))
+    _check(_lib.ct_sqs_diag_noalloc(geom.handle, _ptr(w, "w", geom.na * geom.view_len),
+                                    _ptr(d_l, "d_l", geom.nvox), _stream(stream)))
     return d_l
 
 
 def ct_fbp(geom: Geometry, y: torch.Tensor, x: torch.Tensor, window: str = "hann", stream=None) -> torch.Tensor:
     """Full-scan equiangular fan-beam FBP (initial image of Algorithm 1)."""
     win = {"ramp": CT_FBP_RAMP, "hann": CT_FBP_HANN}[window] if isinstance(window, str) else int(window)
-    _check(_lib.ct_fbp(geom.handle, _ptr(y, "y", geom.na * geom.ns), _ptr(x, "x", geom.nx * geom.ny), win,
+    _check(_lib.ct_fbp(geom.handle, _ptr(y, "y", geom.na * geom.view_len), _ptr(x, "x", geom.nvox), win,
                        _stream(stream)))
     return x
 
@@ -229,7 +269,7 @@ def ct_fbp(geom: Geometry, y: torch.Tensor, x: torch.Tensor, window: str = "hann
 def ct_reg_gradient(geom: Geometry, x: torch.Tensor, beta: float, delta: float, potential: str | int,
                     grad: torch.Tensor, curv: torch.Tensor | None = None, stream=None):
     pot = POTENTIALS[potential] if isinstance(potential, str) else int(potential)
-    n = geom.nx * geom.ny
+    n = geom.nvox
     _check(_lib.ct_reg_gradient(geom.handle, _ptr(x, "x", n), float(beta), float(delta), pot,
                                 _ptr(grad, "grad", n), _ptr(curv, "curv", n), _stream(stream)))
     return grad, curv
@@ -241,12 +281,12 @@ def ct_relaxed_oslalm_solve(geom: Geometry, y: torch.Tensor, w: torch.Tensor, x:
                             x_ref: torch.Tensor | None = None, hu_per_unit=1.0, fov_radius=0.0,
                             stop_rmsd_hu=0.0, init_fbp=False, stream=None) -> dict:
     """Relaxed OS-LALM (Algorithm 1 / 2); x is updated in place.  Returns the report as a dict."""
-    n = geom.nx * geom.ny
+    n = geom.nvox
     p = _params(geom, M=M, n_iter=n_iter, alpha=alpha, beta=beta, delta=delta, potential=potential,
                 algorithm=algorithm, nonneg=nonneg, continuation=continuation, rho_fixed=rho_fixed, x_ref=x_ref,
                 hu_per_unit=hu_per_unit, fov_radius=fov_radius, stop_rmsd_hu=stop_rmsd_hu, init_fbp=init_fbp)
     r, trace, its = _report(n_iter)
-    _check(_lib.ct_relaxed_oslalm_solve(geom.handle, _ptr(y, "y", geom.na * geom.ns), _ptr(w, "w", geom.na * geom.ns),
+    _check(_lib.ct_relaxed_oslalm_solve(geom.handle, _ptr(y, "y", geom.na * geom.view_len), _ptr(w, "w", geom.na * geom.view_len),
                                         ctypes.byref(p), _ptr(x, "x", n), ctypes.byref(r), _stream(stream)))
     return _report_dict(r, trace, its, x_ref is not None)
 
@@ -254,7 +294,7 @@ def ct_relaxed_oslalm_solve(geom: Geometry, y: torch.Tensor, w: torch.Tensor, x:
 def _params(geom, *, M, n_iter, alpha, beta, delta, potential="hyperbola", algorithm="proposed", nonneg=True,
             continuation=True, rho_fixed=0.0, x_ref=None, hu_per_unit=1.0, fov_radius=0.0, stop_rmsd_hu=0.0,
             init_fbp=False):
-    n = geom.nx * geom.ny
+    n = geom.nvox
     p = ct_solve_params()
     p.M, p.n_iter, p.alpha, p.beta, p.delta = M, n_iter, alpha, beta, delta
     p.potential = POTENTIALS[potential] if isinstance(potential, str) else int(potential)
