@@ -132,21 +132,27 @@ __device__ __forceinline__ void row_boundary(float b_minus_c, float ia_hi, float
 }
 
 template <int MODE, int NT>
-__global__ void __launch_bounds__(kHxWarps * 32) fp_helix_kernel(FanDev G, HelixDev H, const float *__restrict__ x,
+__global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, HelixDev H, const float *__restrict__ x,
                                                                 const int *__restrict__ views, int nviews,
                                                                 float *__restrict__ out, const float *__restrict__ y,
                                                                 const float *__restrict__ w)
 {
     constexpr int PS = NT + 4;  // stride of a staged axial profile (floats; float4-aligned)
-    __shared__ int s_pre[kHxMaxMarch + 1];
-    __shared__ int s_lo[kHxMaxMarch];
     __shared__ float s_w[kHxWarps][32][kHxMaxSpan + 1];
     __shared__ int s_c[kHxWarps][32];
     __shared__ int s_n[kHxWarps][32];
     __shared__ int s_part[kHxWarps];
     __shared__ float s_rc[NT];
+    __shared__ float4 s_ax[kHxWarps][32];   // staged column: ia_hi, ia_lo, a, ofr*ia - zbf
+    __shared__ int s_col[kHxWarps][32];     // staged column index iy * nx + ix
+    __shared__ int2 s_kr[kHxWarps][32];     // voxel range [kmin, kmax] its rows reach
+    __shared__ int s_k0[kHxWarps][32];      // lowest row boundary K + f
+    __shared__ float s_f0[kHxWarps][32];
+    __shared__ float s_xw[kHxWarps][64];    // z-window of the column being profiled
     extern __shared__ float4 s_dyn4[];
     float *s_p = reinterpret_cast<float *>(s_dyn4);  // [warp][32][PS] profiles; later [warp][NT][32] partial sums
+    int *s_pre = reinterpret_cast<int *>(s_p + kHxWarps * 32 * PS);  // [nmax + 1] wedge columns before march index a
+    int *s_lo = s_pre + max(G.nx, G.ny) + 1;                          // [nmax] first wedge column at march index a
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nb = (G.ns + 31) >> 5;
     const int k = blockIdx.x / nb;
@@ -233,7 +239,7 @@ __global__ void __launch_bounds__(kHxWarps * 32) fp_helix_kernel(FanDev G, Helix
         const int ls = min(count_le(e, t), 31);
         const int c = col + ls;
         int cf = 1 << 20, cnt = 0;
-        if (lane < n) {  // column role: footprint weights and axial profile of one column
+        if (lane < n) {  // column role: footprint weights and axial parameters of one column
             const int bc = s_lo[c] + (t - s_pre[c]);
             const int ix = M.col ? c : bc, iy = M.col ? bc : c;
             const int tx = ix / kTile, ty = iy / kTile;
@@ -250,47 +256,94 @@ __global__ void __launch_bounds__(kHxWarps * 32) fp_helix_kernel(FanDev G, Helix
                 Fp = Fn;
             }
             cf = F.n + j0 - s0;
-            // axial profile: row r covers voxel coordinates between its two boundaries
+            // axial parameters; the lowest and highest row boundaries give the voxel range
             const float4 X = __ldg(&H.tile_ax[(size_t)v * (G.ntx * G.nty) + ty * G.ntx + tx]);
             const ColumnAxial C = column_axial(H, A, X, cs.x, cs.y, ox, oy);
-            const float a = C.a_hi + C.a_lo;
             const float cz = fmaf(H.ofr, C.ia_hi + C.ia_lo, -zb.y);
-            const float *xc = (MODE == FP_ONES_W) ? x : x + ((size_t)iy * G.nx + ix) * nz;
-            int Kl;
-            float fl;
-            row_boundary(-0.5f - H.ct0i, C.ia_hi, C.ia_lo, zb.x, cz, nz, Kl, fl);
-            float *pl = sp + lane * PS;
-#pragma unroll 2
-            for (int r = 0; r < NT; r++) {
-                if (r < nt) {
-                    int Kh;
-                    float fh;
-                    row_boundary((float)r + 0.5f - H.ct0i, C.ia_hi, C.ia_lo, zb.x, cz, nz, Kh, fh);
-                    float sacc = 0.0f;
-                    if (Kh >= 0 && Kl < nz) {
-                        const int k0 = Kl < 0 ? 0 : Kl, k1 = Kh >= nz ? nz - 1 : Kh;
-                        const float f0 = Kl < 0 ? 0.0f : fl, f1 = Kh >= nz ? 1.0f : fh;
-                        if (MODE == FP_ONES_W) {
-                            sacc = (float)(k1 - k0) + (f1 - f0);
-                        } else if (k0 == k1) {
-                            sacc = __ldg(&xc[k0]) * (f1 - f0);
-                        } else {
-                            sacc = __ldg(&xc[k0]) * (1.0f - f0);
-                            for (int kk = k0 + 1; kk < k1; kk++) sacc += __ldg(&xc[kk]);
-                            sacc = fmaf(__ldg(&xc[k1]), f1, sacc);
-                        }
-                    }
-                    pl[r] = a * sacc;
-                    Kl = Kh;
-                    fl = fh;
-                } else {
-                    pl[r] = 0.0f;
-                }
-            }
+            int K0, K1;
+            float f0, f1;
+            row_boundary(-0.5f - H.ct0i, C.ia_hi, C.ia_lo, zb.x, cz, nz, K0, f0);
+            row_boundary((float)nt - 0.5f - H.ct0i, C.ia_hi, C.ia_lo, zb.x, cz, nz, K1, f1);
+            s_ax[warp][lane] = make_float4(C.ia_hi, C.ia_lo, C.a_hi + C.a_lo, cz);
+            s_col[warp][lane] = iy * G.nx + ix;
+            s_kr[warp][lane] = make_int2(max(K0, 0), min(K1, nz - 1));
+            s_k0[warp][lane] = K0;
+            s_f0[warp][lane] = f0;
         }
         scf[lane] = cf;
         sns[lane] = cnt;
         __syncwarp();
+        // axial profiles of the staged columns: the warp loads each column's z-window
+        // (coalesced, one column ahead) into shared memory and lane r forms row r:
+        // p_r = a * sum_k x_k |[k, k+1] ∩ [z(r - 1/2), z(r + 1/2)]|
+        {
+            float xn0 = 0.0f, xn1 = 0.0f;
+            auto fetch = [&](int l, float &v0, float &v1) {
+                const int2 kr = s_kr[warp][l];
+                const float *xc = x + (size_t)s_col[warp][l] * nz;
+                const int k0 = kr.x + lane, k1 = kr.x + 32 + lane;
+                v0 = (k0 <= kr.y) ? __ldg(&xc[k0]) : 0.0f;
+                v1 = (k1 <= kr.y) ? __ldg(&xc[k1]) : 0.0f;
+            };
+            if (MODE != FP_ONES_W && n > 0) fetch(0, xn0, xn1);
+            for (int l = 0; l < n; l++) {
+                const float xc0 = xn0, xc1 = xn1;
+                if (MODE != FP_ONES_W && l + 1 < n) fetch(l + 1, xn0, xn1);
+                const float4 P = s_ax[warp][l];
+                const int2 kr = s_kr[warp][l];
+                float *pl = sp + l * PS;
+                if (MODE != FP_ONES_W) {
+                    s_xw[warp][lane] = xc0;
+                    s_xw[warp][32 + lane] = xc1;
+                }
+                __syncwarp();
+                int Kc = s_k0[warp][l];
+                float fc = s_f0[warp][l];
+                const float *xw = s_xw[warp] - kr.x;
+#pragma unroll
+                for (int r0 = 0; r0 < NT; r0 += 32) {
+                    const int r = r0 + lane;
+                    int Kh;
+                    float fh;
+                    row_boundary((float)r + 0.5f - H.ct0i, P.x, P.y, zb.x, P.w, nz, Kh, fh);
+                    int Kl = __shfl_up_sync(kFull, Kh, 1);
+                    float fl = __shfl_up_sync(kFull, fh, 1);
+                    if (lane == 0) {
+                        Kl = Kc;
+                        fl = fc;
+                    }
+                    Kc = __shfl_sync(kFull, Kh, 31);
+                    fc = __shfl_sync(kFull, fh, 31);
+                    float sacc = 0.0f;
+                    if (r < nt && Kh >= 0 && Kl < nz) {
+                        const int k0 = max(Kl, 0), k1 = min(Kh, nz - 1);
+                        const float g0 = Kl < 0 ? 0.0f : fl, g1 = Kh >= nz ? 1.0f : fh;
+                        if (MODE == FP_ONES_W) {
+                            sacc = (float)(k1 - k0) + (g1 - g0);
+                        } else if (k1 - kr.x < 64) {
+                            if (k0 == k1) {
+                                sacc = xw[k0] * (g1 - g0);
+                            } else {
+                                sacc = xw[k0] * (1.0f - g0);
+                                for (int kk = k0 + 1; kk < k1; kk++) sacc += xw[kk];
+                                sacc = fmaf(xw[k1], g1, sacc);
+                            }
+                        } else {  // a row beyond the staged 64-voxel window
+                            const float *xg = x + (size_t)s_col[warp][l] * nz;
+                            if (k0 == k1) {
+                                sacc = __ldg(&xg[k0]) * (g1 - g0);
+                            } else {
+                                sacc = __ldg(&xg[k0]) * (1.0f - g0);
+                                for (int kk = k0 + 1; kk < k1; kk++) sacc += __ldg(&xg[kk]);
+                                sacc = fmaf(__ldg(&xg[k1]), g1, sacc);
+                            }
+                        }
+                    }
+                    if (r < NT) pl[r] = P.z * sacc;
+                }
+                __syncwarp();
+            }
+        }
         // cell role: add weight x profile of every staged column this lane's wedge crosses
         const int lmax = __shfl_sync(kFull, ls, n - 1);
         for (int l = 0; l <= lmax; l++) {
@@ -659,13 +712,21 @@ cudaError_t fp_helix_dispatch(const ct_geom *g, const float *x, const int *views
     const HelixDev &H = g->hx;
     const unsigned blocks = (unsigned)nviews * (unsigned)((G.ns + 31) / 32);
     const int nt = H.nt;
-#define CT_FP_HX(NTV)                                                                                   \
-    fp_helix_kernel<MODE, NTV><<<blocks, kHxWarps * 32, sizeof(float) * kHxWarps * 32 * (NTV + 4), st>>>( \
-        G, H, x, views, nviews, out, y, w)
+    const int nmax = G.nx > G.ny ? G.nx : G.ny;
+#define CT_FP_HX(NTV)                                                                                       \
+    fp_helix_kernel<MODE, NTV><<<blocks, kHxWarps * 32,                                                     \
+                                 sizeof(float) * kHxWarps * 32 * (NTV + 4) + sizeof(int) * (2 * nmax + 1), \
+                                 st>>>(G, H, x, views, nviews, out, y, w)
     if (nt <= 8) CT_FP_HX(8);
     else if (nt <= 16) CT_FP_HX(16);
     else if (nt <= 32) CT_FP_HX(32);
-    else CT_FP_HX(64);
+    else {
+        const size_t dyn = sizeof(float) * kHxWarps * 32 * (64 + 4) + sizeof(int) * (2 * nmax + 1);
+        cudaError_t e = cudaFuncSetAttribute(fp_helix_kernel<MODE, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)dyn);
+        if (e != cudaSuccess) return e;
+        CT_FP_HX(64);
+    }
 #undef CT_FP_HX
     return cudaGetLastError();
 }
