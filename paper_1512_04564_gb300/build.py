@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "libct.so")
-SOURCES = ["geom.cu", "projectors.cu", "matrix.cu", "reg2d.cu", "solve.cu", "noalloc.cu", "fbp.cu", "batched.cu", "tune.cu", "helical.cu"]
+SOURCES = ["geom.cu", "projectors.cu", "matrix.cu", "reg2d.cu", "solve.cu", "noalloc.cu", "fbp.cu", "batched.cu", "tune.cu",
+           "helical.cu", "unet.cu"]
 HEADERS = ["ct_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -61,6 +61,13 @@ class ct_solve_report(ctypes.Structure):
     ]
 
 
+class ct_unet_desc(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int), ("base_channels", ctypes.c_int), ("height", ctypes.c_int), ("width", ctypes.c_int),
+        ("max_batch", ctypes.c_int), ("in_scale", ctypes.c_float), ("seed", ctypes.c_ulonglong),
+    ]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
@@ -81,6 +88,18 @@ def _load():
         "ct_relaxed_oslalm_solve_batched": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                             ctypes.POINTER(ct_solve_params), ctypes.POINTER(vp), cint,
                                             ctypes.POINTER(ct_solve_report), vp],
+        "ct_gemm_bf16": [vp, vp, vp, cint, cint, cint, vp, vp],
+        "ct_conv3x3_bf16": [vp, cint, cint, vp, cint, vp, vp, vp, cint, cint, cint, cint, vp, vp],
+        "ct_conv3x3_bf16_dgrad": [vp, cint, vp, vp, cint, cint, vp, cint, vp, vp, cint, cint, cint, vp, vp],
+        "ct_conv3x3_bf16_wgrad": [vp, cint, cint, vp, cint, vp, cint, vp, vp, vp, ctypes.c_longlong, cint, cint, cint,
+                                  vp, vp],
+        "ct_unet_create": [ctypes.POINTER(ct_unet_desc), ctypes.POINTER(vp)],
+        "ct_unet_get_params": [vp, vp, cint],
+        "ct_unet_set_params": [vp, vp],
+        "ct_unet_forward": [vp, vp, vp, cint, vp],
+        "ct_unet_backward": [vp, vp, cint, vp],
+        "ct_unet_adam": [vp, cfl, cfl, cfl, cfl, cfl, vp],
+        "ct_unet_status": [vp],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -91,13 +110,22 @@ def _load():
     lib.ct_last_error.argtypes = []
     lib.ct_last_error.restype = ctypes.c_char_p
     lib.ct_version.restype = cint
+    lib.ct_unet_destroy.argtypes = [vp]
+    lib.ct_unet_destroy.restype = None
+    lib.ct_unet_num_params.argtypes = [vp]
+    lib.ct_unet_num_params.restype = ctypes.c_longlong
+    lib.ct_conv3x3_wgrad_workspace.argtypes = [cint, cint, cint, cint, cint]
+    lib.ct_conv3x3_wgrad_workspace.restype = ctypes.c_longlong
     return lib
 
 
 _lib = _load()
 EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_geom_precompute", "ct_geom_autotune", "ct_forward", "ct_back", "ct_sqs_diag",
             "ct_sqs_diag_noalloc", "ct_fbp", "ct_reg_gradient", "ct_relaxed_oslalm_solve",
-            "ct_relaxed_oslalm_solve_batched", "ct_last_error", "ct_version")
+            "ct_relaxed_oslalm_solve_batched", "ct_last_error", "ct_version", "ct_gemm_bf16", "ct_conv3x3_bf16",
+            "ct_conv3x3_bf16_dgrad", "ct_conv3x3_wgrad_workspace", "ct_conv3x3_bf16_wgrad", "ct_unet_create",
+            "ct_unet_destroy", "ct_unet_num_params", "ct_unet_get_params", "ct_unet_set_params", "ct_unet_forward",
+            "ct_unet_backward", "ct_unet_adam", "ct_unet_status")
 
 
 class CTError(RuntimeError):
@@ -111,11 +139,11 @@ def _check(st: int):
         raise CTError(st, _lib.ct_last_error().decode())
 
 
-def _ptr(t: torch.Tensor | None, name: str, numel: int | None = None):
+def _ptr(t: torch.Tensor | None, name: str, numel: int | None = None, dtype=torch.float32):
     if t is None:
         return None
-    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
-        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} CUDA tensor")
     if numel is not None and t.numel() != numel:
         raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
     return ctypes.c_void_p(t.data_ptr())
@@ -351,3 +379,148 @@ def ct_relaxed_oslalm_solve_batched(geoms, ys, ws, xs, params: list[dict], strea
 
 def version() -> int:
     return int(_lib.ct_version())
+
+
+def _err_flag(err):
+    if err is None:
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    return err
+
+
+def ct_gemm_bf16(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None, err=None, stream=None):
+    """Tensor-core GEMM C = A B^T (A [M][K], B [N][K] bfloat16; C [M][N] float32)."""
+    if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16:
+        raise TypeError("A and B must be bfloat16")
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("A and B disagree on K")
+    if C is None:
+        C = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    err = _err_flag(err)
+    _check(_lib.ct_gemm_bf16(_ptr(A, "A", M * K, torch.bfloat16), _ptr(B, "B", N * K, torch.bfloat16),
+                             _ptr(C, "C", M * N), M, N, K, _ptr(err, "err", 1, torch.int32), _stream(stream)))
+    return C, err
+
+
+def _bf(t, name, numel):
+    return _ptr(t, name, numel, torch.bfloat16)
+
+
+def ct_conv3x3_bf16(in1, c1, up1, in2, c2, w, bias, out, B, H, W, co, err=None, stream=None):
+    """out = bf16(relu(conv3x3(cat(up?(in1), in2)) + bias)); NHWC bfloat16 tensors."""
+    h1, w1 = (H // 2, W // 2) if up1 else (H, W)
+    err = _err_flag(err)
+    _check(_lib.ct_conv3x3_bf16(_bf(in1, "in1", B * h1 * w1 * c1), c1, int(bool(up1)),
+                                _bf(in2, "in2", B * H * W * c2) if c2 else None, c2,
+                                _bf(w, "w", co * 9 * (c1 + c2)), _ptr(bias, "bias", co),
+                                _bf(out, "out", B * H * W * co), B, H, W, co, _ptr(err, "err", 1, torch.int32),
+                                _stream(stream)))
+    return out, err
+
+
+def ct_conv3x3_bf16_dgrad(gout, co, wt, m1, c1, up1, m2, c2, g1, g2, B, H, W, err=None, stream=None):
+    h1, w1 = (H // 2, W // 2) if up1 else (H, W)
+    err = _err_flag(err)
+    _check(_lib.ct_conv3x3_bf16_dgrad(_bf(gout, "gout", B * H * W * co), co, _bf(wt, "wt", co * 9 * (c1 + c2)),
+                                      _bf(m1, "m1", B * h1 * w1 * c1), c1, int(bool(up1)),
+                                      _bf(m2, "m2", B * H * W * c2) if c2 else None, c2,
+                                      _bf(g1, "g1", B * H * W * c1), _bf(g2, "g2", B * H * W * c2) if c2 else None,
+                                      B, H, W, _ptr(err, "err", 1, torch.int32), _stream(stream)))
+    return g1, g2, err
+
+
+def ct_conv3x3_wgrad_workspace(B, H, W, ci, co) -> int:
+    return int(_lib.ct_conv3x3_wgrad_workspace(B, H, W, ci, co))
+
+
+def ct_conv3x3_bf16_wgrad(in1, c1, up1, in2, c2, gout, co, dw, db, B, H, W, work=None, err=None, stream=None):
+    h1, w1 = (H // 2, W // 2) if up1 else (H, W)
+    nwork = ct_conv3x3_wgrad_workspace(B, H, W, c1 + c2, co)
+    if work is None:
+        work = torch.empty(max(nwork, 1), dtype=torch.float32, device="cuda")
+    err = _err_flag(err)
+    _check(_lib.ct_conv3x3_bf16_wgrad(_bf(in1, "in1", B * h1 * w1 * c1), c1, int(bool(up1)),
+                                      _bf(in2, "in2", B * H * W * c2) if c2 else None, c2,
+                                      _bf(gout, "gout", B * H * W * co), co, _ptr(dw, "dw", co * 9 * (c1 + c2)),
+                                      _ptr(db, "db", co), _ptr(work, "work"), work.numel(), B, H, W,
+                                      _ptr(err, "err", 1, torch.int32), _stream(stream)))
+    return dw, db, err
+
+
+class UNet:
+    """Owner of a ``ct_unet`` handle (ct_unet_create / ct_unet_destroy)."""
+
+    def __init__(self, *, levels=4, base_channels=32, height=256, width=256, max_batch=8, in_scale=50.0, seed=0):
+        d = ct_unet_desc(levels, base_channels, height, width, max_batch, in_scale, seed)
+        h = ctypes.c_void_p()
+        _check(_lib.ct_unet_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self.levels, self.base_channels, self.height, self.width = levels, base_channels, height, width
+        self.max_batch, self.in_scale = max_batch, in_scale
+
+    @property
+    def num_params(self) -> int:
+        return int(_lib.ct_unet_num_params(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.ct_unet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ct_unet_num_params(net: UNet) -> int:
+    return net.num_params
+
+
+def ct_unet_get_params(net: UNet, which: str = "params"):
+    import numpy as np
+
+    out = np.empty(net.num_params, dtype=np.float32)
+    _check(_lib.ct_unet_get_params(net.handle, out.ctypes.data_as(ctypes.c_void_p), 0 if which == "params" else 1))
+    return out
+
+
+def ct_unet_set_params(net: UNet, params):
+    import numpy as np
+
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.size != net.num_params:
+        raise ValueError(f"expected {net.num_params} parameters, got {a.size}")
+    _check(_lib.ct_unet_set_params(net.handle, a.ctypes.data_as(ctypes.c_void_p)))
+
+
+def ct_unet_forward(net: UNet, x: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    B = x.shape[0]
+    if y is None:
+        y = torch.empty_like(x)
+    n = B * net.height * net.width
+    _check(_lib.ct_unet_forward(net.handle, _ptr(x, "x", n), _ptr(y, "y", n), B, _stream(stream)))
+    return y
+
+
+def ct_unet_backward(net: UNet, gy: torch.Tensor, stream=None):
+    B = gy.shape[0]
+    _check(_lib.ct_unet_backward(net.handle, _ptr(gy, "gy", B * net.height * net.width), B, _stream(stream)))
+
+
+def ct_unet_adam(net: UNet, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
+    _check(_lib.ct_unet_adam(net.handle, lr, beta1, beta2, eps, weight_decay, _stream(stream)))
+
+
+def ct_unet_status(net: UNet):
+    _check(_lib.ct_unet_status(net.handle))
+
+
+def ct_unet_create(**kw) -> UNet:
+    return UNet(**kw)
+
+
+def ct_unet_destroy(net: UNet):
+    net.close()
