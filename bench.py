@@ -68,6 +68,11 @@ def parse():
                     help="only time one subset forward and back projection (profiling mode)")
     ap.add_argument("--views", type=int, default=None,
                     help="override the number of views over 360 deg (profiling smaller cases)")
+    ap.add_argument("--ws-train", type=int, default=2000, help="warm-start workload: training problems")
+    ap.add_argument("--ws-eval", type=int, default=200, help="warm-start workload: held-out problems")
+    ap.add_argument("--ws-epochs", type=int, default=12)
+    ap.add_argument("--ws-batch", type=int, default=16)
+    ap.add_argument("--ws-xstar-iters", type=int, default=400, help="M = 1 iterations of the held-out x*")
     ap.add_argument("--xstar-iters-helix", type=int, default=300,
                     help="M = 1 iterations (after a 10-iteration M = 12 warm start) for the helical x*")
     return ap.parse_args()
@@ -472,6 +477,144 @@ def run_helix(args):
     return 0
 
 
+def unet_flops(levels, base, H, W):
+    """FLOPs of one U-Net forward per image (2 per multiply-add of the 3x3 layers and the 1x1 output)."""
+    ch = [base << l for l in range(levels)]
+    f = 0
+    for l in range(levels):
+        hw = (H >> l) * (W >> l)
+        f += 2 * hw * 9 * ((1 if l == 0 else ch[l - 1]) * ch[l] + ch[l] * ch[l])
+    for l in range(levels - 2, -1, -1):
+        hw = (H >> l) * (W >> l)
+        f += 2 * hw * 9 * ((ch[l + 1] + ch[l]) * ch[l] + ch[l] * ch[l])
+    return f + 2 * H * W * base
+
+
+def unet_roofline(ct, net, levels, base, H, W, B, peaks, clock_mhz):
+    """Device time of one U-Net forward and one forward + backward at batch B (CUDA events), against the
+    measured BF16 dense peak; the largest tensor-core layer alone is timed with the single-layer entry."""
+    import torch
+
+    x = torch.rand(B, H, W, device="cuda") * 0.02
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps * 1e-3
+
+    gy = torch.randn(B, H, W, device="cuda")
+    t_fwd = timed(lambda: ct.ct_unet_forward(net, x))
+
+    def step():
+        ct.ct_unet_forward(net, x)
+        ct.ct_unet_backward(net, gy)
+
+    t_step = timed(step)
+    f_fwd = unet_flops(levels, base, H, W) * B
+    f_step = 3 * f_fwd  # forward, input gradients, weight gradients
+    # the largest layer: decoder level 0, conv a (upsampled 2 C0 + skip C0 -> C0) at full resolution
+    c1, c2, co = 2 * base, base, base
+    a1 = torch.randn(B, H // 2, W // 2, c1, device="cuda").to(torch.bfloat16)
+    a2 = torch.randn(B, H, W, c2, device="cuda").to(torch.bfloat16)
+    wl = (torch.randn(co, 9 * (c1 + c2), device="cuda") * 0.05).to(torch.bfloat16)
+    bl = torch.zeros(co, device="cuda")
+    out = torch.empty(B, H, W, co, dtype=torch.bfloat16, device="cuda")
+    t_layer = timed(lambda: ct.ct_conv3x3_bf16(a1, c1, 1, a2, c2, wl, bl, out, B, H, W, co))
+    f_layer = 2 * B * H * W * 9 * (c1 + c2) * co
+    peak = peaks.get("bf16_tflops", 1900.0)
+    k = {"unet_forward": {"ms": t_fwd * 1e3, "tflops": f_fwd / t_fwd / 1e12},
+         "unet_train_step": {"ms": t_step * 1e3, "tflops": f_step / t_step / 1e12},
+         "conv3x3_dec0a_forward": {"ms": t_layer * 1e3, "tflops": f_layer / t_layer / 1e12}}
+    return {"bound": "tensor", "kernel": f"U-Net forward (batch {B}, {H}x{W}, tcgen05 BF16 convs)",
+            "achieved": k["unet_forward"]["tflops"], "peak": peak, "unit": "TFLOP/s",
+            "frac": k["unet_forward"]["tflops"] / peak, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured, cuBLAS burst)" if peaks else "fallback 1900",
+            "kernels": k}
+
+
+def run_warmstart(args):
+    """Learned warm start: 2000 generated 256x256 problems (FBP -> x*), training on the GPU, and iterations /
+    seconds of relaxed OS-LALM to 1 HU from the warm start vs the FBP start on 200 held-out problems."""
+    n_train, n_eval = args.ws_train, args.ws_eval
+    g = synth.warmstart_geometry(256)
+    t0 = time.perf_counter()
+    seeds = list(range(n_train)) + list(range(100_000, 100_000 + n_eval))
+    y_np, w_np = synth.warmstart.problems(seeds, g, n_gauss=1, processes=min(16, os.cpu_count() or 1))
+    t_data = time.perf_counter() - t0
+    import torch
+
+    from paper_1512_04564_gb300 import ct, warmstart
+
+    torch.cuda.set_device(0)
+    G = ct.Geometry.from_fan(g)
+    mat = ct.ct_geom_precompute(G)
+    ys, ws = torch.from_numpy(y_np).cuda(), torch.from_numpy(w_np).cuda()
+    del y_np, w_np
+    cfg = synth.fan2d_512()
+    beta, delta, hu = cfg.beta_per_mm, cfg.delta, cfg.hu_per_unit
+    M = args.M or 10  # the workload names M = 20; relaxed OS-LALM uses half the subsets (Sec. III-A)
+    t0 = time.perf_counter()
+    xs_train = warmstart.solve_xstar(G, ys[:n_train], ws[:n_train], beta, delta, os_iters=15, m1_iters=40, M=M)
+    xs_eval = warmstart.solve_xstar(G, ys[n_train:], ws[n_train:], beta, delta, os_iters=20,
+                                    m1_iters=args.ws_xstar_iters, M=M)
+    torch.cuda.synchronize()
+    t_xstar = time.perf_counter() - t0
+    kkt = [kkt_rms_hu(ct, G, g, ys[n_train + i], ws[n_train + i], xs_eval[i], beta, delta, cfg.potential, hu)
+           for i in range(min(4, n_eval))]
+    # the training targets' distance to a converged x* (on the first problems of the training set)
+    ref = warmstart.solve_xstar(G, ys[:4], ws[:4], beta, delta, os_iters=20, m1_iters=args.ws_xstar_iters, M=M)
+    X = (torch.arange(g.nx, device="cuda") - (g.nx - 1) / 2.0) * g.dx
+    mask = (X[None, :] ** 2 + X[:, None] ** 2) <= g.fov_radius() ** 2
+    tgt_err = [float(((xs_train[i] - ref[i])[mask].double().pow(2).mean().sqrt()) * hu) for i in range(4)]
+    fbp = warmstart.fbp_images(G, ys)
+    net = ct.UNet(levels=4, base_channels=32, height=256, width=256, max_batch=args.ws_batch, in_scale=1 / 0.02,
+                  seed=0)
+    t0 = time.perf_counter()
+    hist = warmstart.train(net, G, fbp[:n_train], xs_train, ys[:n_train], ws[:n_train], epochs=args.ws_epochs,
+                           batch=args.ws_batch, lr=2e-3, lr_min=5e-5, lam_dc=1e-4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = warmstart.evaluate(net, G, ys[n_train:], ws[n_train:], xs_eval, beta=beta, delta=delta, M=M, n_iter=40)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    clock_info = clocks.stop()
+    roof = unet_roofline(ct, net, 4, 32, 256, 256, args.ws_batch, peaks, clock_info.get("sm_mhz"))
+    res.pop("per_problem", None)
+    line = {
+        "metric": METRIC + ", learned warm start", "value": res["warm_seconds"]["mean"], "unit": UNIT, "n_gpus": 1,
+        "steps": n_eval, "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 U-Net / f32 solver", "data": "synthetic",
+        "config": {"workload": "warmstart256", "image": [256, 256], "bins": g.ns, "views": g.na,
+                   "train_problems": n_train, "eval_problems": n_eval, "I0": [2e4, 2e5], "M": M, "M_named": 20,
+                   "alpha": 1.999, "unet": {"levels": 4, "base_channels": 32, "params": net.num_params},
+                   "epochs": args.ws_epochs, "batch": args.ws_batch, "loss": "MSE (water units) + 1e-4 DC",
+                   "xstar_eval": f"20 its M={M} + {args.ws_xstar_iters} its M=1 from FBP",
+                   "xstar_train": f"15 its M={M} + 40 its M=1 from FBP",
+                   "xstar_kkt_rms_hu": kkt, "train_target_rmsd_to_xstar_hu": tgt_err,
+                   "resident_matrix_bytes": mat},
+        "plain_start_seconds": res["plain_seconds"]["mean"],
+        "results": res,
+        "train_loss_by_epoch": [round(h, 6) for h in hist],
+        "timings_s": {"data_generation": round(t_data, 1), "xstar": round(t_xstar, 1), "training": round(t_train, 1)},
+        "roofline": roof,
+        "clocks": clock_info,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -511,6 +654,8 @@ def main():
         return run_batch(args)
     if args.workload.startswith("helix"):
         return run_helix(args)
+    if args.workload == "warmstart256":
+        return run_warmstart(args)
 
     import torch
 

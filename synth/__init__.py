@@ -12,7 +12,8 @@ caller's seed.
 """
 
 from .configs import (FanArcGeometry, HelicalConeGeometry, ScanConfig, fan2d_128, fan2d_512, helix3d_64,
-                      helix3d_512, config_by_name)
+                      helix3d_512, config_by_name, warmstart_geometry)
+from . import warmstart
 from .phantom import (
     Ellipse,
     random_ellipses_cfg1,
@@ -47,6 +48,8 @@ __all__ = [
     "helical_line_integrals",
     "helical_line_integrals_sampled",
     "phantom_of",
+    "warmstart_geometry",
+    "warmstart",
     "fan2d_128",
     "fan2d_512",
     "config_by_name",

@@ -242,3 +242,14 @@ def helix3d_64(seed: int = 0) -> ScanConfig:
 def config_by_name(name: str, seed: int = 0) -> ScanConfig:
     return {"fan2d_128": fan2d_128, "fan2d_512": fan2d_512, "helix3d_64": helix3d_64,
             "helix3d_512": helix3d_512}[name](seed)
+
+
+def warmstart_geometry(n: int = 256, pixel: float | None = None) -> FanArcGeometry:
+    """Fan-beam scan of the learned-warm-start workload: n x n pixels of 0.98 * 512 / n mm by default
+    (the ~500 mm field of the clinical geometry), 444 * n / 256 bins of 1.0239 * 888 / 444 mm (the
+    888-channel arc at half sampling; with a smaller pixel the arc shrinks with the field), 492 * n / 256
+    views.  n = 256 is the workload; smaller n with pixel = 1.96 gives its reduced-field test version."""
+    px = 0.98 * 512 / n if pixel is None else pixel
+    ns = 444 * n // 256
+    return FanArcGeometry(nx=n, ny=n, dx=px, dy=px, ns=ns, ds=1.0239 * 888 / 444, na=492 * n // 256, dso=541.0,
+                          dsd=949.0)
