@@ -542,6 +542,21 @@ def unet_roofline(ct, net, levels, base, H, W, B, peaks, clock_mhz):
 def run_warmstart(args):
     """Learned warm start: 2000 generated 256x256 problems (FBP -> x*), training on the GPU, and iterations /
     seconds of relaxed OS-LALM to 1 HU from the warm start vs the FBP start on 200 held-out problems."""
+    if args.kernels_only:
+        import torch
+
+        from paper_1512_04564_gb300 import ct
+
+        torch.cuda.set_device(0)
+        net = ct.UNet(levels=4, base_channels=32, height=256, width=256, max_batch=args.ws_batch, in_scale=50.0)
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except OSError:
+            pass
+        roof = unet_roofline(ct, net, 4, 32, 256, 256, args.ws_batch, peaks, None)
+        print(json.dumps({"mode": "kernels-only", "workload": "warmstart256", "roofline": roof}), flush=True)
+        return 0
     n_train, n_eval = args.ws_train, args.ws_eval
     g = synth.warmstart_geometry(256)
     t0 = time.perf_counter()
