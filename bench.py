@@ -68,6 +68,8 @@ def parse():
                     help="only time one subset forward and back projection (profiling mode)")
     ap.add_argument("--views", type=int, default=None,
                     help="override the number of views over 360 deg (profiling smaller cases)")
+    ap.add_argument("--study", action="store_true",
+                    help="relaxed (alpha=1.999, M) vs unrelaxed (alpha=1, 2M) subsets, Algorithm 2 and fixed rho")
     ap.add_argument("--ws-train", type=int, default=2000, help="warm-start workload: training problems")
     ap.add_argument("--ws-eval", type=int, default=200, help="warm-start workload: held-out problems")
     ap.add_argument("--ws-epochs", type=int, default=12)
@@ -720,6 +722,8 @@ def main():
     ct.ct_relaxed_oslalm_solve(G, y, w, xstar, M=1, n_iter=args.xstar_iters, alpha=1.999, **common)
     t_xstar = time.perf_counter() - t0
     kkt = kkt_rms_hu(ct, G, g, y, w, xstar, beta, delta, cfg.potential, hu)
+    if args.study:
+        return run_study(args, ct, G, g, y, w, xstar, common, hu, kkt, cfg)
 
     fbp0 = args.x0 == "fbp"
 
@@ -818,6 +822,44 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def run_study(args, ct, G, g, y, w, xstar, common, hu, kkt, cfg):
+    """The paper's comparisons on the synthetic workload, each as iterations and device seconds to 1 HU of x*
+    from the FBP start: relaxed (alpha = 1.999) with M subsets against unrelaxed (alpha = 1) with M and 2M
+    (Sec. IV: the relaxed method matches the unrelaxed one with about twice the subsets); the proposed
+    relaxation (Algorithm 1) against the simple one (Algorithm 2), with continuation and with fixed rho = 0.05;
+    and the supplement's majorizer study (maximum-curvature D_R; D_L scaled by 0.5 .. 4)."""
+    import torch
+
+    n_iter = args.n_iter or 40
+
+    def run(M, alpha, algorithm="proposed", continuation=True, rho_fixed=0.0, curvature="huber", dl_scale=1.0):
+        x = torch.zeros(g.ny, g.nx, device="cuda")
+        r = ct.ct_relaxed_oslalm_solve(G, y, w, x, M=M, n_iter=n_iter, alpha=alpha, algorithm=algorithm,
+                                       continuation=continuation, rho_fixed=rho_fixed, x_ref=xstar, hu_per_unit=hu,
+                                       init_fbp=True, curvature=curvature, dl_scale=dl_scale, **common)
+        tr = r["rmsd_trace_hu"]
+        hit = next((i + 1 for i, v in enumerate(tr) if v <= args.tol_hu), None)
+        return {"M": M, "alpha": alpha, "algorithm": algorithm,
+                "rho": "continuation" if continuation else rho_fixed, "curvature": curvature, "dl_scale": dl_scale,
+                "iters_to_1hu": hit,
+                "seconds_to_1hu": r["seconds_to_tol"] if r["seconds_to_tol"] > 0 else None,
+                "min_rmsd_hu": round(min(tr), 4), "rmsd_trace_hu": [round(v, 3) for v in tr]}
+
+    for _ in range(2):  # warm-up of the graph path
+        run(10, 1.999)
+    pairs = [{"relaxed": run(M, 1.999), "unrelaxed": run(M, 1.0), "unrelaxed_2M": run(2 * M, 1.0)}
+             for M in (5, 10, 20)]
+    algs = [run(20, 1.999, "proposed"), run(20, 1.999, "simple"),
+            run(20, 1.999, "proposed", continuation=False, rho_fixed=0.05),
+            run(20, 1.999, "simple", continuation=False, rho_fixed=0.05)]
+    majorizers = [run(20, 1.999, curvature="max")] + [run(20, 1.999, dl_scale=k) for k in (0.5, 0.75, 2.0, 4.0)]
+    line = {"mode": "study", "workload": cfg.name, "x0": "fbp", "n_iter": n_iter, "xstar_kkt_rms_hu": kkt,
+            "relaxed_M_vs_unrelaxed_2M": pairs, "proposed_vs_simple_relaxation": algs,
+            "majorizers": majorizers}
+    print(json.dumps(line), flush=True)
     return 0
 
 

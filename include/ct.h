@@ -161,6 +161,7 @@ ct_status ct_fbp(const ct_geom *g, const float *y, float *x, int window, void *s
 
 enum { CT_POT_HYPERBOLA = 0, CT_POT_FAIR = 1, CT_POT_QUADRATIC = 2 };
 enum { CT_ALG_PROPOSED = 0, CT_ALG_SIMPLE = 1 };
+enum { CT_CURV_HUBER = 0, CT_CURV_MAX = 1 };
 
 /* Gradient and Huber-curvature SQS diagonal of the regularizer
  * R(x) = sum_i beta_i sum_n phi([C_i x]_n) (Eq. (def_reg)) over the 8
@@ -187,6 +188,9 @@ typedef struct {
     float fov_radius;   /* RMSD mask radius in mm; <= 0 selects the scan's full field of view */
     float stop_rmsd_hu; /* > 0: stop after the first iteration with RMSD <= this (needs x_ref) */
     int init_fbp;       /* 1: overwrite x_inout with the Hann-windowed FBP of y first (timed with the solve) */
+    int curvature;      /* D_R majorizer (Sec. II-B): CT_CURV_HUBER (Huber's optimal curvature, the default)
+                           or CT_CURV_MAX (the potential's maximum curvature, phi''(0) = 1) */
+    float dl_scale;     /* D_L <- dl_scale * diag(A'WA1) (supplement's majorizer study); 0 reads as 1 */
 } ct_solve_params;
 
 /* Report filled by ct_relaxed_oslalm_solve.  The two array pointers are

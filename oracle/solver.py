@@ -82,7 +82,11 @@ class PWLSProblem:
     def grad_R(self, x):
         return reg.gradient(x, self.beta, self.delta, self.potential)
 
-    def D_R(self, x):
+    def D_R(self, x, curvature: str = "huber"):
+        """SQS diagonal of R: Huber's optimal curvature omega(t) = phi'(t)/t, or the potential's maximum
+        curvature phi''(0) = 1 for every pair (Sec. II-B; the supplement compares the two)."""
+        if curvature == "max":
+            return reg.curvature(x, self.beta, self.delta, "quadratic")
         return reg.curvature(x, self.beta, self.delta, self.potential)
 
 
@@ -98,8 +102,12 @@ def relaxed_os_lalm(problem: PWLSProblem, x0: np.ndarray, M: int, alpha: float, 
                     algorithm: str = "proposed", continuation: bool = True, rho_fixed: float | None = None,
                     nonneg: bool = True, D_L: np.ndarray | None = None,
                     callback: Callable[[int, np.ndarray], None] | None = None,
-                    sub_callback: Callable[[int, np.ndarray], None] | None = None) -> np.ndarray:
+                    sub_callback: Callable[[int, np.ndarray], None] | None = None,
+                    curvature: str = "huber", dl_scale: float = 1.0) -> np.ndarray:
     """Algorithm 1 ("proposed") or Algorithm 2 ("simple") of Sec. III-A.
+
+    ``curvature`` selects the regularizer majorizer ("huber" or "max"); ``dl_scale`` multiplies
+    D_L (the supplement's study of the data-term majorizer: too small diverges, larger slows).
 
     ``callback(k, x)`` runs after each outer iteration k = 1..n_iter and
     ``sub_callback(t, x)`` after each subiteration t = 1..n_iter*M.
@@ -110,7 +118,7 @@ def relaxed_os_lalm(problem: PWLSProblem, x0: np.ndarray, M: int, alpha: float, 
         raise ValueError(algorithm)
     na = problem.proj.geom.na
     S = interleaved_subsets(na, M)
-    DL = problem.D_L() if D_L is None else D_L
+    DL = dl_scale * (problem.D_L() if D_L is None else D_L)
     rho_of = (lambda t: rho_continuation(t, alpha)) if continuation else (lambda t: float(rho_fixed))
 
     x = np.array(x0, dtype=np.float64, copy=True)
@@ -126,7 +134,7 @@ def relaxed_os_lalm(problem: PWLSProblem, x0: np.ndarray, M: int, alpha: float, 
                 s = rho * (DL * x - h) + (1.0 - rho) * g
             else:
                 s = rho * zeta + (1.0 - rho) * g
-            x = _x_step(x, s, problem.grad_R(x), rho, DL, problem.D_R(x), nonneg)
+            x = _x_step(x, s, problem.grad_R(x), rho, DL, problem.D_R(x, curvature), nonneg)
             zeta = M * problem.grad_L_subset(x, S[m])
             g_new = rho / (rho + 1.0) * (alpha * zeta + (1.0 - alpha) * g) + g / (rho + 1.0)
             if algorithm == "proposed":

@@ -380,7 +380,8 @@ extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms
             !(p->beta >= 0.0f) || p->potential < CT_POT_HYPERBOLA || p->potential > CT_POT_QUADRATIC ||
             (p->potential != CT_POT_QUADRATIC && !(p->delta > 0.0f)) ||
             (p->algorithm != CT_ALG_PROPOSED && p->algorithm != CT_ALG_SIMPLE) ||
-            (!p->continuation && !(p->rho_fixed > 0.0f))) {
+            (!p->continuation && !(p->rho_fixed > 0.0f)) ||
+            (p->curvature != CT_CURV_HUBER && p->curvature != CT_CURV_MAX) || !(p->dl_scale >= 0.0f)) {
             set_error("slice %d: invalid solver parameters", i);
             return CT_EINVAL;
         }
@@ -453,7 +454,7 @@ extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms
         B.perm = perm;
         B.sub_off = sub;
         B.rho = rho;
-        B.P = Pot{p->potential, p->potential == CT_POT_QUADRATIC ? 0.0f : 1.0f / p->delta};
+        B.P = Pot{p->potential, p->potential == CT_POT_QUADRATIC ? 0.0f : 1.0f / p->delta, p->curvature};
         B.alpha = p->alpha;
         B.beta = p->beta;
         const double R = p->fov_radius > 0.0f ? (double)p->fov_radius : g->fov_radius;
@@ -496,7 +497,8 @@ extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms
         if (p->init_fbp) CT_CUDA_TRY(launch_fbp(g, y[i], x_inout[i], CT_FBP_HANN, ws), "initial FBP");
         CT_CUDA_TRY(launch_fp(g->fan, FP_ONES_W, nullptr, g->d_views_all, g->fan.na, g->d_sino_ws, nullptr, w[i], ws),
                     "D_L forward");
-        CT_CUDA_TRY(launch_bp(g->fan, BP_PLAIN, g->d_sino_ws, g->d_views_all, g->fan.na, B.d_l, 1.0f, 0, nullptr, ws),
+        CT_CUDA_TRY(launch_bp(g->fan, BP_PLAIN, g->d_sino_ws, g->d_views_all, g->fan.na, B.d_l,
+                              p->dl_scale > 0.0f ? p->dl_scale : 1.0f, 0, nullptr, ws),
                     "D_L back");
         // rho = 1, zeta = g = M grad L_M(x), h = D_L x - zeta (last subset)
         const int M = p->M;

@@ -336,7 +336,7 @@ cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *v
 cudaError_t launch_reg_gradient(const FanDev &G, const float *x, float beta, float delta, int potential,
                                 float *grad, float *curv, cudaStream_t st);
 cudaError_t launch_reg_update(const FanDev &G, const SolveDev &S, float beta, float delta, int potential,
-                              cudaStream_t st);
+                              int maxcurv, cudaStream_t st);
 
 cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t st, bool *too_big);
 cudaError_t launch_fbp(const ct_geom *g, const float *y, float *x, int window, cudaStream_t st);
@@ -352,7 +352,7 @@ cudaError_t launch_bp_helix(const ct_geom *g, int mode, const float *sino, const
 cudaError_t launch_reg_gradient_helix(const ct_geom *g, const float *x, float beta, float delta, int potential,
                                       float *grad, float *curv, cudaStream_t st);
 cudaError_t launch_reg_update_helix(const ct_geom *g, const SolveDev &S, float beta, float delta, int potential,
-                                    cudaStream_t st);
+                                    int maxcurv, cudaStream_t st);
 cudaError_t launch_rmsd_helix(const ct_geom *g, const float *x, const float *xr, float r2max, double *partial,
                               int *counter, float *trace, int M, float hu, cudaStream_t st);
 int helix_chunk_voxels(double a_max);  // largest chunk whose magnified extent fits the row buffer, 0 if none
@@ -376,6 +376,7 @@ ct_status stage_views(const ct_geom *g, const int *views, int nviews, const int 
 struct Pot {
     int kind;
     float inv_delta;
+    int maxcurv;  // 1: the SQS curvature is the potential's maximum curvature (1) instead of Huber's omega(t)
     // phi'(t) and omega(t) = phi'(t)/t
     __device__ __forceinline__ void eval(float t, float &dphi, float &omega) const
     {
@@ -417,14 +418,14 @@ __device__ __forceinline__ void reg_terms(const FanDev &G, const float *__restri
             float d, o;
             P.eval(xj - ld_img<COHERENT>(&x[(size_t)fy * G.nx + fx]), d, o);
             grad = fmaf(bi, d, grad);
-            curv = fmaf(2.0f * bi, o, curv);
+            curv = fmaf(2.0f * bi, P.maxcurv ? 1.0f : o, curv);
         }
         const int bx = ix - ddx[i], by = iy - ddy[i];
         if (bx >= 0 && bx < G.nx && by >= 0 && by < G.ny) {
             float d, o;
             P.eval(ld_img<COHERENT>(&x[(size_t)by * G.nx + bx]) - xj, d, o);
             grad = fmaf(-bi, d, grad);
-            curv = fmaf(2.0f * bi, o, curv);
+            curv = fmaf(2.0f * bi, P.maxcurv ? 1.0f : o, curv);
         }
     }
 }

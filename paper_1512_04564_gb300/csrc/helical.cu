@@ -570,7 +570,7 @@ __device__ __forceinline__ void reg_terms3(const float *__restrict__ x, const Vo
                 float d, o;
                 P.eval(xj - __ldg(&x[j + dx * D.sx + dy * D.sy + dz * D.sz]), d, o);
                 grad = fmaf(bi, d, grad);
-                curv = fmaf(2.0f * bi, o, curv);
+                curv = fmaf(2.0f * bi, P.maxcurv ? 1.0f : o, curv);
             }
 }
 
@@ -702,7 +702,10 @@ cudaError_t transpose(const float *src, float *dst, long long R, long long C, fl
     return cudaGetLastError();
 }
 
-Pot make_pot(int potential, float delta) { return Pot{potential, potential == CT_POT_QUADRATIC ? 0.0f : 1.0f / delta}; }
+Pot make_pot(int potential, float delta, int maxcurv = 0)
+{
+    return Pot{potential, potential == CT_POT_QUADRATIC ? 0.0f : 1.0f / delta, maxcurv};
+}
 
 template <int MODE>
 cudaError_t fp_helix_dispatch(const ct_geom *g, const float *x, const int *views, int nviews, float *out,
@@ -803,11 +806,11 @@ cudaError_t launch_reg_gradient_helix(const ct_geom *g, const float *x, float be
 }
 
 cudaError_t launch_reg_update_helix(const ct_geom *g, const SolveDev &S, float beta, float delta, int potential,
-                                    cudaStream_t st)
+                                    int maxcurv, cudaStream_t st)
 {
     const VolDims D = column_dims(g);
     const long long n = (long long)D.nx * D.ny * D.nz;
-    reg_update3_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(D, S, beta, make_pot(potential, delta));
+    reg_update3_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(D, S, beta, make_pot(potential, delta, maxcurv));
     return cudaGetLastError();
 }
 

@@ -58,9 +58,9 @@ cudaError_t launch_reg_gradient(const FanDev &G, const float *x, float beta, flo
 }
 
 cudaError_t launch_reg_update(const FanDev &G, const SolveDev &S, float beta, float delta, int potential,
-                              cudaStream_t st)
+                              int maxcurv, cudaStream_t st)
 {
-    Pot P{potential, potential == CT_POT_QUADRATIC ? 0.0f : 1.0f / delta};
+    Pot P{potential, potential == CT_POT_QUADRATIC ? 0.0f : 1.0f / delta, maxcurv};
     dim3 grid((G.nx + 31) / 32, (G.ny + 7) / 8);
     reg_update_kernel<<<grid, 256, 0, st>>>(G, S, beta, P);
     return cudaGetLastError();

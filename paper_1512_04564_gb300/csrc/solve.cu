@@ -123,8 +123,8 @@ double rho_continuation(long k, double alpha)
 // The launches of one subiteration step, for either geometry kind.
 cudaError_t step_update(const ct_geom *g, const SolveDev &S, const ct_solve_params *p, cudaStream_t st)
 {
-    return g->helical ? launch_reg_update_helix(g, S, p->beta, p->delta, p->potential, st)
-                      : launch_reg_update(g->fan, S, p->beta, p->delta, p->potential, st);
+    return g->helical ? launch_reg_update_helix(g, S, p->beta, p->delta, p->potential, p->curvature, st)
+                      : launch_reg_update(g->fan, S, p->beta, p->delta, p->potential, p->curvature, st);
 }
 
 cudaError_t step_fp(const ct_geom *g, int mode, const float *x, const int *views, int nviews, float *out,
@@ -135,10 +135,10 @@ cudaError_t step_fp(const ct_geom *g, int mode, const float *x, const int *views
 }
 
 cudaError_t step_bp(const ct_geom *g, int mode, const float *sino, const int *views, int nviews, float *x,
-                    const SolveDev *S, cudaStream_t st)
+                    const SolveDev *S, cudaStream_t st, float scale = 1.0f)
 {
-    return g->helical ? launch_bp_helix(g, mode, sino, views, nviews, x, 1.0f, 0, S, st)
-                      : launch_bp(g->fan, mode, sino, views, nviews, x, 1.0f, 0, S, st);
+    return g->helical ? launch_bp_helix(g, mode, sino, views, nviews, x, scale, 0, S, st)
+                      : launch_bp(g->fan, mode, sino, views, nviews, x, scale, 0, S, st);
 }
 
 struct Events {
@@ -177,6 +177,11 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
     if (p->stop_rmsd_hu > 0.0f && !p->x_ref) { set_error("stop_rmsd_hu needs x_ref"); return CT_EINVAL; }
     if ((long)p->n_iter * p->M > 200000000L) { set_error("n_iter * M too large"); return CT_EINVAL; }
     if (p->init_fbp != 0 && p->init_fbp != 1) { set_error("init_fbp must be 0 or 1"); return CT_EINVAL; }
+    if (p->curvature != CT_CURV_HUBER && p->curvature != CT_CURV_MAX) {
+        set_error("unknown curvature %d", p->curvature);
+        return CT_EINVAL;
+    }
+    if (!(p->dl_scale >= 0.0f) || !std::isfinite(p->dl_scale)) { set_error("dl_scale must be >= 0"); return CT_EINVAL; }
     if (p->init_fbp) {
         ct_status sf = validate_fbp(g, CT_FBP_HANN);
         if (sf != CT_OK) return sf;
@@ -282,7 +287,8 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
     }
     // D_L = diag(A' W A 1) over all views
     CT_CUDA_TRY(step_fp(g, FP_ONES_W, nullptr, g->d_views_all, na, g->d_sino_ws, nullptr, w, ws), "D_L forward");
-    CT_CUDA_TRY(step_bp(g, BP_PLAIN, g->d_sino_ws, g->d_views_all, na, W.d_l, nullptr, ws), "D_L back");
+    CT_CUDA_TRY(step_bp(g, BP_PLAIN, g->d_sino_ws, g->d_views_all, na, W.d_l, nullptr, ws,
+                        p->dl_scale > 0.0f ? p->dl_scale : 1.0f), "D_L back");
     // rho = 1, zeta = g = M grad L_M(x), h = D_L x - zeta  (last subset)
     CT_CUDA_TRY(step_fp(g, FP_RESID, S.x, W.perm + off[M - 1], cnt[M - 1], W.resid, y, w, ws), "init forward");
     CT_CUDA_TRY(step_bp(g, BP_SOLVE_INIT, W.resid, W.perm + off[M - 1], cnt[M - 1], nullptr, &S, ws), "init back");

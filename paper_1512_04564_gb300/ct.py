@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libct.so")
 
 CT_OK, CT_EINVAL, CT_ENOMEM, CT_ECUDA, CT_ETIMEOUT, CT_ENOTSUP = range(6)
 CT_FAN_ARC_2D = 1
+CURVATURES = {"huber": 0, "max": 1}
 CT_HELICAL_CONE_ARC = 2
 CT_POT_HYPERBOLA, CT_POT_FAIR, CT_POT_QUADRATIC = 0, 1, 2
 CT_ALG_PROPOSED, CT_ALG_SIMPLE = 0, 1
@@ -47,7 +48,8 @@ class ct_solve_params(ctypes.Structure):
         ("potential", ctypes.c_int), ("algorithm", ctypes.c_int), ("nonneg", ctypes.c_int),
         ("continuation", ctypes.c_int), ("rho_fixed", ctypes.c_float),
         ("x_ref", ctypes.c_void_p), ("hu_per_unit", ctypes.c_float), ("fov_radius", ctypes.c_float),
-        ("stop_rmsd_hu", ctypes.c_float), ("init_fbp", ctypes.c_int),
+        ("stop_rmsd_hu", ctypes.c_float), ("init_fbp", ctypes.c_int), ("curvature", ctypes.c_int),
+        ("dl_scale", ctypes.c_float),
     ]
 
 
@@ -307,12 +309,13 @@ def ct_relaxed_oslalm_solve(geom: Geometry, y: torch.Tensor, w: torch.Tensor, x:
                             n_iter: int, alpha: float, beta: float, delta: float, potential="hyperbola",
                             algorithm="proposed", nonneg=True, continuation=True, rho_fixed=0.0,
                             x_ref: torch.Tensor | None = None, hu_per_unit=1.0, fov_radius=0.0,
-                            stop_rmsd_hu=0.0, init_fbp=False, stream=None) -> dict:
+                            stop_rmsd_hu=0.0, init_fbp=False, curvature="huber", dl_scale=1.0, stream=None) -> dict:
     """Relaxed OS-LALM (Algorithm 1 / 2); x is updated in place.  Returns the report as a dict."""
     n = geom.nvox
     p = _params(geom, M=M, n_iter=n_iter, alpha=alpha, beta=beta, delta=delta, potential=potential,
                 algorithm=algorithm, nonneg=nonneg, continuation=continuation, rho_fixed=rho_fixed, x_ref=x_ref,
-                hu_per_unit=hu_per_unit, fov_radius=fov_radius, stop_rmsd_hu=stop_rmsd_hu, init_fbp=init_fbp)
+                hu_per_unit=hu_per_unit, fov_radius=fov_radius, stop_rmsd_hu=stop_rmsd_hu, init_fbp=init_fbp,
+                curvature=curvature, dl_scale=dl_scale)
     r, trace, its = _report(n_iter)
     _check(_lib.ct_relaxed_oslalm_solve(geom.handle, _ptr(y, "y", geom.na * geom.view_len), _ptr(w, "w", geom.na * geom.view_len),
                                         ctypes.byref(p), _ptr(x, "x", n), ctypes.byref(r), _stream(stream)))
@@ -321,7 +324,7 @@ def ct_relaxed_oslalm_solve(geom: Geometry, y: torch.Tensor, w: torch.Tensor, x:
 
 def _params(geom, *, M, n_iter, alpha, beta, delta, potential="hyperbola", algorithm="proposed", nonneg=True,
             continuation=True, rho_fixed=0.0, x_ref=None, hu_per_unit=1.0, fov_radius=0.0, stop_rmsd_hu=0.0,
-            init_fbp=False):
+            init_fbp=False, curvature="huber", dl_scale=1.0):
     n = geom.nvox
     p = ct_solve_params()
     p.M, p.n_iter, p.alpha, p.beta, p.delta = M, n_iter, alpha, beta, delta
@@ -331,6 +334,8 @@ def _params(geom, *, M, n_iter, alpha, beta, delta, potential="hyperbola", algor
     p.x_ref = _ptr(x_ref, "x_ref", n)
     p.hu_per_unit, p.fov_radius, p.stop_rmsd_hu = hu_per_unit, fov_radius, stop_rmsd_hu
     p.init_fbp = int(bool(init_fbp))
+    p.curvature = CURVATURES[curvature] if isinstance(curvature, str) else int(curvature)
+    p.dl_scale = float(dl_scale)
     return p
 
 

@@ -208,7 +208,7 @@ def test_reg_gradient_parity(ct, pot):
 
 
 def _solve_case(ct, c, M, alpha, n_iter, algorithm="proposed", continuation=True, rho_fixed=0.0, x0=None,
-                make_geom=None):
+                make_geom=None, curvature="huber", dl_scale=1.0):
     d = synth.make_scan(c)
     y32, w32 = d.y.astype(np.float32), d.w.astype(np.float32)
     g = c.geom
@@ -216,12 +216,13 @@ def _solve_case(ct, c, M, alpha, n_iter, algorithm="proposed", continuation=True
     prob = osolver.PWLSProblem(FanProjector(g), y32.astype(np.float64), w32.astype(np.float64),
                                c.beta_per_mm, c.delta, c.potential)
     xo = osolver.relaxed_os_lalm(prob, x0.astype(np.float64), M, alpha, n_iter, algorithm=algorithm,
-                                 continuation=continuation, rho_fixed=rho_fixed)
+                                 continuation=continuation, rho_fixed=rho_fixed, curvature=curvature,
+                                 dl_scale=dl_scale)
     G = make_geom(g) if make_geom else ct.Geometry.from_fan(g)
     xg = dev(x0)
     ct.ct_relaxed_oslalm_solve(G, dev(y32), dev(w32), xg, M=M, n_iter=n_iter, alpha=alpha, beta=c.beta_per_mm,
                                delta=c.delta, potential=c.potential, algorithm=algorithm,
-                               continuation=continuation, rho_fixed=rho_fixed)
+                               continuation=continuation, rho_fixed=rho_fixed, curvature=curvature, dl_scale=dl_scale)
     mask = osolver.fov_mask(g)
     return osolver.rmsd_hu(xg.cpu().numpy().astype(np.float64), xo, mask, c.hu_per_unit), xo
 
@@ -236,6 +237,13 @@ def _solve_case(ct, c, M, alpha, n_iter, algorithm="proposed", continuation=True
 ])
 def test_solve_parity_fan2d_128(ct, make_geom, M, alpha, n_iter, alg):
     rmsd, _ = _solve_case(ct, synth.fan2d_128(), M, alpha, n_iter, algorithm=alg, make_geom=make_geom)
+    assert rmsd <= 0.1, rmsd
+
+
+@pytest.mark.parametrize("curvature,dl_scale", [("max", 1.0), ("huber", 2.0), ("max", 0.75)])
+def test_solve_parity_majorizer_variants(ct, curvature, dl_scale):
+    """The supplement's majorizer study: maximum-curvature D_R and scaled D_L, against the oracle."""
+    rmsd, _ = _solve_case(ct, synth.fan2d_128(), 5, 1.999, 10, curvature=curvature, dl_scale=dl_scale)
     assert rmsd <= 0.1, rmsd
 
 

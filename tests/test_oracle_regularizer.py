@@ -91,3 +91,17 @@ def test_potential_limits():
     assert abs(phi(np.array([delta]))[0] - delta ** 2 * (math.sqrt(2) - 1)) < 1e-18
     phi, dphi, omega = reg.potential("fair", delta)
     assert abs(phi(np.array([delta]))[0] - delta ** 2 * (1 - math.log(2))) < 1e-18
+
+
+@pytest.mark.parametrize("kind", ["hyperbola", "fair"])
+def test_max_curvature_majorizes(kind):
+    """phi''(0) = 1 bounds the curvature of both potentials, so 2 beta_i per pair majorizes R."""
+    rng = np.random.default_rng(6)
+    delta = 0.03
+    for _ in range(20):
+        x = rng.random((8, 8)) * 0.3
+        d = rng.standard_normal((8, 8)) * rng.choice([0.001, 0.05, 0.5])
+        R0 = reg.value(x, 1.7, delta, kind)
+        g = reg.gradient(x, 1.7, delta, kind)
+        D = reg.curvature(x, 1.7, delta, "quadratic")
+        assert reg.value(x + d, 1.7, delta, kind) <= R0 + np.sum(g * d) + 0.5 * np.sum(D * d * d) + 1e-12

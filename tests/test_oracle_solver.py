@@ -279,3 +279,29 @@ def test_dense_direct_solve_quadratic_32():
     assert np.sqrt(np.mean(r0 ** 2)) < 1e-9 * np.abs(x_hat).max()
     r1 = solver.kkt_residual(prob, x_hat.reshape(ny, nx) * 1.01, nonneg=False)
     assert np.sqrt(np.mean(r1 ** 2)) > 1e-4 * np.abs(x_hat).max()
+
+
+def test_max_curvature_majorizer_is_larger_and_monotone():
+    """The maximum-curvature D_R bounds Huber's from above (omega <= phi''(0) = 1) and, as an SQS
+    majorizer, keeps the plain SQS special case monotone."""
+    prob, g = _small_ct(potential="hyperbola")
+    rng = np.random.default_rng(9)
+    x = rng.random((g.ny, g.nx)) * 0.03
+    assert np.all(prob.D_R(x, "max") >= prob.D_R(x, "huber") - 1e-15)
+    x = np.zeros((g.ny, g.nx))
+    DL = prob.D_L()
+    costs = [prob.cost(x)]
+    for _ in range(30):
+        x = solver.relaxed_os_lalm(prob, x, 1, 1.0, 1, continuation=False, rho_fixed=1.0, D_L=DL, curvature="max")
+        costs.append(prob.cost(x))
+    assert np.all(np.diff(costs) <= 1e-12 * abs(costs[0]))
+
+
+def test_dl_scale_enters_as_kappa_times_dl():
+    """dl_scale = k gives the same iterates as passing k * D_L explicitly."""
+    prob, g = _small_ct()
+    DL = prob.D_L()
+    x0 = np.zeros((g.ny, g.nx))
+    a = solver.relaxed_os_lalm(prob, x0, 2, 1.5, 3, dl_scale=2.0)
+    b = solver.relaxed_os_lalm(prob, x0, 2, 1.5, 3, D_L=2.0 * DL)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-15)
