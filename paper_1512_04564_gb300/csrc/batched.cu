@@ -306,13 +306,22 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const BatchSlice *__r
                         an = __ldcs(&B.G.foot_an[i]);
                     }
                     for (int k = 0; k < nv; k++) {
-                        const Footprint F = footprint_from(tn, an);
+                        const float4 w = tn;
+                        const float2 b = an;
                         if (k + 1 < nv) {
                             const size_t i = (size_t)B.perm[v0 + k + 1] * vstride + base;
                             tn = __ldcs(&B.G.foot_t[i]);
                             an = __ldcs(&B.G.foot_an[i]);
                         }
-                        acc += footprint_dot_coherent(F, B.resid + (size_t)k * B.G.ns, B.G.ns);
+                        const float *row = B.resid + (size_t)k * B.G.ns;
+                        if (__float_as_int(b.y) == kWideRecord) {  // wider than a record: on the fly
+                            const int v = B.perm[v0 + k];
+                            const float2 cs = __ldg(&B.G.view_cs[v]);
+                            const float4 A = __ldg(&B.G.anchor[(size_t)v * ntiles + tile]);
+                            acc += footprint_dot_coherent(sf_footprint(B.G, cs.x, cs.y, A, ox, oy), row, B.G.ns);
+                        } else {
+                            acc += record_dot<true>(w, b, row, B.G.ns);
+                        }
                     }
                 } else {
                     for (int k = 0; k < nv; k++) {

@@ -34,8 +34,9 @@ struct FanDev {
     const float2 *view_cs;    // [na]: (cos beta, sin beta)
     const float *view_beta;   // [na]: beta in [0, 2 pi)
     // resident system matrix (ct_geom_precompute); null when footprints are computed on the fly
-    const float4 *foot_t;     // [na][ntiles][256]: trapezoid vertices t0..t3 (cells, relative to n)
-    const float2 *foot_an;    // [na][ntiles][256]: amplitude, n (int bits)
+    const float4 *foot_t;     // [na][ntiles][256]: a_ij of the pixel's first four cells n0 .. n0+3
+    const float2 *foot_an;    // [na][ntiles][256]: a_ij of cell n0+4, and n0 as int bits (kWideRecord:
+                              // the footprint covers more than kRecordCells cells; evaluate it on the fly)
     const long long *row_ptr; // [na*ns + 1]: start of each ray's entries
     const int2 *row_ent;      // (pixel index, a_ij bits), ray-major, march order within a ray
     int fp_variant;           // forward projector chosen by ct_geom_autotune (FP_AUTO: default order)
@@ -370,6 +371,27 @@ ct_status helix_sqs_diag(const ct_geom *g, const float *w, float *d_l, cudaStrea
 ct_status helix_reg_gradient(const ct_geom *g, const float *x, float beta, float delta, int potential, float *grad,
                              float *curv, cudaStream_t st);
 ct_status stage_views(const ct_geom *g, const int *views, int nviews, const int **dev_views, cudaStream_t st);
+
+// ---------------------------------------------------------------- stored cell-weight records (resident matrix)
+
+constexpr int kRecordCells = 5;          // cells per stored (view, pixel) record
+constexpr int kWideRecord = -(1 << 30);  // base-cell code of a footprint wider than kRecordCells cells
+
+// sum_k a_k row[n0 + k] over one stored record (cells outside [0, ns) read as 0).  COHERENT loads
+// bypass L1 (rows rewritten by other CTAs of a persistent kernel).
+template <bool COHERENT = false>
+__device__ __forceinline__ float record_dot(float4 w, float2 w4n, const float *row, int ns)
+{
+    const int n0 = __float_as_int(w4n.y);
+    const float wk[kRecordCells] = {w.x, w.y, w.z, w.w, w4n.x};
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kRecordCells; k++) {
+        const int c = n0 + k;
+        if ((unsigned)c < (unsigned)ns) acc = fmaf(wk[k], COHERENT ? __ldcg(&row[c]) : __ldg(&row[c]), acc);
+    }
+    return acc;
+}
 
 // ---------------------------------------------------------------- regularizer (Eq. (def_reg))
 

@@ -7,8 +7,10 @@
 // use and then streamed:
 //   * ray-major rows: for every ray, the (pixel, a_ij) pairs in the order the
 //     ray kernel visits them (march order), for the ray-driven projector;
-//   * per-(view, pixel) footprints: trapezoid vertices, amplitude and base
-//     cell, laid out tile by tile, for the voxel-driven back-projector.
+//   * per-(view, pixel) records: the a_ij of the footprint's first five cells
+//     and the base cell, laid out tile by tile, for the voxel-driven
+//     back-projector (footprints wider than five cells, ~1% at 512x512, are
+//     marked and evaluated on the fly).
 // Building it: count each ray's nonzero weights, exclusive-scan the counts
 // into row pointers, fill the rows, store the footprints.
 #include <vector>
@@ -57,8 +59,16 @@ __global__ void __launch_bounds__(256) matrix_foot_kernel(FanDev G, float4 *__re
     const float4 A = __ldg(&G.anchor[(size_t)v * (G.ntx * G.nty) + tile]);
     const Footprint F = sf_footprint(G, cs.x, cs.y, A, ((float)lx - kTileHalf) * G.dx, ((float)ly - kTileHalf) * G.dy);
     const size_t i = ((size_t)v * (G.ntx * G.nty) + tile) * (kTile * kTile) + threadIdx.x;
-    ft[i] = make_float4(F.t0, F.t1, F.t2, F.t3);
-    fan[i] = make_float2(F.amp, __int_as_float(F.n));
+    // the footprint's cells, as cell_weight evaluates them (the same a_ij as the ray-major rows)
+    const int j0 = (int)floorf(F.t0 - 0.5f) + 1, jl = (int)ceilf(F.t3 + 0.5f) - 1;
+    float w[kRecordCells] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    int code = kWideRecord;
+    if (jl - j0 + 1 <= kRecordCells) {
+        for (int k = 0; k <= jl - j0; k++) w[k] = cell_weight(F, F.n + j0 + k);
+        code = F.n + j0;
+    }
+    ft[i] = make_float4(w[0], w[1], w[2], w[3]);
+    fan[i] = make_float2(w[4], __int_as_float(code));
 }
 
 // in-place exclusive scan of blocks of 1024 values; block totals to sums

@@ -352,8 +352,9 @@ __device__ __forceinline__ void bp_epilogue(const FanDev &G, const SolveDev &S, 
 }
 
 // One CTA per 16x16 tile, 128 threads, two pixels per thread (rows ly and
-// ly + 8 of the tile).  With the resident matrix, the next view's footprints
-// are loaded while the current view's are used.
+// ly + 8 of the tile).  With the resident matrix each (view, pixel) is one
+// stored record of cell weights, and the next view's records are loaded
+// while the current view's are used.
 template <int MODE, bool STORED>
 __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const float *__restrict__ sino,
                                                               const int *__restrict__ views, int nviews,
@@ -378,15 +379,27 @@ __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const
             tn1 = __ldcs(&G.foot_t[i + kBpThreads]); an1 = __ldcs(&G.foot_an[i + kBpThreads]);
         }
         for (int k = 0; k < nviews; k++) {
-            const Footprint F0 = footprint_from(tn0, an0), F1 = footprint_from(tn1, an1);
+            const float4 w0 = tn0, w1 = tn1;
+            const float2 b0 = an0, b1 = an1;
             if (k + 1 < nviews) {
                 const size_t i = (size_t)__ldg(&views[k + 1]) * vstride + base;
                 tn0 = __ldcs(&G.foot_t[i]); an0 = __ldcs(&G.foot_an[i]);
                 tn1 = __ldcs(&G.foot_t[i + kBpThreads]); an1 = __ldcs(&G.foot_an[i + kBpThreads]);
             }
             const float *row = sino + (size_t)k * G.ns;
-            acc0 += footprint_dot(F0, row, G.ns);
-            acc1 += footprint_dot(F1, row, G.ns);
+            const bool wide0 = __float_as_int(b0.y) == kWideRecord, wide1 = __float_as_int(b1.y) == kWideRecord;
+            if (wide0 || wide1) {  // rare: a footprint wider than a record, evaluated on the fly
+                const int v = __ldg(&views[k]);
+                const float2 cs = __ldg(&G.view_cs[v]);
+                const float4 A = __ldg(&G.anchor[(size_t)v * ntiles + tile]);
+                const float ox = ((float)lx - kTileHalf) * G.dx;
+                if (wide0) acc0 += footprint_dot(sf_footprint(G, cs.x, cs.y, A, ox, ((float)ly - kTileHalf) * G.dy), row, G.ns);
+                if (wide1)
+                    acc1 += footprint_dot(sf_footprint(G, cs.x, cs.y, A, ox, ((float)(ly + kTile / 2) - kTileHalf) * G.dy),
+                                          row, G.ns);
+            }
+            if (!wide0) acc0 += record_dot(w0, b0, row, G.ns);
+            if (!wide1) acc1 += record_dot(w1, b1, row, G.ns);
         }
     } else {
         const float ox = ((float)lx - kTileHalf) * G.dx;
