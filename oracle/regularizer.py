@@ -5,7 +5,9 @@ ORACLE -- test infrastructure only.
 R(x) = sum_i beta_i sum_n kappa_n kappa_{n+s_i} phi([C_i x]_n)      (Sec. III, Eq. (def_reg))
 
 with [C_i x]_n = x_n - x_{n+s_i}, counted for pairs whose both pixels lie in
-the image, kappa = 1, and beta_i = beta / ||s_i|| with ||s_i|| in index units
+the image, kappa_n the voxel-dependent weights (``kappa=None`` reads as
+kappa = 1; ``resolution_kappa`` in oracle.solver gives the resolution-
+uniformity choice), and beta_i = beta / ||s_i|| with ||s_i|| in index units
 (axis neighbours beta, face diagonals beta/sqrt(2), body diagonals
 beta/sqrt(3)).  In 2-D the four directions (1,0), (0,1), (1,1), (1,-1) cover
 all 8 neighbours; in 3-D thirteen directions cover all 26 (the paper's 3-D
@@ -15,8 +17,9 @@ and arrays are [iy][ix] or [iz][iy][ix].
 The SQS diagonal uses Huber's curvature omega(t) = phi'(t)/t (Sec. III-A: the
 iteration-dependent curvature used "for faster convergence"):
 
-D_R(x) = |C|' diag(beta_i omega([C_i x]_n)) |C| 1, i.e. each pair adds
-2 beta_i omega(t) to both of its pixels (|C_i| 1 = 2).
+D_R(x) = |C|' diag(beta_i kappa_n kappa_{n+s_i} omega([C_i x]_n)) |C| 1, i.e.
+each pair adds 2 beta_i kappa_n kappa_{n+s_i} omega(t) to both of its pixels
+(|C_i| 1 = 2).
 """
 
 from __future__ import annotations
@@ -73,36 +76,41 @@ def _pair_slices(shape, d):
     return a, b
 
 
-def value(x: np.ndarray, beta: float, delta: float, kind: str) -> float:
+def _pair_weight(kappa, a, b):
+    """kappa_n kappa_{n+s_i} of each pair (1 without kappa)."""
+    return 1.0 if kappa is None else kappa[a] * kappa[b]
+
+
+def value(x: np.ndarray, beta: float, delta: float, kind: str, kappa: np.ndarray | None = None) -> float:
     phi, _, _ = potential(kind, delta)
     dirs = directions(x.ndim)
     tot = 0.0
     for d, bi in zip(dirs, direction_weights(beta, dirs)):
         a, b = _pair_slices(x.shape, d)
-        tot += bi * float(np.sum(phi(x[a] - x[b])))
+        tot += bi * float(np.sum(_pair_weight(kappa, a, b) * phi(x[a] - x[b])))
     return tot
 
 
-def gradient(x: np.ndarray, beta: float, delta: float, kind: str) -> np.ndarray:
+def gradient(x: np.ndarray, beta: float, delta: float, kind: str, kappa: np.ndarray | None = None) -> np.ndarray:
     _, dphi, _ = potential(kind, delta)
     dirs = directions(x.ndim)
     g = np.zeros_like(x, dtype=np.float64)
     for d, bi in zip(dirs, direction_weights(beta, dirs)):
         a, b = _pair_slices(x.shape, d)
-        f = bi * dphi(x[a] - x[b])
+        f = bi * _pair_weight(kappa, a, b) * dphi(x[a] - x[b])
         g[a] += f
         g[b] -= f
     return g
 
 
-def curvature(x: np.ndarray, beta: float, delta: float, kind: str) -> np.ndarray:
+def curvature(x: np.ndarray, beta: float, delta: float, kind: str, kappa: np.ndarray | None = None) -> np.ndarray:
     """Huber-curvature SQS diagonal D_R(x)."""
     _, _, omega = potential(kind, delta)
     dirs = directions(x.ndim)
     D = np.zeros_like(x, dtype=np.float64)
     for d, bi in zip(dirs, direction_weights(beta, dirs)):
         a, b = _pair_slices(x.shape, d)
-        c = 2.0 * bi * omega(x[a] - x[b])
+        c = 2.0 * bi * _pair_weight(kappa, a, b) * omega(x[a] - x[b])
         D[a] += c
         D[b] += c
     return D

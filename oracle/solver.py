@@ -56,6 +56,7 @@ class PWLSProblem:
     beta: float
     delta: float
     potential: str = "hyperbola"
+    kappa: np.ndarray | None = None  # kappa_n of Eq. (def_reg), image-shaped; None: kappa = 1
 
     @property
     def shape(self):
@@ -77,17 +78,29 @@ class PWLSProblem:
 
     def cost(self, x: np.ndarray) -> float:
         r = self.proj.forward(x) - self.y
-        return 0.5 * float(np.sum(self.w * r * r)) + reg.value(x, self.beta, self.delta, self.potential)
+        return 0.5 * float(np.sum(self.w * r * r)) + reg.value(x, self.beta, self.delta, self.potential, self.kappa)
 
     def grad_R(self, x):
-        return reg.gradient(x, self.beta, self.delta, self.potential)
+        return reg.gradient(x, self.beta, self.delta, self.potential, self.kappa)
 
     def D_R(self, x, curvature: str = "huber"):
         """SQS diagonal of R: Huber's optimal curvature omega(t) = phi'(t)/t, or the potential's maximum
         curvature phi''(0) = 1 for every pair (Sec. II-B; the supplement compares the two)."""
         if curvature == "max":
-            return reg.curvature(x, self.beta, self.delta, "quadratic")
-        return reg.curvature(x, self.beta, self.delta, self.potential)
+            return reg.curvature(x, self.beta, self.delta, "quadratic", self.kappa)
+        return reg.curvature(x, self.beta, self.delta, self.potential, self.kappa)
+
+
+def resolution_kappa(proj, w: np.ndarray) -> np.ndarray:
+    """Voxel weights kappa_n of Eq. (def_reg) "for improving resolution uniformity" (Sec. III, citing
+    Fessler and Rogers 1996): kappa_j = sqrt(sum_i a_ij w_i / sum_i a_ij), the square root of the
+    a_ij-weighted mean of the statistical weights of the rays through voxel j, over all views; 0 where
+    no ray meets the voxel.  (The cited paper weights by a_ij^2; the first power is the common
+    simplification, computable with A' alone.)"""
+    num = proj.back(w)
+    den = proj.back(np.ones_like(w))
+    safe = np.where(den > 0, den, 1.0)
+    return np.where(den > 0, np.sqrt(np.maximum(num, 0.0) / safe), 0.0)
 
 
 def _x_step(x, s, gR, rho, DL, DR, nonneg):
