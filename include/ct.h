@@ -164,12 +164,25 @@ enum { CT_ALG_PROPOSED = 0, CT_ALG_SIMPLE = 1 };
 enum { CT_CURV_HUBER = 0, CT_CURV_MAX = 1 };
 
 /* Gradient and Huber-curvature SQS diagonal of the regularizer
- * R(x) = sum_i beta_i sum_n phi([C_i x]_n) (Eq. (def_reg)) over the 8
- * neighbours in 2-D, beta_i = beta / ||s_i||, kappa = 1.  potential:
+ * R(x) = sum_i beta_i sum_n kappa_n kappa_{n+s_i} phi([C_i x]_n)
+ * (Eq. (def_reg)) over the 8 neighbours in 2-D (26 in 3-D),
+ * beta_i = beta / ||s_i||.  kappa: optional device image of the voxel
+ * weights kappa_n (same layout as x), NULL for kappa = 1.  potential:
  * CT_POT_*, delta > 0 its scale (same units as x).  grad, curv: device
- * [ny][nx] outputs (curv may be NULL).  Errors: CT_EINVAL, CT_ECUDA. */
-ct_status ct_reg_gradient(const ct_geom *g, const float *x, float beta, float delta, int potential, float *grad,
-                          float *curv, void *stream);
+ * outputs shaped as x (curv may be NULL).  Errors: CT_EINVAL, CT_ECUDA. */
+ct_status ct_reg_gradient(const ct_geom *g, const float *x, const float *kappa, float beta, float delta,
+                          int potential, float *grad, float *curv, void *stream);
+
+/* Voxel weights for resolution uniformity, kappa_n of Eq. (def_reg) (Sec. III
+ * cites Fessler and Rogers for them; the paper gives no formula):
+ * kappa_j = sqrt( [A' w]_j / [A' 1]_j ), the square root of the a_ij-weighted
+ * mean of the statistical weights of the rays through voxel j over all views
+ * (the cited work weights by a_ij^2; the first power needs only A'), and 0
+ * where no ray meets voxel j.  w: device sinogram of weights (>= 0), shaped
+ * as for ct_sqs_diag; kappa: device output shaped as the image.  Uses the
+ * geometry's sinogram workspace and allocates one image of stream-ordered
+ * device scratch for the call.  Errors: CT_EINVAL, CT_ENOMEM, CT_ECUDA. */
+ct_status ct_kappa(const ct_geom *g, const float *w, float *kappa, void *stream);
 
 /* Parameters of ct_relaxed_oslalm_solve. */
 typedef struct {
@@ -191,6 +204,8 @@ typedef struct {
     int curvature;      /* D_R majorizer (Sec. II-B): CT_CURV_HUBER (Huber's optimal curvature, the default)
                            or CT_CURV_MAX (the potential's maximum curvature, phi''(0) = 1) */
     float dl_scale;     /* D_L <- dl_scale * diag(A'WA1) (supplement's majorizer study); 0 reads as 1 */
+    const float *kappa; /* optional device image of the regularizer's voxel weights kappa_n (Eq. (def_reg),
+                           e.g. from ct_kappa; same layout as x_inout), NULL for kappa = 1 */
 } ct_solve_params;
 
 /* Report filled by ct_relaxed_oslalm_solve.  The two array pointers are

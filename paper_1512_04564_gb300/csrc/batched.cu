@@ -31,6 +31,7 @@ struct BatchSlice {
     FanDev G;
     float *x, *x_new, *g, *h, *d_l, *resid;
     const float *y, *w, *x_ref;
+    const float *kappa;  // regularizer voxel weights, or nullptr for kappa = 1
     const int *perm;     // views in subset order
     const int *sub_off;  // [M+1] offsets into perm
     const float *rho;    // [T]
@@ -213,7 +214,10 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const BatchSlice *__r
                 const int ix = j % B.G.nx, iy = j / B.G.nx;
                 const float rho = B.rho[t];
                 float gr, cv;
-                reg_terms<true>(B.G, B.x, ix, iy, B.beta, B.P, gr, cv);
+                if (B.kappa)
+                    reg_terms<true, true>(B.G, B.x, ix, iy, B.beta, B.P, gr, cv, B.kappa);
+                else
+                    reg_terms<true, false>(B.G, B.x, ix, iy, B.beta, B.P, gr, cv);
                 const float xj = __ldcg(&B.x[j]), dl = __ldcg(&B.d_l[j]), g = __ldcg(&B.g[j]), h = __ldcg(&B.h[j]);
                 const float sv = (B.algorithm == CT_ALG_PROPOSED) ? fmaf(rho, fmaf(dl, xj, -h), (1.0f - rho) * g)
                                                                   : fmaf(rho, h, (1.0f - rho) * g);
@@ -460,6 +464,7 @@ extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms
         B.y = y[i];
         B.w = w[i];
         B.x_ref = p->x_ref;
+        B.kappa = p->kappa;
         B.perm = perm;
         B.sub_off = sub;
         B.rho = rho;

@@ -55,6 +55,7 @@ struct SolveDev {
     float alpha, M_scale;
     int algorithm;   // CT_ALG_*
     int nonneg;
+    const float *kappa;  // regularizer voxel weights kappa_n (same layout as x), or nullptr for kappa = 1
 };
 
 // Axial part of a helical cone-beam geometry (the transaxial part is a FanDev
@@ -334,8 +335,8 @@ cudaError_t launch_fp(const FanDev &G, int mode, const float *x, const int *view
                       const float *y, const float *w, cudaStream_t st);
 cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *views, int nviews, float *x,
                       float scale, int accumulate, const SolveDev *S, cudaStream_t st);
-cudaError_t launch_reg_gradient(const FanDev &G, const float *x, float beta, float delta, int potential,
-                                float *grad, float *curv, cudaStream_t st);
+cudaError_t launch_reg_gradient(const FanDev &G, const float *x, const float *kappa, float beta, float delta,
+                                int potential, float *grad, float *curv, cudaStream_t st);
 cudaError_t launch_reg_update(const FanDev &G, const SolveDev &S, float beta, float delta, int potential,
                               int maxcurv, cudaStream_t st);
 
@@ -350,8 +351,8 @@ cudaError_t launch_fp_helix(const ct_geom *g, int mode, const float *x, const in
                             const float *y, const float *w, cudaStream_t st);
 cudaError_t launch_bp_helix(const ct_geom *g, int mode, const float *sino, const int *views, int nviews, float *x,
                             float scale, int accumulate, const SolveDev *S, cudaStream_t st);
-cudaError_t launch_reg_gradient_helix(const ct_geom *g, const float *x, float beta, float delta, int potential,
-                                      float *grad, float *curv, cudaStream_t st);
+cudaError_t launch_reg_gradient_helix(const ct_geom *g, const float *x, const float *kappa, float beta, float delta,
+                                      int potential, float *grad, float *curv, cudaStream_t st);
 cudaError_t launch_reg_update_helix(const ct_geom *g, const SolveDev &S, float beta, float delta, int potential,
                                     int maxcurv, cudaStream_t st);
 cudaError_t launch_rmsd_helix(const ct_geom *g, const float *x, const float *xr, float r2max, double *partial,
@@ -368,8 +369,8 @@ ct_status helix_forward(const ct_geom *g, const float *x, float *y, const int *v
 ct_status helix_back(const ct_geom *g, const float *y, float *x, const int *views, int nviews, float scale,
                      int accumulate, cudaStream_t st);
 ct_status helix_sqs_diag(const ct_geom *g, const float *w, float *d_l, cudaStream_t st);
-ct_status helix_reg_gradient(const ct_geom *g, const float *x, float beta, float delta, int potential, float *grad,
-                             float *curv, cudaStream_t st);
+ct_status helix_reg_gradient(const ct_geom *g, const float *x, const float *kappa, float beta, float delta,
+                             int potential, float *grad, float *curv, cudaStream_t st);
 ct_status stage_views(const ct_geom *g, const int *views, int nviews, const int **dev_views, cudaStream_t st);
 
 // ---------------------------------------------------------------- stored cell-weight records (resident matrix)
@@ -422,11 +423,16 @@ __device__ __forceinline__ float ld_img(const float *p)
     return COHERENT ? __ldcg(p) : __ldg(p);
 }
 
-template <bool COHERENT = false>
+// grad R_j and the SQS diagonal D_R,j of Eq. (def_reg) at pixel (ix, iy):
+//   grad R_j = kappa_j sum_i beta_i [kappa_{j+s_i} phi'(x_j - x_{j+s_i}) - kappa_{j-s_i} phi'(x_{j-s_i} - x_j)]
+//   D_R,j    = kappa_j sum_i 2 beta_i [kappa_{j+s_i} omega(.) + kappa_{j-s_i} omega(.)]
+// (KAPPA = false: kappa = 1, and the kappa pointer is not read).
+template <bool COHERENT = false, bool KAPPA = false>
 __device__ __forceinline__ void reg_terms(const FanDev &G, const float *__restrict__ x, int ix, int iy, float beta,
-                                          Pot P, float &grad, float &curv)
+                                          Pot P, float &grad, float &curv, const float *__restrict__ kappa = nullptr)
 {
-    const float xj = ld_img<COHERENT>(&x[(size_t)iy * G.nx + ix]);
+    const size_t j = (size_t)iy * G.nx + ix;
+    const float xj = ld_img<COHERENT>(&x[j]);
     const int ddx[4] = {1, 0, 1, 1};
     const int ddy[4] = {0, 1, 1, -1};
     const float bd = beta * 0.70710678118654752f;
@@ -437,18 +443,27 @@ __device__ __forceinline__ void reg_terms(const FanDev &G, const float *__restri
         const float bi = (i < 2) ? beta : bd;
         const int fx = ix + ddx[i], fy = iy + ddy[i];
         if (fx >= 0 && fx < G.nx && fy >= 0 && fy < G.ny) {
+            const size_t f = (size_t)fy * G.nx + fx;
+            const float bk = KAPPA ? bi * ld_img<COHERENT>(&kappa[f]) : bi;
             float d, o;
-            P.eval(xj - ld_img<COHERENT>(&x[(size_t)fy * G.nx + fx]), d, o);
-            grad = fmaf(bi, d, grad);
-            curv = fmaf(2.0f * bi, P.maxcurv ? 1.0f : o, curv);
+            P.eval(xj - ld_img<COHERENT>(&x[f]), d, o);
+            grad = fmaf(bk, d, grad);
+            curv = fmaf(2.0f * bk, P.maxcurv ? 1.0f : o, curv);
         }
         const int bx = ix - ddx[i], by = iy - ddy[i];
         if (bx >= 0 && bx < G.nx && by >= 0 && by < G.ny) {
+            const size_t b = (size_t)by * G.nx + bx;
+            const float bk = KAPPA ? bi * ld_img<COHERENT>(&kappa[b]) : bi;
             float d, o;
-            P.eval(ld_img<COHERENT>(&x[(size_t)by * G.nx + bx]) - xj, d, o);
-            grad = fmaf(-bi, d, grad);
-            curv = fmaf(2.0f * bi, P.maxcurv ? 1.0f : o, curv);
+            P.eval(ld_img<COHERENT>(&x[b]) - xj, d, o);
+            grad = fmaf(-bk, d, grad);
+            curv = fmaf(2.0f * bk, P.maxcurv ? 1.0f : o, curv);
         }
+    }
+    if (KAPPA) {
+        const float kj = ld_img<COHERENT>(&kappa[j]);
+        grad *= kj;
+        curv *= kj;
     }
 }
 

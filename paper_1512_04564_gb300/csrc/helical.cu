@@ -547,10 +547,13 @@ struct VolDims {
     long long sx, sy, sz;  // element strides along x, y, z
 };
 
-// grad R_j = sum over the 26 neighbours n of beta/||s|| phi'(x_j - x_n);
-// D_R,j = sum 2 beta/||s|| omega(x_j - x_n) (pairs outside the volume absent).
-__device__ __forceinline__ void reg_terms3(const float *__restrict__ x, const VolDims &D, int ix, int iy, int iz,
-                                           long long j, float beta, Pot P, float &grad, float &curv)
+// grad R_j = kappa_j sum over the 26 neighbours n of beta/||s|| kappa_n phi'(x_j - x_n);
+// D_R,j = kappa_j sum 2 beta/||s|| kappa_n omega(x_j - x_n) (pairs outside the volume absent;
+// KAPPA = false: kappa = 1 and the pointer is not read).
+template <bool KAPPA>
+__device__ __forceinline__ void reg_terms3(const float *__restrict__ x, const float *__restrict__ kappa,
+                                           const VolDims &D, int ix, int iy, int iz, long long j, float beta, Pot P,
+                                           float &grad, float &curv)
 {
     const float xj = __ldg(&x[j]);
     const float b1 = beta, b2 = beta * 0.70710678118654752f, b3 = beta * 0.57735026918962576f;
@@ -566,18 +569,26 @@ __device__ __forceinline__ void reg_terms3(const float *__restrict__ x, const Vo
                 if (n2 == 0) continue;
                 const int fx = ix + dx, fy = iy + dy, fz = iz + dz;
                 if (fx < 0 || fx >= D.nx || fy < 0 || fy >= D.ny || fz < 0 || fz >= D.nz) continue;
-                const float bi = n2 == 1 ? b1 : (n2 == 2 ? b2 : b3);
+                const long long n = j + dx * D.sx + dy * D.sy + dz * D.sz;
+                const float b0 = n2 == 1 ? b1 : (n2 == 2 ? b2 : b3);
+                const float bi = KAPPA ? b0 * __ldg(&kappa[n]) : b0;
                 float d, o;
-                P.eval(xj - __ldg(&x[j + dx * D.sx + dy * D.sy + dz * D.sz]), d, o);
+                P.eval(xj - __ldg(&x[n]), d, o);
                 grad = fmaf(bi, d, grad);
                 curv = fmaf(2.0f * bi, P.maxcurv ? 1.0f : o, curv);
             }
+    if (KAPPA) {
+        const float kj = __ldg(&kappa[j]);
+        grad *= kj;
+        curv *= kj;
+    }
 }
 
 // One thread per voxel in memory order of a volume with strides D.
+template <bool KAPPA>
 __global__ void __launch_bounds__(256) reg_gradient3_kernel(VolDims D, int zfast, const float *__restrict__ x,
-                                                           float beta, Pot P, float *__restrict__ grad,
-                                                           float *__restrict__ curv)
+                                                           const float *__restrict__ kappa, float beta, Pot P,
+                                                           float *__restrict__ grad, float *__restrict__ curv)
 {
     const long long n = (long long)D.nx * D.ny * D.nz;
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -595,12 +606,13 @@ __global__ void __launch_bounds__(256) reg_gradient3_kernel(VolDims D, int zfast
         iz = (int)(c / D.ny);
     }
     float gr, cv;
-    reg_terms3(x, D, ix, iy, iz, j, beta, P, gr, cv);
+    reg_terms3<KAPPA>(x, kappa, D, ix, iy, iz, j, beta, P, gr, cv);
     grad[j] = gr;
     if (curv) curv[j] = cv;
 }
 
 // Fused x-update of Algorithm 1/2 on a column-major volume.
+template <bool KAPPA>
 __global__ void __launch_bounds__(256) reg_update3_kernel(VolDims D, SolveDev S, float beta, Pot P)
 {
     const long long n = (long long)D.nx * D.ny * D.nz;
@@ -611,7 +623,7 @@ __global__ void __launch_bounds__(256) reg_update3_kernel(VolDims D, SolveDev S,
     const int ix = (int)(c % D.nx), iy = (int)(c / D.nx);
     const float rho = __ldcg(&S.rho_tab[__ldcg(&S.counter[0])]);
     float gr, cv;
-    reg_terms3(S.x, D, ix, iy, iz, j, beta, P, gr, cv);
+    reg_terms3<KAPPA>(S.x, S.kappa, D, ix, iy, iz, j, beta, P, gr, cv);
     const float xj = S.x[j], dl = S.d_l[j], g = S.g[j], h = S.h[j];
     const float s = (S.algorithm == CT_ALG_PROPOSED) ? fmaf(rho, fmaf(dl, xj, -h), (1.0f - rho) * g)
                                                      : fmaf(rho, h, (1.0f - rho) * g);
@@ -793,15 +805,18 @@ static VolDims column_dims(const ct_geom *g)
     return VolDims{nx, ny, nz, (long long)nz, (long long)nx * nz, 1};
 }
 
-cudaError_t launch_reg_gradient_helix(const ct_geom *g, const float *x, float beta, float delta, int potential,
-                                      float *grad, float *curv, cudaStream_t st)
+cudaError_t launch_reg_gradient_helix(const ct_geom *g, const float *x, const float *kappa, float beta, float delta,
+                                      int potential, float *grad, float *curv, cudaStream_t st)
 {
     // the C ABI's layout, [iz][iy][ix]
     const int nx = g->fan.nx, ny = g->fan.ny, nz = g->hx.nz;
     const VolDims D{nx, ny, nz, 1, (long long)nx, (long long)nx * ny};
     const long long n = (long long)nx * ny * nz;
-    reg_gradient3_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(D, 0, x, beta, make_pot(potential, delta),
-                                                                      grad, curv);
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (kappa)
+        reg_gradient3_kernel<true><<<blocks, 256, 0, st>>>(D, 0, x, kappa, beta, make_pot(potential, delta), grad, curv);
+    else
+        reg_gradient3_kernel<false><<<blocks, 256, 0, st>>>(D, 0, x, kappa, beta, make_pot(potential, delta), grad, curv);
     return cudaGetLastError();
 }
 
@@ -810,7 +825,11 @@ cudaError_t launch_reg_update_helix(const ct_geom *g, const SolveDev &S, float b
 {
     const VolDims D = column_dims(g);
     const long long n = (long long)D.nx * D.ny * D.nz;
-    reg_update3_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(D, S, beta, make_pot(potential, delta, maxcurv));
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (S.kappa)
+        reg_update3_kernel<true><<<blocks, 256, 0, st>>>(D, S, beta, make_pot(potential, delta, maxcurv));
+    else
+        reg_update3_kernel<false><<<blocks, 256, 0, st>>>(D, S, beta, make_pot(potential, delta, maxcurv));
     return cudaGetLastError();
 }
 
@@ -864,10 +883,11 @@ ct_status helix_sqs_diag(const ct_geom *g, const float *w, float *d_l, cudaStrea
     return CT_OK;
 }
 
-ct_status helix_reg_gradient(const ct_geom *g, const float *x, float beta, float delta, int potential, float *grad,
-                             float *curv, cudaStream_t st)
+ct_status helix_reg_gradient(const ct_geom *g, const float *x, const float *kappa, float beta, float delta,
+                             int potential, float *grad, float *curv, cudaStream_t st)
 {
-    CT_CUDA_TRY(launch_reg_gradient_helix(g, x, beta, delta, potential, grad, curv, st), "ct_reg_gradient launch");
+    CT_CUDA_TRY(launch_reg_gradient_helix(g, x, kappa, beta, delta, potential, grad, curv, st),
+                "ct_reg_gradient launch");
     return CT_OK;
 }
 

@@ -75,18 +75,19 @@ struct Workspace {
     int *perm, *counter;
     double *partial;
     float *x_col, *xref_col;  // helical: column-major copies of x and x_ref
+    float *kappa_col;         // helical with kappa: column-major copy of kappa
 };
 
-ct_status ensure_workspace(ct_geom *g, int max_sub, int T, int n_iter, Workspace &W)
+ct_status ensure_workspace(ct_geom *g, int max_sub, int T, int n_iter, bool kappa, Workspace &W)
 {
     const size_t npix = (size_t)g->fan.nx * g->fan.ny * (g->helical ? g->hx.nz : 1);
     const size_t view_len = (size_t)g->fan.ns * (g->helical ? g->hx.nt : 1);
     const size_t vol_h = g->helical ? npix * 4 : 0;
-    size_t off[12], sz = 0;
-    const size_t sizes[12] = {npix * 4, npix * 4, npix * 4, npix * 4, (size_t)max_sub * view_len * 4,
+    size_t off[13], sz = 0;
+    const size_t sizes[13] = {npix * 4, npix * 4, npix * 4, npix * 4, (size_t)max_sub * view_len * 4,
                               (size_t)T * 4, (size_t)(n_iter > 0 ? n_iter : 1) * 4, (size_t)g->fan.na * 4, 16 * 4,
-                              (size_t)kRmsdBlocks * 2 * 8, vol_h, vol_h};
-    for (int i = 0; i < 12; i++) {
+                              (size_t)kRmsdBlocks * 2 * 8, vol_h, vol_h, kappa ? vol_h : 0};
+    for (int i = 0; i < 13; i++) {
         off[i] = sz;
         sz += align_up(sizes[i]);
     }
@@ -110,6 +111,7 @@ ct_status ensure_workspace(ct_geom *g, int max_sub, int T, int n_iter, Workspace
     W.partial = (double *)(b + off[9]);
     W.x_col = g->helical ? (float *)(b + off[10]) : nullptr;
     W.xref_col = g->helical ? (float *)(b + off[11]) : nullptr;
+    W.kappa_col = g->helical && kappa ? (float *)(b + off[12]) : nullptr;
     return CT_OK;
 }
 
@@ -206,7 +208,7 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
         rho[t] = (float)(p->continuation ? rho_continuation(t, p->alpha) : (double)p->rho_fixed);
 
     Workspace W;
-    ct_status st = ensure_workspace(g, max_sub, (int)(T > 0 ? T : 1), p->n_iter, W);
+    ct_status st = ensure_workspace(g, max_sub, (int)(T > 0 ? T : 1), p->n_iter, p->kappa != nullptr, W);
     if (st != CT_OK) return st;
 
     cudaStream_t user = (cudaStream_t)stream, ws = nullptr;
@@ -241,6 +243,7 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
     S.M_scale = (float)M;
     S.algorithm = p->algorithm;
     S.nonneg = p->nonneg;
+    S.kappa = g->helical ? W.kappa_col : p->kappa;
     const FanDev &G = g->fan;
     const double R = p->fov_radius > 0.0f ? (double)p->fov_radius : g->fov_radius;
     const float r2max = (float)(R * R);
@@ -284,6 +287,7 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
     if (g->helical) {  // the kernels work on column-major volumes
         CT_CUDA_TRY(launch_to_columns(g, x, W.x_col, ws), "x layout");
         if (p->x_ref) CT_CUDA_TRY(launch_to_columns(g, p->x_ref, W.xref_col, ws), "x_ref layout");
+        if (p->kappa) CT_CUDA_TRY(launch_to_columns(g, p->kappa, W.kappa_col, ws), "kappa layout");
     }
     // D_L = diag(A' W A 1) over all views
     CT_CUDA_TRY(step_fp(g, FP_ONES_W, nullptr, g->d_views_all, na, g->d_sino_ws, nullptr, w, ws), "D_L forward");

@@ -49,7 +49,7 @@ class ct_solve_params(ctypes.Structure):
         ("continuation", ctypes.c_int), ("rho_fixed", ctypes.c_float),
         ("x_ref", ctypes.c_void_p), ("hu_per_unit", ctypes.c_float), ("fov_radius", ctypes.c_float),
         ("stop_rmsd_hu", ctypes.c_float), ("init_fbp", ctypes.c_int), ("curvature", ctypes.c_int),
-        ("dl_scale", ctypes.c_float),
+        ("dl_scale", ctypes.c_float), ("kappa", ctypes.c_void_p),
     ]
 
 
@@ -84,7 +84,8 @@ def _load():
         "ct_fbp": [vp, vp, vp, cint, vp],
         "ct_geom_precompute": [vp, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong), vp],
         "ct_geom_autotune": [vp, cint, ip, ip, vp],
-        "ct_reg_gradient": [vp, vp, cfl, cfl, cint, vp, vp, vp],
+        "ct_reg_gradient": [vp, vp, vp, cfl, cfl, cint, vp, vp, vp],
+        "ct_kappa": [vp, vp, vp, vp],
         "ct_relaxed_oslalm_solve": [vp, vp, vp, ctypes.POINTER(ct_solve_params), vp,
                                     ctypes.POINTER(ct_solve_report), vp],
         "ct_relaxed_oslalm_solve_batched": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -123,7 +124,7 @@ def _load():
 
 _lib = _load()
 EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_geom_precompute", "ct_geom_autotune", "ct_forward", "ct_back", "ct_sqs_diag",
-            "ct_sqs_diag_noalloc", "ct_fbp", "ct_reg_gradient", "ct_relaxed_oslalm_solve",
+            "ct_sqs_diag_noalloc", "ct_fbp", "ct_reg_gradient", "ct_kappa", "ct_relaxed_oslalm_solve",
             "ct_relaxed_oslalm_solve_batched", "ct_last_error", "ct_version", "ct_gemm_bf16", "ct_conv3x3_bf16",
             "ct_conv3x3_bf16_dgrad", "ct_conv3x3_wgrad_workspace", "ct_conv3x3_bf16_wgrad", "ct_unet_create",
             "ct_unet_destroy", "ct_unet_num_params", "ct_unet_get_params", "ct_unet_set_params", "ct_unet_forward",
@@ -297,25 +298,34 @@ def ct_fbp(geom: Geometry, y: torch.Tensor, x: torch.Tensor, window: str = "hann
 
 
 def ct_reg_gradient(geom: Geometry, x: torch.Tensor, beta: float, delta: float, potential: str | int,
-                    grad: torch.Tensor, curv: torch.Tensor | None = None, stream=None):
+                    grad: torch.Tensor, curv: torch.Tensor | None = None, kappa: torch.Tensor | None = None,
+                    stream=None):
     pot = POTENTIALS[potential] if isinstance(potential, str) else int(potential)
     n = geom.nvox
-    _check(_lib.ct_reg_gradient(geom.handle, _ptr(x, "x", n), float(beta), float(delta), pot,
-                                _ptr(grad, "grad", n), _ptr(curv, "curv", n), _stream(stream)))
+    _check(_lib.ct_reg_gradient(geom.handle, _ptr(x, "x", n), _ptr(kappa, "kappa", n), float(beta), float(delta),
+                                pot, _ptr(grad, "grad", n), _ptr(curv, "curv", n), _stream(stream)))
     return grad, curv
+
+
+def ct_kappa(geom: Geometry, w: torch.Tensor, kappa: torch.Tensor, stream=None) -> torch.Tensor:
+    """Resolution-uniformity voxel weights kappa_j = sqrt([A'w]_j / [A'1]_j) (0 where no ray meets voxel j)."""
+    _check(_lib.ct_kappa(geom.handle, _ptr(w, "w", geom.na * geom.view_len), _ptr(kappa, "kappa", geom.nvox),
+                         _stream(stream)))
+    return kappa
 
 
 def ct_relaxed_oslalm_solve(geom: Geometry, y: torch.Tensor, w: torch.Tensor, x: torch.Tensor, *, M: int,
                             n_iter: int, alpha: float, beta: float, delta: float, potential="hyperbola",
                             algorithm="proposed", nonneg=True, continuation=True, rho_fixed=0.0,
                             x_ref: torch.Tensor | None = None, hu_per_unit=1.0, fov_radius=0.0,
-                            stop_rmsd_hu=0.0, init_fbp=False, curvature="huber", dl_scale=1.0, stream=None) -> dict:
+                            stop_rmsd_hu=0.0, init_fbp=False, curvature="huber", dl_scale=1.0,
+                            kappa: torch.Tensor | None = None, stream=None) -> dict:
     """Relaxed OS-LALM (Algorithm 1 / 2); x is updated in place.  Returns the report as a dict."""
     n = geom.nvox
     p = _params(geom, M=M, n_iter=n_iter, alpha=alpha, beta=beta, delta=delta, potential=potential,
                 algorithm=algorithm, nonneg=nonneg, continuation=continuation, rho_fixed=rho_fixed, x_ref=x_ref,
                 hu_per_unit=hu_per_unit, fov_radius=fov_radius, stop_rmsd_hu=stop_rmsd_hu, init_fbp=init_fbp,
-                curvature=curvature, dl_scale=dl_scale)
+                curvature=curvature, dl_scale=dl_scale, kappa=kappa)
     r, trace, its = _report(n_iter)
     _check(_lib.ct_relaxed_oslalm_solve(geom.handle, _ptr(y, "y", geom.na * geom.view_len), _ptr(w, "w", geom.na * geom.view_len),
                                         ctypes.byref(p), _ptr(x, "x", n), ctypes.byref(r), _stream(stream)))
@@ -324,7 +334,7 @@ def ct_relaxed_oslalm_solve(geom: Geometry, y: torch.Tensor, w: torch.Tensor, x:
 
 def _params(geom, *, M, n_iter, alpha, beta, delta, potential="hyperbola", algorithm="proposed", nonneg=True,
             continuation=True, rho_fixed=0.0, x_ref=None, hu_per_unit=1.0, fov_radius=0.0, stop_rmsd_hu=0.0,
-            init_fbp=False, curvature="huber", dl_scale=1.0):
+            init_fbp=False, curvature="huber", dl_scale=1.0, kappa=None):
     n = geom.nvox
     p = ct_solve_params()
     p.M, p.n_iter, p.alpha, p.beta, p.delta = M, n_iter, alpha, beta, delta
@@ -336,6 +346,7 @@ def _params(geom, *, M, n_iter, alpha, beta, delta, potential="hyperbola", algor
     p.init_fbp = int(bool(init_fbp))
     p.curvature = CURVATURES[curvature] if isinstance(curvature, str) else int(curvature)
     p.dl_scale = float(dl_scale)
+    p.kappa = _ptr(kappa, "kappa", n)
     return p
 
 
