@@ -3,9 +3,10 @@
 ORACLE -- test infrastructure only.  Only ``tests/``, ``__graft_entry__.smoke()``
 and ``bench.py``'s CPU-baseline leg may import this module.
 
-The system matrix is the separable-footprint (trapezoid x rectangle) A of the
-PWLS problem (Sec. III, Eq. (ct_problem)) for the 3-D helical scans of
-Sec. IV; its definition is written out in the C file's header.  Volumes are
+The system matrix is the separable-footprint A of the PWLS problem (Sec. III,
+Eq. (ct_problem)) for the 3-D helical scans of Sec. IV, with a trapezoid
+transaxial footprint and a rectangle (SF-TR) or trapezoid (SF-TT) axial one;
+its definition is written out in the C file's header.  Volumes are
 ``[nz][ny][nx]``; sinograms ``[view][row][cell]``.
 """
 
@@ -30,7 +31,10 @@ class _HGeom(ctypes.Structure):
         ("offset_s", ctypes.c_double), ("offset_t", ctypes.c_double),
         ("dso", ctypes.c_double), ("dsd", ctypes.c_double),
         ("orbit_deg", ctypes.c_double), ("orbit_start_deg", ctypes.c_double), ("pitch", ctypes.c_double),
+        ("axial", ctypes.c_int),
     ]
+
+AXIAL = {"rect": 0, "trap": 1}
 
 
 def _lib():
@@ -64,13 +68,15 @@ def _ip(a):
 
 
 class HelicalProjector:
-    """FP64 SF-TR helical cone-beam projector A (oracle)."""
+    """FP64 separable-footprint helical cone-beam projector A (oracle): SF-TR, or SF-TT when the
+    geometry's ``axial`` is "trap"."""
 
     def __init__(self, geom):
         self.geom = geom
         g = geom
         self._g = _HGeom(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, g.offset_x, g.offset_y, g.offset_z, g.ns, g.nt, g.na,
-                         g.ds, g.dt, g.offset_s, g.offset_t, g.dso, g.dsd, g.orbit_deg, g.orbit_start_deg, g.pitch)
+                         g.ds, g.dt, g.offset_s, g.offset_t, g.dso, g.dsd, g.orbit_deg, g.orbit_start_deg, g.pitch,
+                         AXIAL[getattr(g, "axial", "rect")])
         _lib()
 
     @property

@@ -23,6 +23,15 @@
  *            ray through row t (height v_t on the cylinder at dsd) crosses
  *            the voxel over l_xy / cos(cone angle).
  *
+ * With axial = 1 the axial factor is a trapezoid instead (SF-TT, the other
+ * axial model of the cited separable-footprint method):
+ *
+ *   R_j(t) = (1/dt) * integral over row t of the unit trapezoid whose
+ *            vertices are the detector heights of the voxel's two z-faces
+ *            seen from the nearest and the farthest of its column's four
+ *            (x, y) corners (transaxial distances L_min, L_max): the shadow's
+ *            edges smeared over the range of magnifications the voxel spans.
+ *
  * Geometry: voxel (ix, iy, iz) centred at ((ix-(nx-1)/2+ox) dx,
  * (iy-(ny-1)/2+oy) dy, (iz-(nz-1)/2+oz) dz); view v at angle
  * beta_v = orbit_start + v * orbit / na (orbit may span several turns);
@@ -47,6 +56,7 @@ typedef struct {
     int ns, nt, na;
     double ds, dt, offset_s, offset_t;
     double dso, dsd, orbit_deg, orbit_start_deg, pitch;
+    int axial; /* 0: rectangle axial footprint (SF-TR); 1: trapezoid (SF-TT) */
 } orc_helix_geom;
 
 static double hx_beta(const orc_helix_geom *g, int v)
@@ -90,9 +100,10 @@ static double hx_trap_cdf(const double t[4], double u)
 }
 
 /* Column (ix, iy) in the view with direction (cb, sb): trapezoid vertices in
- * cell units (cell s centred at s), chord l_xy and transaxial distance L. */
+ * cell units (cell s centred at s), chord l_xy, transaxial distance L of the
+ * column's centre and the smallest and largest of its corners' (lmm[0..1]). */
 static void hx_column(const orc_helix_geom *g, double cb, double sb, int ix, int iy, double tau[4], double *lxy,
-                      double *L)
+                      double *L, double lmm[2])
 {
     const double xc = ((double)ix - (g->nx - 1) / 2.0 + g->offset_x) * g->dx;
     const double yc = ((double)iy - (g->ny - 1) / 2.0 + g->offset_y) * g->dy;
@@ -105,6 +116,9 @@ static void hx_column(const orc_helix_geom *g, double cb, double sb, int ix, int
             const double px = xc + 0.5 * sx * g->dx + g->dso * cb, py = yc + 0.5 * sy * g->dy + g->dso * sb;
             const double along = px * cb + py * sb, across = -px * sb + py * cb;
             tau[k++] = atan2(across, along) * cells_per_rad + c0;
+            const double lc = sqrt(px * px + py * py);
+            if (k == 1 || lc < lmm[0]) lmm[0] = lc;
+            if (k == 1 || lc > lmm[1]) lmm[1] = lc;
         }
     for (int i = 1; i < 4; i++) { /* insertion sort */
         double v = tau[i];
@@ -127,8 +141,8 @@ static void hx_view_column(const orc_helix_geom *g, int v, int ix, int iy, int i
                            void *ctx)
 {
     const double b = hx_beta(g, v), cb = cos(b), sb = sin(b), zsrc = hx_source_z(g, b);
-    double tau[4], lxy, L;
-    hx_column(g, cb, sb, ix, iy, tau, &lxy, &L);
+    double tau[4], lxy, L, lmm[2];
+    hx_column(g, cb, sb, ix, iy, tau, &lxy, &L, lmm);
     int s_lo = (int)floor(tau[0] - 0.5) + 1, s_hi = (int)ceil(tau[3] + 0.5) - 1;
     if (s_lo < 0) s_lo = 0;
     if (s_hi > g->ns - 1) s_hi = g->ns - 1;
@@ -141,16 +155,37 @@ static void hx_view_column(const orc_helix_geom *g, int v, int ix, int iy, int i
     const int iz_first = iz_only >= 0 ? iz_only : 0, iz_last = iz_only >= 0 ? iz_only : g->nz - 1;
     for (int iz = iz_first; iz <= iz_last; iz++) {
         const double zc = ((double)iz - (g->nz - 1) / 2.0 + g->offset_z) * g->dz;
-        const double u0 = hx_row_of(g, (zc - 0.5 * g->dz - zsrc) * mag);
-        const double u1 = hx_row_of(g, (zc + 0.5 * g->dz - zsrc) * mag);
+        double u0, u1, ua[4];
+        if (g->axial == 1) { /* trapezoid: each face at the near and the far magnification */
+            const double zf[2] = {zc - 0.5 * g->dz - zsrc, zc + 0.5 * g->dz - zsrc};
+            for (int f = 0; f < 2; f++)
+                for (int m = 0; m < 2; m++) ua[2 * f + m] = hx_row_of(g, zf[f] * g->dsd / lmm[m]);
+            for (int i = 1; i < 4; i++) { /* insertion sort */
+                double v = ua[i];
+                int q = i - 1;
+                while (q >= 0 && ua[q] > v) { ua[q + 1] = ua[q]; q--; }
+                ua[q + 1] = v;
+            }
+            u0 = ua[0];
+            u1 = ua[3];
+        } else {
+            u0 = hx_row_of(g, (zc - 0.5 * g->dz - zsrc) * mag);
+            u1 = hx_row_of(g, (zc + 0.5 * g->dz - zsrc) * mag);
+        }
         int t_lo = (int)floor(u0 - 0.5) + 1, t_hi = (int)ceil(u1 + 0.5) - 1;
         if (t_lo < 0) t_lo = 0;
         if (t_hi > g->nt - 1) t_hi = g->nt - 1;
         const size_t j = ((size_t)iz * g->ny + iy) * g->nx + ix;
         for (int t = t_lo; t <= t_hi; t++) {
-            const double lo = u0 > t - 0.5 ? u0 : t - 0.5, hi = u1 < t + 0.5 ? u1 : t + 0.5;
-            if (hi <= lo) continue;
-            const double rt = hi - lo;
+            double rt;
+            if (g->axial == 1) {
+                rt = hx_trap_cdf(ua, t + 0.5) - hx_trap_cdf(ua, t - 0.5);
+                if (!(rt > 0.0)) continue;
+            } else {
+                const double lo = u0 > t - 0.5 ? u0 : t - 0.5, hi = u1 < t + 0.5 ? u1 : t + 0.5;
+                if (hi <= lo) continue;
+                rt = hi - lo;
+            }
             const double ct = hx_cone_factor(g, t);
             for (int s = s_lo; s <= s_hi; s++) {
                 const double ts = hx_trap_cdf(tau, s + 0.5) - hx_trap_cdf(tau, s - 0.5);
@@ -166,6 +201,7 @@ static int hx_check(const orc_helix_geom *g)
     if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0) || !(g->ds > 0) || !(g->dt > 0) || !(g->dso > 0) ||
         !(g->dsd > 0))
         return 1;
+    if (g->axial != 0 && g->axial != 1) return 1;
     return 0;
 }
 

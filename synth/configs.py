@@ -153,6 +153,8 @@ class HelicalConeGeometry:
       ``(s-(ns-1)/2+offset_s) ds/dsd``) by ``nt`` rows of height ``dt``
       (row t at height ``(t-(nt-1)/2+offset_t) dt`` on the cylinder);
       sinograms are stored ``[view][row][cell]``.
+    * ``axial`` names the projector's axial footprint model: "rect" (SF-TR)
+      or "trap" (SF-TT).
     """
 
     nx: int
@@ -176,6 +178,7 @@ class HelicalConeGeometry:
     offset_z: float = 0.0
     offset_s: float = 0.0
     offset_t: float = 0.0
+    axial: str = "rect"  # axial footprint: "rect" (SF-TR) or "trap" (SF-TT)
 
     @property
     def dgamma(self) -> float:
