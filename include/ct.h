@@ -56,11 +56,31 @@ typedef enum {
 
 enum { CT_FAN_ARC_2D = 1, CT_HELICAL_CONE_ARC = 2 };
 
+/* Axial footprint of the helical projector (the 3-D separable-footprint
+ * method the paper cites for A, Sec. III, has two axial models):
+ * CT_AXIAL_RECT (SF-TR): the voxel's z-extent magnified at its column
+ * centre's distance from the source, a rectangle in the detector row
+ * coordinate; CT_AXIAL_TRAP (SF-TT): a trapezoid whose edges ramp between the
+ * magnifications of the column's nearest and farthest (x, y) corners. */
+enum { CT_AXIAL_RECT = 0, CT_AXIAL_TRAP = 1 };
+
 typedef struct ct_geom ct_geom; /* opaque; owns device geometry tables and workspace */
 
 /* Scan geometry (plain data, copied by ct_geom_create).  Lengths in mm,
  * angles in degrees.  For CT_FAN_ARC_2D the fields nz, dz, offset_z, nt, dt,
- * offset_t and pitch are ignored. */
+ * offset_t, pitch and axial are ignored.
+ *
+ * CT_HELICAL_CONE_ARC (3-D helical cone-beam, cylindrical detector): volumes
+ * are float32 [nz][ny][nx], voxel (ix, iy, iz) centred at the pixel's (x, y)
+ * and z = (iz - (nz-1)/2 + offset_z) dz; sinograms are float32
+ * [view][row][cell]; row t lies at height (t - (nt-1)/2 + offset_t) dt on the
+ * cylinder of radius dsd.  The views span orbit_deg (several turns allowed);
+ * the source rises z_src = pitch * (nt dt dso / dsd) * (beta - beta_mid) / 2 pi
+ * (table feed per turn = pitch times the detector's axial coverage at the
+ * isocentre, centred on the volume at mid-scan).  The system matrix is
+ * a = l_xy * c_t * T(s) * R(t): T the transaxial trapezoid footprint (as in
+ * 2-D), l_xy its chord, c_t = 1 / cos(cone angle of row t), R the axial
+ * footprint selected by `axial`. */
 typedef struct {
     int kind;
     int nx, ny, nz;
@@ -72,6 +92,7 @@ typedef struct {
     double dso, dsd;           /* source-to-isocentre, source-to-detector */
     double orbit_deg, orbit_start_deg;
     double pitch;
+    int axial; /* CT_AXIAL_RECT or CT_AXIAL_TRAP (helical only; 0 for 2-D) */
 } ct_geom_desc;
 
 /* Create the device-side description of a scan geometry (Sec. III: A is the
@@ -91,8 +112,8 @@ void ct_geom_destroy(ct_geom *g);
  * a_ij that the projectors otherwise evaluate on the fly (Sec. III: A is the
  * forward projection matrix of the scan), stored once in device memory
  * owned by g as (1) ray-major compressed rows of (pixel, a_ij) for the
- * ray-driven forward projector and (2) per-(view, pixel) footprint
- * trapezoids for the voxel-driven back-projector.  Afterwards ct_forward,
+ * ray-driven forward projector and (2) per-(view, pixel) records of the
+ * pixel's cell weights for the voxel-driven back-projector.  Afterwards ct_forward,
  * ct_back, ct_sqs_diag and ct_relaxed_oslalm_solve stream it instead of
  * recomputing footprints; results stay within FP32 rounding of the
  * on-the-fly path.  max_bytes: refuse with CT_ENOMEM (nothing kept) when the

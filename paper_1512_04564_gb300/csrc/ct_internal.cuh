@@ -72,6 +72,7 @@ struct HelixDev {
     const float *row_c;      // [nt]: 1 / cos(cone angle of row t) = sqrt(1 + (v_t / dsd)^2)
     const float4 *tile_ax;   // [na][ntiles]: at each anchor tile's centre, voxels per row 1/a = L/kA and
                              // rows per voxel a = kA/L, each as hi + lo floats (FP64-derived)
+    int trap;                // axial footprint: 0 rectangle (SF-TR), 1 trapezoid (SF-TT)
 };
 
 }  // namespace ct
@@ -357,7 +358,8 @@ cudaError_t launch_reg_update_helix(const ct_geom *g, const SolveDev &S, float b
                                     int maxcurv, cudaStream_t st);
 cudaError_t launch_rmsd_helix(const ct_geom *g, const float *x, const float *xr, float r2max, double *partial,
                               int *counter, float *trace, int M, float hu, cudaStream_t st);
-int helix_chunk_voxels(double a_max);  // largest chunk whose magnified extent fits the row buffer, 0 if none
+// largest chunk whose magnified extent (plus extra_rows) fits the row buffer, 0 if none
+int helix_chunk_voxels(double a_max, double extra_rows);
 int helix_max_rows();
 int helix_max_span();
 int helix_max_march();

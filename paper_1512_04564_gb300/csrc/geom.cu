@@ -155,7 +155,29 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
                       helix_max_span());
             return CT_ENOTSUP;
         }
-        zc = helix_chunk_voxels(d->dz * d->dsd / d->dt / (d->dso - r_img));
+        if (d->axial != CT_AXIAL_RECT && d->axial != CT_AXIAL_TRAP) {
+            set_error("unknown axial footprint %d", d->axial);
+            return CT_EINVAL;
+        }
+        const double a_max = d->dz * d->dsd / d->dt / (d->dso - r_img);
+        double extra_rows = 0.0;
+        if (d->axial == CT_AXIAL_TRAP) {
+            // ramp half-width h = eps |z - z_src| / dz voxels, eps = (L_max - L_min) / (L_max + L_min)
+            // <= diagonal / (2 (dso - r_img)); the kernels need h < 1/2 (a voxel's two ramps apart)
+            const double eps_max = std::hypot(d->dx, d->dy) / (2.0 * (d->dso - r_img));
+            const double face0 = (-d->nz / 2.0 + d->offset_z) * d->dz, face1 = face0 + d->nz * d->dz;
+            const double cover = d->nt * d->dt * d->dso / d->dsd;
+            const double zs = std::fabs(d->pitch) * cover * std::fabs(d->orbit_deg) / 720.0;  // |z_src| at the ends
+            const double zmax = std::fmax(std::fabs(face0), std::fabs(face1)) + zs;
+            const double h_max = eps_max * zmax / d->dz;
+            if (!(h_max < 0.5)) {
+                set_error("trapezoid axial footprints too wide for the voxels (ramp half-width up to %.3g voxels; "
+                          "needs < 0.5)", h_max);
+                return CT_ENOTSUP;
+            }
+            extra_rows = 2.0 * h_max * a_max;
+        }
+        zc = helix_chunk_voxels(a_max, extra_rows);
         if (zc == 0) {
             set_error("voxels too tall for the detector rows: one voxel's shadow exceeds the row buffer");
             return CT_ENOTSUP;
@@ -285,6 +307,7 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         g->hx.view_zb = g->d_view_zb;
         g->hx.row_c = g->d_row_c;
         g->hx.tile_ax = g->d_tile_ax;
+        g->hx.trap = d->axial == CT_AXIAL_TRAP ? 1 : 0;
     }
     F.anchor = g->d_anchor;
     F.view_cs = g->d_view_cs;

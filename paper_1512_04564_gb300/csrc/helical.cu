@@ -16,6 +16,18 @@
 //           falls at row coordinate u_k = a (k + zb_v) + ct0, a = dz dsd / (dt L);
 //   c_t:    1 / cos(cone angle of row t).
 //
+// With the trapezoid axial footprint (SF-TT) the voxel's z-faces project at
+// every magnification between those of the column's farthest and nearest
+// corners (L_max, L_min), so each face's shadow edge becomes a linear ramp.
+// Summed over a column, the voxels' trapezoids are the rectangle model at the
+// ramps' centre (L = the harmonic mean of L_min and L_max) with each jump from
+// x_{k-1} to x_k replaced by a ramp of half-width h_k = eps |z_k - z_src| / dz
+// voxels, eps = (L_max - L_min) / (L_max + L_min).  So both kernels run the
+// rectangle arithmetic at that L and add, at every row boundary that a ramp
+// straddles at distance d (voxels) from its centre, (x_k - x_{k-1}) a
+// (h_k - d)^2 / (4 h_k) to the row below and subtract it from the row above
+// (ramps of one column never overlap: the geometry keeps h_k < 1/2).
+//
 // Forward projector (ray-driven, cell-owned outputs, no atomics): one CTA per
 // (view, 32 adjacent cells); its warps split the image columns of the
 // bundle's transaxial fan wedge.  Per round a warp stages 32 columns, one per
@@ -97,21 +109,65 @@ struct ColumnAxial {
     float ia_hi, ia_lo, a_hi, a_lo;
 };
 
+//
+// TT (trapezoid axial footprint): the scale is taken at the harmonic mean H of
+// the column's nearest and farthest corner distances, L_min,max^2 = L^2 + q -+ P
+// (P = |C_x| dx + |C_y| dy with C the column centre relative to the source in
+// the world frame, q = (dx^2 + dy^2) / 4), again as a small correction
+// H - L = (L (d+ + d-) + 2 d+ d-) / (2L + d+ + d-), d+- = L_max,min - L; eps
+// receives (L_max - L_min) / (L_max + L_min).
+template <bool TT>
 __device__ __forceinline__ ColumnAxial column_axial(const HelixDev &H, float4 A, float4 X, float cb, float sb,
-                                                    float ox, float oy)
+                                                    float ox, float oy, float pdx, float pdy, float &eps)
 {
     const float dpar = fmaf(ox, cb, oy * sb), dperp = fmaf(oy, cb, -ox * sb);
     const float cpar = A.x + dpar, cperp = A.y + dperp;
     const float L = sqrtf(fmaf(cpar, cpar, cperp * cperp));
     const float LA = X.x * H.kA;
     const float num = fmaf(2.0f, fmaf(A.x, dpar, A.y * dperp), fmaf(dpar, dpar, dperp * dperp));
-    const float dL = __fdividef(num, L + LA);
+    float dL = __fdividef(num, L + LA);
+    float Lc = L;
+    eps = 0.0f;
+    if (TT) {
+        const float Cx = fmaf(cpar, cb, -cperp * sb), Cy = fmaf(cpar, sb, cperp * cb);
+        const float P = fmaf(fabsf(Cx), pdx, fabsf(Cy) * pdy);
+        const float q = 0.25f * fmaf(pdx, pdx, pdy * pdy);
+        const float dp = __fdividef(P + q, sqrtf(fmaf(L, L, P + q)) + L);
+        const float dm = __fdividef(q - P, sqrtf(fmaf(L, L, q - P)) + L);
+        const float den = 2.0f * L + dp + dm;
+        const float dH = __fdividef(fmaf(L, dp + dm, 2.0f * dp * dm), den);
+        eps = __fdividef(dp - dm, den);
+        dL += dH;
+        Lc = L + dH;
+    }
     ColumnAxial C;
     C.ia_hi = X.x;
     C.ia_lo = fmaf(dL, H.inv_kA, X.y);
     C.a_hi = X.z;
-    C.a_lo = fmaf(-X.z, __fdividef(dL, L), X.w);
+    C.a_lo = fmaf(-X.z, __fdividef(dL, Lc), X.w);
     return C;
+}
+
+// Ramp correction at a row boundary that lies at voxel coordinate z = K + f
+// (0 <= f < 1) of a column: sum over the ramps of boundaries K and K+1 that
+// straddle it of (x_k - x_{k-1}) (h_k - d)^2 / (4 h_k), d its distance from
+// the ramp's centre, h_k = eps |k + zb|.  xv(k) returns x_k (0 outside).
+template <class XV>
+__device__ __forceinline__ float ramp_correction(int K, float f, float eps, float zb, XV xv)
+{
+    float c = 0.0f;
+    const float h0 = eps * fabsf((float)K + zb);
+    if (f < h0) {
+        const float d = h0 - f;
+        c = (xv(K) - xv(K - 1)) * __fdividef(d * d, 4.0f * h0);
+    }
+    const float h1 = eps * fabsf((float)(K + 1) + zb);
+    const float g = 1.0f - f;
+    if (g < h1) {
+        const float d = h1 - g;
+        c = fmaf(xv(K + 1) - xv(K), __fdividef(d * d, 4.0f * h1), c);
+    }
+    return c;
 }
 
 // Detector-row boundary b (row coordinate b - 1/2) of a column, in voxel
@@ -131,7 +187,7 @@ __device__ __forceinline__ void row_boundary(float b_minus_c, float ia_hi, float
     else if (f >= 1.0f) { K += 1; f -= 1.0f; }
 }
 
-template <int MODE, int NT>
+template <int MODE, int NT, bool TT>
 __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, HelixDev H, const float *__restrict__ x,
                                                                 const int *__restrict__ views, int nviews,
                                                                 float *__restrict__ out, const float *__restrict__ y,
@@ -148,6 +204,7 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
     __shared__ int2 s_kr[kHxWarps][32];     // voxel range [kmin, kmax] its rows reach
     __shared__ int s_k0[kHxWarps][32];      // lowest row boundary K + f
     __shared__ float s_f0[kHxWarps][32];
+    __shared__ float s_eps[kHxWarps][TT ? 32 : 1];  // TT: the column's ramp-width factor eps
     __shared__ float s_xw[kHxWarps][64];    // z-window of the column being profiled
     extern __shared__ float4 s_dyn4[];
     float *s_p = reinterpret_cast<float *>(s_dyn4);  // [warp][32][PS] profiles; later [warp][NT][32] partial sums
@@ -258,7 +315,9 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
             cf = F.n + j0 - s0;
             // axial parameters; the lowest and highest row boundaries give the voxel range
             const float4 X = __ldg(&H.tile_ax[(size_t)v * (G.ntx * G.nty) + ty * G.ntx + tx]);
-            const ColumnAxial C = column_axial(H, A, X, cs.x, cs.y, ox, oy);
+            float eps;
+            const ColumnAxial C = column_axial<TT>(H, A, X, cs.x, cs.y, ox, oy, G.dx, G.dy, eps);
+            if (TT) s_eps[warp][lane] = eps;
             const float cz = fmaf(H.ofr, C.ia_hi + C.ia_lo, -zb.y);
             int K0, K1;
             float f0, f1;
@@ -300,6 +359,16 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
                 int Kc = s_k0[warp][l];
                 float fc = s_f0[warp][l];
                 const float *xw = s_xw[warp] - kr.x;
+                // TT: x_k of this column for the ramp corrections (0 outside the volume)
+                const float *xg_l = x + (size_t)s_col[warp][l] * nz;
+                auto xv = [&](int kk) -> float {
+                    if (kk < 0 || kk >= nz) return 0.0f;
+                    if (MODE == FP_ONES_W) return 1.0f;
+                    return (unsigned)(kk - kr.x) < 64u ? xw[kk] : __ldg(&xg_l[kk]);
+                };
+                const float eps_l = TT ? s_eps[warp][TT ? l : 0] : 0.0f;
+                const float zbf = zb.x + zb.y;
+                float corr_c = TT ? ramp_correction(Kc, fc, eps_l, zbf, xv) : 0.0f;
 #pragma unroll
                 for (int r0 = 0; r0 < NT; r0 += 32) {
                     const int r = r0 + lane;
@@ -315,29 +384,38 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
                     Kc = __shfl_sync(kFull, Kh, 31);
                     fc = __shfl_sync(kFull, fh, 31);
                     float sacc = 0.0f;
+                    if (TT) {  // + the ramps at the row's upper boundary, - those at its lower one
+                        const float ch = ramp_correction(Kh, fh, eps_l, zbf, xv);
+                        float cl = __shfl_up_sync(kFull, ch, 1);
+                        if (lane == 0) cl = corr_c;
+                        corr_c = __shfl_sync(kFull, ch, 31);
+                        sacc = ch - cl;
+                    }
                     if (r < nt && Kh >= 0 && Kl < nz) {
                         const int k0 = max(Kl, 0), k1 = min(Kh, nz - 1);
                         const float g0 = Kl < 0 ? 0.0f : fl, g1 = Kh >= nz ? 1.0f : fh;
+                        float rs;
                         if (MODE == FP_ONES_W) {
-                            sacc = (float)(k1 - k0) + (g1 - g0);
+                            rs = (float)(k1 - k0) + (g1 - g0);
                         } else if (k1 - kr.x < 64) {
                             if (k0 == k1) {
-                                sacc = xw[k0] * (g1 - g0);
+                                rs = xw[k0] * (g1 - g0);
                             } else {
-                                sacc = xw[k0] * (1.0f - g0);
-                                for (int kk = k0 + 1; kk < k1; kk++) sacc += xw[kk];
-                                sacc = fmaf(xw[k1], g1, sacc);
+                                rs = xw[k0] * (1.0f - g0);
+                                for (int kk = k0 + 1; kk < k1; kk++) rs += xw[kk];
+                                rs = fmaf(xw[k1], g1, rs);
                             }
                         } else {  // a row beyond the staged 64-voxel window
                             const float *xg = x + (size_t)s_col[warp][l] * nz;
                             if (k0 == k1) {
-                                sacc = __ldg(&xg[k0]) * (g1 - g0);
+                                rs = __ldg(&xg[k0]) * (g1 - g0);
                             } else {
-                                sacc = __ldg(&xg[k0]) * (1.0f - g0);
-                                for (int kk = k0 + 1; kk < k1; kk++) sacc += __ldg(&xg[kk]);
-                                sacc = fmaf(__ldg(&xg[k1]), g1, sacc);
+                                rs = __ldg(&xg[k0]) * (1.0f - g0);
+                                for (int kk = k0 + 1; kk < k1; kk++) rs += __ldg(&xg[kk]);
+                                rs = fmaf(__ldg(&xg[k1]), g1, rs);
                             }
                         }
+                        sacc += rs;
                     }
                     if (r < NT) pl[r] = P.z * sacc;
                 }
@@ -422,29 +500,62 @@ __device__ __forceinline__ void bp_helix_epilogue(const SolveDev &S, float *__re
     }
 }
 
-// Running sum of the row sums at voxel boundary k of a column, over rows
-// [t_lo, t_lo + nr): qb[i] = sum of q over the first i rows, linear inside a
-// row.  The boundary's row coordinate is u + 1/2 = (k + zbi)(a_hi + a_lo) +
-// zbf a + ct0i + 1/2 - ofr = r + fr (row r, 0 <= fr < 1); with k + zbi and
-// ct0i + 1/2 - r exact, fr comes from one fma at magnitude ~1.  cb0 = zbf a - ofr.
-__device__ __forceinline__ float row_cdf(const float *qb, int k, float zbi, float a_hi, float a_lo, float cb0,
-                                         float c_half, int t_lo, int nr, int nt)
+// Row position of voxel boundary k of a column: its row coordinate is
+// u + 1/2 = (k + zbi)(a_hi + a_lo) + zbf a + ct0i + 1/2 - ofr = r + fr (row r,
+// 0 <= fr < 1); with k + zbi and ct0i + 1/2 - r exact, fr comes from one fma
+// at magnitude ~1.  cb0 = zbf a - ofr.
+struct RowPos {
+    int r;
+    float fr;
+};
+
+__device__ __forceinline__ RowPos row_pos(int k, float zbi, float a_hi, float a_lo, float cb0, float c_half, int nt)
 {
     const float Z = (float)k + zbi;
     const float sm = fmaf(Z, a_lo, cb0);
     const float approx = fmaf(Z, a_hi, sm + c_half);
-    int r = (int)floorf(fminf(fmaxf(approx, -2.0f), (float)nt + 1.0f));
-    float fr = fmaf(Z, a_hi, c_half - (float)r) + sm;
-    if (fr < 0.0f) { r -= 1; fr += 1.0f; }
-    else if (fr >= 1.0f) { r += 1; fr -= 1.0f; }
-    const int rel = r - t_lo;
+    RowPos p;
+    p.r = (int)floorf(fminf(fmaxf(approx, -2.0f), (float)nt + 1.0f));
+    p.fr = fmaf(Z, a_hi, c_half - (float)p.r) + sm;
+    if (p.fr < 0.0f) { p.r -= 1; p.fr += 1.0f; }
+    else if (p.fr >= 1.0f) { p.r += 1; p.fr -= 1.0f; }
+    return p;
+}
+
+// Running sum of the row sums at a voxel boundary, over rows [t_lo, t_lo + nr):
+// qb[i] = sum of q over the first i rows, linear inside a row.
+__device__ __forceinline__ float row_cdf(const float *qb, RowPos p, int t_lo, int nr)
+{
+    const int rel = p.r - t_lo;
     if (rel < 0) return 0.0f;
     if (rel >= nr) return qb[nr * kHxBpCols];
     const float lo = qb[rel * kHxBpCols], hi = qb[(rel + 1) * kHxBpCols];
-    return fmaf(fr, hi - lo, lo);
+    return fmaf(p.fr, hi - lo, lo);
 }
 
-template <int MODE, int ZC>
+// TT: adjoint of the ramp correction of voxel boundary k (at row position p,
+// ramp half-width hw rows): sum over the row boundaries the ramp straddles of
+// (hw - d)^2 / (4 hw) (q below - q above); voxel k receives +, voxel k-1 -.
+__device__ __forceinline__ float ramp_adjoint(const float *qb, RowPos p, float hw, int t_lo, int nr)
+{
+    auto q = [&](int t) -> float {
+        const int i = t - t_lo;
+        return (i >= 0 && i < nr) ? qb[(i + 1) * kHxBpCols] - qb[i * kHxBpCols] : 0.0f;
+    };
+    float D = 0.0f;
+    if (p.fr < hw) {
+        const float d = hw - p.fr;
+        D = __fdividef(d * d, 4.0f * hw) * (q(p.r - 1) - q(p.r));
+    }
+    const float g = 1.0f - p.fr;
+    if (g < hw) {
+        const float d = hw - g;
+        D = fmaf(__fdividef(d * d, 4.0f * hw), q(p.r) - q(p.r + 1), D);
+    }
+    return D;
+}
+
+template <int MODE, int ZC, bool TT>
 __global__ void __launch_bounds__(kHxBpCols) bp_helix_kernel(FanDev G, HelixDev H, const float *__restrict__ sino,
                                                              const int *__restrict__ views, int nviews,
                                                              float *__restrict__ xo, float scale, int accumulate,
@@ -478,13 +589,20 @@ __global__ void __launch_bounds__(kHxBpCols) bp_helix_kernel(FanDev G, HelixDev 
             const float2 cs = __ldg(&G.view_cs[v]);
             const float4 A = __ldg(&G.anchor[(size_t)v * ntiles + tile]);
             const float2 zb = __ldg(&H.view_zb[v]);
-            const ColumnAxial Cx = column_axial(H, A, __ldg(&H.tile_ax[(size_t)v * ntiles + tile]), cs.x, cs.y, ox, oy);
+            float eps;
+            const ColumnAxial Cx = column_axial<TT>(H, A, __ldg(&H.tile_ax[(size_t)v * ntiles + tile]), cs.x, cs.y,
+                                                    ox, oy, G.dx, G.dy, eps);
             const float a = Cx.a_hi + Cx.a_lo;
-            // rows the chunk's shadow reaches (approximate ends, widened by 1e-3 row)
-            const float uA = fmaf(a, (float)z0 + zb.x + zb.y, H.ct0);
+            const float zbf = zb.x + zb.y;
+            // rows the chunk's shadow reaches (approximate ends, widened by 1e-3 row and, with
+            // trapezoids, by the end faces' ramp half-widths)
+            const float ea = eps * a;
+            const float hwA = TT ? ea * fabsf((float)z0 + zbf) : 0.0f;
+            const float hwB = TT ? ea * fabsf((float)(z0 + ZC) + zbf) : 0.0f;
+            const float uA = fmaf(a, (float)z0 + zbf, H.ct0);
             const float uB = fmaf(a, (float)ZC, uA);
-            const int t_lo = (int)fmaxf(floorf(uA + 0.499f), 0.0f);
-            const int t_hi = (int)fminf(floorf(uB + 0.501f), (float)(nt - 1));
+            const int t_lo = (int)fmaxf(floorf(uA - hwA + 0.499f), 0.0f);
+            const int t_hi = (int)fminf(floorf(uB + hwB + 0.501f), (float)(nt - 1));
             if (t_lo > t_hi) continue;  // the chunk's shadow misses the detector in this view
             const Footprint F = sf_footprint(G, cs.x, cs.y, A, ox, oy);
             const int j0 = (int)floorf(F.t0 - 0.5f) + 1;
@@ -512,12 +630,20 @@ __global__ void __launch_bounds__(kHxBpCols) bp_helix_kernel(FanDev G, HelixDev 
             const int nr = t_hi - t_lo + 1;
             const float cb0 = fmaf(zb.y, a, -H.ofr);
             const float c_half = H.ct0i + 0.5f;
-            float Cp = row_cdf(qb, z0, zb.x, Cx.a_hi, Cx.a_lo, cb0, c_half, t_lo, nr, nt);
+            RowPos pp = row_pos(z0, zb.x, Cx.a_hi, Cx.a_lo, cb0, c_half, nt);
+            float Cp = row_cdf(qb, pp, t_lo, nr);
+            float Dp = TT ? ramp_adjoint(qb, pp, hwA, t_lo, nr) : 0.0f;
 #pragma unroll
             for (int i = 0; i < ZC; i++) {
-                const float C = row_cdf(qb, z0 + i + 1, zb.x, Cx.a_hi, Cx.a_lo, cb0, c_half, t_lo, nr, nt);
+                const RowPos p = row_pos(z0 + i + 1, zb.x, Cx.a_hi, Cx.a_lo, cb0, c_half, nt);
+                const float C = row_cdf(qb, p, t_lo, nr);
                 acc[i] += C - Cp;
                 Cp = C;
+                if (TT) {
+                    const float D = ramp_adjoint(qb, p, ea * fabsf((float)(z0 + i + 1) + zbf), t_lo, nr);
+                    acc[i] += Dp - D;
+                    Dp = D;
+                }
             }
         }
         const size_t jc = ((size_t)iy * G.nx + ix) * H.nz;
@@ -719,7 +845,7 @@ Pot make_pot(int potential, float delta, int maxcurv = 0)
     return Pot{potential, potential == CT_POT_QUADRATIC ? 0.0f : 1.0f / delta, maxcurv};
 }
 
-template <int MODE>
+template <int MODE, bool TT>
 cudaError_t fp_helix_dispatch(const ct_geom *g, const float *x, const int *views, int nviews, float *out,
                               const float *y, const float *w, cudaStream_t st)
 {
@@ -729,16 +855,16 @@ cudaError_t fp_helix_dispatch(const ct_geom *g, const float *x, const int *views
     const int nt = H.nt;
     const int nmax = G.nx > G.ny ? G.nx : G.ny;
 #define CT_FP_HX(NTV)                                                                                       \
-    fp_helix_kernel<MODE, NTV><<<blocks, kHxWarps * 32,                                                     \
-                                 sizeof(float) * kHxWarps * 32 * (NTV + 4) + sizeof(int) * (2 * nmax + 1), \
-                                 st>>>(G, H, x, views, nviews, out, y, w)
+    fp_helix_kernel<MODE, NTV, TT><<<blocks, kHxWarps * 32,                                                 \
+                                     sizeof(float) * kHxWarps * 32 * (NTV + 4) + sizeof(int) * (2 * nmax + 1), \
+                                     st>>>(G, H, x, views, nviews, out, y, w)
     if (nt <= 8) CT_FP_HX(8);
     else if (nt <= 16) CT_FP_HX(16);
     else if (nt <= 32) CT_FP_HX(32);
     else {
         const size_t dyn = sizeof(float) * kHxWarps * 32 * (64 + 4) + sizeof(int) * (2 * nmax + 1);
-        cudaError_t e = cudaFuncSetAttribute(fp_helix_kernel<MODE, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)dyn);
+        cudaError_t e = cudaFuncSetAttribute(fp_helix_kernel<MODE, 64, TT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
         CT_FP_HX(64);
     }
@@ -746,7 +872,7 @@ cudaError_t fp_helix_dispatch(const ct_geom *g, const float *x, const int *views
     return cudaGetLastError();
 }
 
-template <int MODE>
+template <int MODE, bool TT>
 cudaError_t bp_helix_dispatch(const ct_geom *g, const float *sino, const int *views, int nviews, float *x,
                               float scale, int accumulate, const SolveDev &S, cudaStream_t st)
 {
@@ -754,22 +880,24 @@ cudaError_t bp_helix_dispatch(const ct_geom *g, const float *sino, const int *vi
     const HelixDev &H = g->hx;
     const int zc = g->hx_zc;
     dim3 grid((G.nx + 15) / 16, (G.ny + 7) / 8, (H.nz + zc - 1) / zc);
+#define CT_BP_HX(Z) bp_helix_kernel<MODE, Z, TT><<<grid, kHxBpCols, 0, st>>>(G, H, sino, views, nviews, x, scale, accumulate, S)
     switch (zc) {
-    case 16: bp_helix_kernel<MODE, 16><<<grid, kHxBpCols, 0, st>>>(G, H, sino, views, nviews, x, scale, accumulate, S); break;
-    case 8: bp_helix_kernel<MODE, 8><<<grid, kHxBpCols, 0, st>>>(G, H, sino, views, nviews, x, scale, accumulate, S); break;
-    case 4: bp_helix_kernel<MODE, 4><<<grid, kHxBpCols, 0, st>>>(G, H, sino, views, nviews, x, scale, accumulate, S); break;
-    case 2: bp_helix_kernel<MODE, 2><<<grid, kHxBpCols, 0, st>>>(G, H, sino, views, nviews, x, scale, accumulate, S); break;
-    default: bp_helix_kernel<MODE, 1><<<grid, kHxBpCols, 0, st>>>(G, H, sino, views, nviews, x, scale, accumulate, S); break;
+    case 16: CT_BP_HX(16); break;
+    case 8: CT_BP_HX(8); break;
+    case 4: CT_BP_HX(4); break;
+    case 2: CT_BP_HX(2); break;
+    default: CT_BP_HX(1); break;
     }
+#undef CT_BP_HX
     return cudaGetLastError();
 }
 
 }  // namespace
 
-int helix_chunk_voxels(double a_max)
+int helix_chunk_voxels(double a_max, double extra_rows)
 {
     for (int zc = 16; zc >= 1; zc >>= 1)
-        if (std::ceil(zc * a_max) + 2.0 <= (double)kHxQMax) return zc;
+        if (std::ceil(zc * a_max + extra_rows) + 2.0 <= (double)kHxQMax) return zc;
     return 0;
 }
 
@@ -780,10 +908,17 @@ int helix_max_march() { return kHxMaxMarch; }
 cudaError_t launch_fp_helix(const ct_geom *g, int mode, const float *x, const int *views, int nviews, float *out,
                             const float *y, const float *w, cudaStream_t st)
 {
+    const bool tt = g->hx.trap != 0;
     switch (mode) {
-    case FP_PLAIN: return fp_helix_dispatch<FP_PLAIN>(g, x, views, nviews, out, y, w, st);
-    case FP_RESID: return fp_helix_dispatch<FP_RESID>(g, x, views, nviews, out, y, w, st);
-    default: return fp_helix_dispatch<FP_ONES_W>(g, x, views, nviews, out, y, w, st);
+    case FP_PLAIN:
+        return tt ? fp_helix_dispatch<FP_PLAIN, true>(g, x, views, nviews, out, y, w, st)
+                  : fp_helix_dispatch<FP_PLAIN, false>(g, x, views, nviews, out, y, w, st);
+    case FP_RESID:
+        return tt ? fp_helix_dispatch<FP_RESID, true>(g, x, views, nviews, out, y, w, st)
+                  : fp_helix_dispatch<FP_RESID, false>(g, x, views, nviews, out, y, w, st);
+    default:
+        return tt ? fp_helix_dispatch<FP_ONES_W, true>(g, x, views, nviews, out, y, w, st)
+                  : fp_helix_dispatch<FP_ONES_W, false>(g, x, views, nviews, out, y, w, st);
     }
 }
 
@@ -792,10 +927,17 @@ cudaError_t launch_bp_helix(const ct_geom *g, int mode, const float *sino, const
 {
     SolveDev s0{};
     const SolveDev &SS = S ? *S : s0;
+    const bool tt = g->hx.trap != 0;
     switch (mode) {
-    case BP_PLAIN: return bp_helix_dispatch<BP_PLAIN>(g, sino, views, nviews, x, scale, accumulate, SS, st);
-    case BP_SOLVE_INIT: return bp_helix_dispatch<BP_SOLVE_INIT>(g, sino, views, nviews, x, scale, accumulate, SS, st);
-    default: return bp_helix_dispatch<BP_SOLVE_UPDATE>(g, sino, views, nviews, x, scale, accumulate, SS, st);
+    case BP_PLAIN:
+        return tt ? bp_helix_dispatch<BP_PLAIN, true>(g, sino, views, nviews, x, scale, accumulate, SS, st)
+                  : bp_helix_dispatch<BP_PLAIN, false>(g, sino, views, nviews, x, scale, accumulate, SS, st);
+    case BP_SOLVE_INIT:
+        return tt ? bp_helix_dispatch<BP_SOLVE_INIT, true>(g, sino, views, nviews, x, scale, accumulate, SS, st)
+                  : bp_helix_dispatch<BP_SOLVE_INIT, false>(g, sino, views, nviews, x, scale, accumulate, SS, st);
+    default:
+        return tt ? bp_helix_dispatch<BP_SOLVE_UPDATE, true>(g, sino, views, nviews, x, scale, accumulate, SS, st)
+                  : bp_helix_dispatch<BP_SOLVE_UPDATE, false>(g, sino, views, nviews, x, scale, accumulate, SS, st);
     }
 }
 

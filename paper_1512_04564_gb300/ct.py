@@ -19,6 +19,7 @@ CT_OK, CT_EINVAL, CT_ENOMEM, CT_ECUDA, CT_ETIMEOUT, CT_ENOTSUP = range(6)
 CT_FAN_ARC_2D = 1
 CURVATURES = {"huber": 0, "max": 1}
 CT_HELICAL_CONE_ARC = 2
+AXIAL = {"rect": 0, "trap": 1}  # CT_AXIAL_RECT (SF-TR), CT_AXIAL_TRAP (SF-TT)
 CT_POT_HYPERBOLA, CT_POT_FAIR, CT_POT_QUADRATIC = 0, 1, 2
 CT_ALG_PROPOSED, CT_ALG_SIMPLE = 0, 1
 CT_FBP_RAMP, CT_FBP_HANN = 0, 1
@@ -37,7 +38,7 @@ class ct_geom_desc(ctypes.Structure):
         ("offset_s", ctypes.c_double), ("offset_t", ctypes.c_double),
         ("dso", ctypes.c_double), ("dsd", ctypes.c_double),
         ("orbit_deg", ctypes.c_double), ("orbit_start_deg", ctypes.c_double),
-        ("pitch", ctypes.c_double),
+        ("pitch", ctypes.c_double), ("axial", ctypes.c_int),
     ]
 
 
@@ -175,7 +176,7 @@ class Geometry:
 
     def __init__(self, *, nx, ny, dx, dy, ns, ds, na, dso, dsd, offset_x=0.0, offset_y=0.0, offset_s=0.0,
                  orbit_deg=360.0, orbit_start_deg=0.0, kind=CT_FAN_ARC_2D, nz=1, dz=1.0, offset_z=0.0, nt=1,
-                 dt=1.0, offset_t=0.0, pitch=0.0):
+                 dt=1.0, offset_t=0.0, pitch=0.0, axial="rect"):
         d = ct_geom_desc()
         d.kind = kind
         d.nx, d.ny, d.nz = nx, ny, nz
@@ -186,6 +187,7 @@ class Geometry:
         d.dso, d.dsd = dso, dsd
         d.orbit_deg, d.orbit_start_deg = orbit_deg, orbit_start_deg
         d.pitch = pitch
+        d.axial = AXIAL[axial] if isinstance(axial, str) else int(axial)
         self.desc = d
         self.kind = kind
         self.nx, self.ny, self.ns, self.na = nx, ny, ns, na
@@ -223,7 +225,8 @@ class Geometry:
         return cls(nx=g.nx, ny=g.ny, dx=g.dx, dy=g.dy, ns=g.ns, ds=g.ds, na=g.na, dso=g.dso, dsd=g.dsd,
                    offset_x=g.offset_x, offset_y=g.offset_y, offset_s=g.offset_s, orbit_deg=g.orbit_deg,
                    orbit_start_deg=g.orbit_start_deg, kind=CT_HELICAL_CONE_ARC, nz=g.nz, dz=g.dz,
-                   offset_z=g.offset_z, nt=g.nt, dt=g.dt, offset_t=g.offset_t, pitch=g.pitch)
+                   offset_z=g.offset_z, nt=g.nt, dt=g.dt, offset_t=g.offset_t, pitch=g.pitch,
+                   axial=getattr(g, "axial", "rect"))
 
     @classmethod
     def from_scan(cls, g) -> "Geometry":

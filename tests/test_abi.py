@@ -60,6 +60,14 @@ def test_host_validation_without_gpu():
     with pytest.raises(ct.CTError) as e:  # negative pixel size
         ct.Geometry(nx=16, ny=16, dx=-1.0, dy=1.0, ns=32, ds=1.0, na=10, dso=100.0, dsd=180.0)
     assert e.value.status == ct.CT_EINVAL
+    hx = dict(nx=16, ny=16, dx=4.0, dy=4.0, ns=64, ds=4.0, na=10, dso=250.0, dsd=450.0, kind=ct.CT_HELICAL_CONE_ARC,
+              nz=80, dz=1.0, nt=8, dt=2.0, pitch=0.5, orbit_deg=360.0)
+    with pytest.raises(ct.CTError) as e:  # unknown axial footprint
+        ct.Geometry(**hx, axial=7)
+    assert e.value.status == ct.CT_EINVAL
+    with pytest.raises(ct.CTError) as e:  # trapezoid ramps wider than half a voxel (80 slices near the source)
+        ct.Geometry(**hx, axial="trap")
+    assert e.value.status == ct.CT_ENOTSUP and "ramp" in str(e.value)
 
 
 def test_struct_layouts_match_header():
