@@ -24,6 +24,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referenc
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -75,6 +76,8 @@ def parse():
     ap.add_argument("--ws-epochs", type=int, default=12)
     ap.add_argument("--ws-batch", type=int, default=16)
     ap.add_argument("--ws-xstar-iters", type=int, default=400, help="M = 1 iterations of the held-out x*")
+    ap.add_argument("--axial", default="rect", choices=["rect", "trap"],
+                    help="helical workloads: axial footprint, rectangle (SF-TR) or trapezoid (SF-TT)")
     ap.add_argument("--xstar-iters-helix", type=int, default=300,
                     help="M = 1 iterations (after a 10-iteration M = 12 warm start) for the helical x*")
     return ap.parse_args()
@@ -381,7 +384,7 @@ def run_helix(args):
     import multiprocessing as mp
 
     cfg = synth.config_by_name(args.workload, 0)
-    g = cfg.geom
+    g = dataclasses.replace(cfg.geom, axial=args.axial)
     if args.kernels_only:
         import torch
 
@@ -393,7 +396,8 @@ def run_helix(args):
         xk = torch.from_numpy(synth.rasterize_solids(S, g, oversample=1, oversample_z=1).astype(np.float32)).cuda()
         M = args.M or cfg.M
         roof = helix_alu_roofline(ct, G, g, M, xk, {}, None)
-        print(json.dumps({"mode": "kernels-only", "workload": cfg.name, "M": M, "roofline": roof}), flush=True)
+        print(json.dumps({"mode": "kernels-only", "workload": cfg.name, "axial": args.axial, "M": M, "roofline": roof}),
+              flush=True)
         return 0
     t0 = time.perf_counter()
     step = max(1, g.na // 64)
@@ -464,6 +468,7 @@ def run_helix(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": cfg.name, "volume": list(shape), "voxel_mm": [g.dx, g.dy, g.dz],
                    "detector": [g.nt, g.ns], "views": g.na, "turns": g.orbit_deg / 360.0, "pitch": g.pitch,
+                   "axial": args.axial,
                    "alpha": alpha, "n_iter": n_iter, "n_iter_named": cfg.n_iter, "M_named": cfg.M, "M_best": best,
                    "x0": "zeros",
                    "beta_water_units": cfg.beta, "xstar": f"10 its M=12 + {args.xstar_iters_helix} its M=1",

@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
                 auto xv = [&](int kk) -> float {
                     if (kk < 0 || kk >= nz) return 0.0f;
                     if (MODE == FP_ONES_W) return 1.0f;
-                    return (unsigned)(kk - kr.x) < 64u ? xw[kk] : __ldg(&xg_l[kk]);
+                    return (kk >= kr.x && kk <= kr.y && kk - kr.x < 64) ? xw[kk] : __ldg(&xg_l[kk]);
                 };
                 const float eps_l = TT ? s_eps[warp][TT ? l : 0] : 0.0f;
                 const float zbf = zb.x + zb.y;

@@ -44,9 +44,10 @@ def test_forward_parity(ct, case, kind):
     ct.ct_forward(G, dev(x), y)
     ref = HelicalProjector(g).forward(x.astype(np.float64))
     assert rel_err(y.cpu().numpy(), ref) <= (TOL if kind == "phantom" else TOL_BORDER)
-    # and the model is not the rectangle one
-    rr = HelicalProjector(CASES[case]).forward(x.astype(np.float64))
-    assert np.max(np.abs(rr - ref)) > 10 * TOL * np.abs(ref).max()
+    # and the model is not the rectangle one (except where one voxel spans the whole detector row)
+    if case != "one_row":
+        rr = HelicalProjector(CASES[case]).forward(x.astype(np.float64))
+        assert np.max(np.abs(rr - ref)) > 10 * TOL * np.abs(ref).max()
 
 
 @pytest.mark.parametrize("case", list(TT_CASES))
