@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const BatchSlice *__r
                 const int m = t % B.M;
                 const int v0 = B.sub_off[m], nv = B.sub_off[m + 1] - v0;
                 const int ntiles = B.G.ntx * B.G.nty;
-                const float ox = ((float)lx - kTileHalf) * B.G.dx, oy = ((float)ly - kTileHalf) * B.G.dy;
+                const int ixc = min(ix, B.G.nx - 1), iyc = min(iy, B.G.ny - 1);  // anchor of an in-image pixel
                 float acc = 0.0f;
                 if (B.G.foot_t) {  // stored footprints, next view's prefetched
                     const size_t vstride = (size_t)ntiles * (kTile * kTile);
@@ -321,8 +321,7 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const BatchSlice *__r
                         if (__float_as_int(b.y) == kWideRecord) {  // wider than a record: on the fly
                             const int v = B.perm[v0 + k];
                             const float2 cs = __ldg(&B.G.view_cs[v]);
-                            const float4 A = __ldg(&B.G.anchor[(size_t)v * ntiles + tile]);
-                            acc += footprint_dot_coherent(sf_footprint(B.G, cs.x, cs.y, A, ox, oy), row, B.G.ns);
+                            acc += footprint_dot_coherent(pixel_footprint(B.G, v, cs.x, cs.y, ixc, iyc), row, B.G.ns);
                         } else {
                             acc += record_dot<true>(w, b, row, B.G.ns);
                         }
@@ -331,8 +330,7 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const BatchSlice *__r
                     for (int k = 0; k < nv; k++) {
                         const int v = B.perm[v0 + k];
                         const float2 cs = __ldg(&B.G.view_cs[v]);
-                        const float4 A = __ldg(&B.G.anchor[(size_t)v * ntiles + tile]);
-                        const Footprint F = sf_footprint(B.G, cs.x, cs.y, A, ox, oy);
+                        const Footprint F = pixel_footprint(B.G, v, cs.x, cs.y, ixc, iyc);
                         acc += footprint_dot_coherent(F, B.resid + (size_t)k * B.G.ns, B.G.ns);
                     }
                 }

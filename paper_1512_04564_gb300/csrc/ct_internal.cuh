@@ -12,13 +12,15 @@
 
 namespace ct {
 
-constexpr int kTile = 16;            // pixels per side of an anchor tile
-constexpr float kTileHalf = 7.5f;    // offset of a tile's centre from its first pixel, in pixels
+constexpr int kTile = 16;            // pixels per side of a back-projector tile (CTA) and record block
+constexpr int kAnchor = 8;           // pixels per side of an anchor tile (FP64-derived reference point)
+constexpr float kAnchorHalf = 3.5f;  // offset of an anchor tile's centre from its first pixel, in pixels
 
 // Fan-beam geometry as the kernels see it (passed by value).
 struct FanDev {
     int nx, ny, ns, na;
-    int ntx, nty;             // anchor tiles along x and y
+    int ntx, nty;             // 16x16 back-projector tiles along x and y
+    int nax, nay;             // 8x8 anchor tiles along x and y
     float dx, dy, hx, hy;     // pixel size and half size (mm)
     float inv_dx, inv_dy;
     float inv_dg;             // detector cells per radian (dsd / ds)
@@ -28,9 +30,10 @@ struct FanDev {
     float x_edge0, y_edge0;   // x of the left edge of column 0, y of the lower edge of row 0 (mm)
     float cxo, cyo;           // (nx-1)/2 - offset_x, (ny-1)/2 - offset_y (pixel index of the origin)
     int max_span;             // upper bound on the detector cells one pixel footprint overlaps
-    const float4 *anchor;     // [na][ntx*nty]: view-frame (t_par, t_perp) of the tile centre,
-                              // and its detector coordinate u = gamma/dgamma + (ns-1)/2 - offset_s
-                              // split into hi + lo floats (FP64-derived)
+    const float4 *anchor;     // [na][nay*nax]: view-frame (t_par, t_perp) of the anchor tile's centre
+                              // relative to the source, and its detector coordinate
+                              // u = gamma/dgamma + (ns-1)/2 - offset_s split into hi + lo floats
+                              // (FP64-derived)
     const float2 *view_cs;    // [na]: (cos beta, sin beta)
     const float *view_beta;   // [na]: beta in [0, 2 pi)
     // resident system matrix (ct_geom_precompute); null when footprints are computed on the fly
@@ -70,7 +73,7 @@ struct HelixDev {
     float kA, inv_kA;        // dz * dsd / dt (rows spanned by one voxel times its source distance), 1 / kA
     const float2 *view_zb;   // [na]: (z of the volume's lower face - z_src(view)) / dz = zbi + zbf, zbi integer
     const float *row_c;      // [nt]: 1 / cos(cone angle of row t) = sqrt(1 + (v_t / dsd)^2)
-    const float4 *tile_ax;   // [na][ntiles]: at each anchor tile's centre, voxels per row 1/a = L/kA and
+    const float4 *tile_ax;   // [na][nay*nax]: at each anchor tile's centre, voxels per row 1/a = L/kA and
                              // rows per voxel a = kA/L, each as hi + lo floats (FP64-derived)
     int trap;                // axial footprint: 0 rectangle (SF-TR), 1 trapezoid (SF-TT)
 };
@@ -244,13 +247,22 @@ __device__ __forceinline__ float footprint_dot(const Footprint &F, const float *
     return F.amp * fmaf(trap_area(F), rp, acc);
 }
 
-// Footprint of pixel (ix, iy) in view v (loads the tile anchor).
+// Anchor of pixel (ix, iy) in view v, and the pixel centre's offset from the
+// anchor tile's centre (mm, image axes).  Small anchor tiles keep the offsets,
+// and with them the FP32 error of the footprint's position, small.
+__device__ __forceinline__ float4 pixel_anchor(const FanDev &G, int v, int ix, int iy, float &ox, float &oy)
+{
+    const int ax = ix / kAnchor, ay = iy / kAnchor;
+    ox = ((float)(ix - ax * kAnchor) - kAnchorHalf) * G.dx;
+    oy = ((float)(iy - ay * kAnchor) - kAnchorHalf) * G.dy;
+    return __ldg(&G.anchor[(size_t)v * (G.nax * G.nay) + ay * G.nax + ax]);
+}
+
+// Footprint of pixel (ix, iy) in view v (loads its anchor).
 __device__ __forceinline__ Footprint pixel_footprint(const FanDev &G, int v, float cb, float sb, int ix, int iy)
 {
-    const int tx = ix / kTile, ty = iy / kTile;
-    const float4 A = __ldg(&G.anchor[(size_t)v * (G.ntx * G.nty) + ty * G.ntx + tx]);
-    const float ox = ((float)(ix - tx * kTile) - kTileHalf) * G.dx;
-    const float oy = ((float)(iy - ty * kTile) - kTileHalf) * G.dy;
+    float ox, oy;
+    const float4 A = pixel_anchor(G, v, ix, iy, ox, oy);
     return sf_footprint(G, cb, sb, A, ox, oy);
 }
 

@@ -193,6 +193,8 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     F.nx = d->nx; F.ny = d->ny; F.ns = d->ns; F.na = d->na;
     F.ntx = (d->nx + kTile - 1) / kTile;
     F.nty = (d->ny + kTile - 1) / kTile;
+    F.nax = (d->nx + kAnchor - 1) / kAnchor;
+    F.nay = (d->ny + kAnchor - 1) / kAnchor;
     F.dx = (float)d->dx; F.dy = (float)d->dy;
     F.hx = (float)(0.5 * d->dx); F.hy = (float)(0.5 * d->dy);
     F.inv_dx = (float)(1.0 / d->dx); F.inv_dy = (float)(1.0 / d->dy);
@@ -206,7 +208,7 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     // widest footprint: a pixel diagonal at the smallest source distance, plus partial cells at both ends
     F.max_span = (int)std::ceil(std::sqrt(d->dx * d->dx + d->dy * d->dy) / ((d->dso - r_img) * dg)) + 2;
 
-    const int na = d->na, ntiles = F.ntx * F.nty;
+    const int na = d->na, ntiles = F.nax * F.nay;  // anchor tiles
     std::vector<float2> cs(na);
     std::vector<float> bet(na);
     std::vector<float4> anc((size_t)na * ntiles);
@@ -218,15 +220,15 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         const double cb = std::cos(b), sb = std::sin(b);
         cs[v] = make_float2((float)cb, (float)sb);
         bet[v] = (float)b;
-        for (int ty = 0; ty < F.nty; ty++)
-            for (int tx = 0; tx < F.ntx; tx++) {
-                const double X = (tx * kTile + (double)kTileHalf - cxo) * d->dx;
-                const double Y = (ty * kTile + (double)kTileHalf - cyo) * d->dy;
+        for (int ty = 0; ty < F.nay; ty++)
+            for (int tx = 0; tx < F.nax; tx++) {
+                const double X = (tx * kAnchor + (double)kAnchorHalf - cxo) * d->dx;
+                const double Y = (ty * kAnchor + (double)kAnchorHalf - cyo) * d->dy;
                 const double tpar = d->dso + X * cb + Y * sb;
                 const double tperp = -X * sb + Y * cb;
                 const double u = std::atan2(tperp, tpar) / dg + c0;
                 const float uhi = (float)u;
-                anc[(size_t)v * ntiles + ty * F.ntx + tx] =
+                anc[(size_t)v * ntiles + ty * F.nax + tx] =
                     make_float4((float)tpar, (float)tperp, uhi, (float)(u - (double)uhi));
             }
     }
@@ -267,15 +269,15 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
             const double zbi = std::nearbyint(zb);
             zbv[v] = make_float2((float)zbi, (float)(zb - zbi));
             const double cb = std::cos(b), sb = std::sin(b);
-            for (int ty = 0; ty < F.nty; ty++)
-                for (int tx = 0; tx < F.ntx; tx++) {
-                    const double X = (tx * kTile + (double)kTileHalf - cxo) * d->dx;
-                    const double Y = (ty * kTile + (double)kTileHalf - cyo) * d->dy;
+            for (int ty = 0; ty < F.nay; ty++)
+                for (int tx = 0; tx < F.nax; tx++) {
+                    const double X = (tx * kAnchor + (double)kAnchorHalf - cxo) * d->dx;
+                    const double Y = (ty * kAnchor + (double)kAnchorHalf - cyo) * d->dy;
                     const double tpar = d->dso + X * cb + Y * sb, tperp = -X * sb + Y * cb;
                     const double L = std::sqrt(tpar * tpar + tperp * tperp);
                     const double ia = L / kA, a = kA / L;
                     const float iah = (float)ia, ah = (float)a;
-                    tax[(size_t)v * ntiles + ty * F.ntx + tx] =
+                    tax[(size_t)v * ntiles + ty * F.nax + tx] =
                         make_float4(iah, (float)(ia - (double)iah), ah, (float)(a - (double)ah));
                 }
         }

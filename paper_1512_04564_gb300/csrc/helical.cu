@@ -299,10 +299,9 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
         if (lane < n) {  // column role: footprint weights and axial parameters of one column
             const int bc = s_lo[c] + (t - s_pre[c]);
             const int ix = M.col ? c : bc, iy = M.col ? bc : c;
-            const int tx = ix / kTile, ty = iy / kTile;
-            const float4 A = __ldg(&G.anchor[(size_t)v * (G.ntx * G.nty) + ty * G.ntx + tx]);
-            const float ox = ((float)(ix - tx * kTile) - kTileHalf) * G.dx;
-            const float oy = ((float)(iy - ty * kTile) - kTileHalf) * G.dy;
+            float ox, oy;
+            const float4 A = pixel_anchor(G, v, ix, iy, ox, oy);
+            const size_t ai = (size_t)v * (G.nax * G.nay) + (iy / kAnchor) * G.nax + ix / kAnchor;
             const Footprint F = sf_footprint(G, cs.x, cs.y, A, ox, oy);
             const int j0 = (int)floorf(F.t0 - 0.5f) + 1;
             cnt = max(min((int)ceilf(F.t3 + 0.5f) - j0, kHxMaxSpan), 0);
@@ -314,7 +313,7 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
             }
             cf = F.n + j0 - s0;
             // axial parameters; the lowest and highest row boundaries give the voxel range
-            const float4 X = __ldg(&H.tile_ax[(size_t)v * (G.ntx * G.nty) + ty * G.ntx + tx]);
+            const float4 X = __ldg(&H.tile_ax[ai]);
             float eps;
             const ColumnAxial C = column_axial<TT>(H, A, X, cs.x, cs.y, ox, oy, G.dx, G.dy, eps);
             if (TT) s_eps[warp][lane] = eps;
@@ -570,11 +569,11 @@ __global__ void __launch_bounds__(kHxBpCols) bp_helix_kernel(FanDev G, HelixDev 
     if (tid < kHxMaxRows) s_rc[tid] = tid < H.nt ? __ldg(&H.row_c[tid]) : 0.0f;
     __syncthreads();
     const bool inside = ix < G.nx && iy < G.ny;
-    const int tx = min(ix, G.nx - 1) / kTile, ty = min(iy, G.ny - 1) / kTile;
-    const int tile = ty * G.ntx + tx;
-    const int ntiles = G.ntx * G.nty;
-    const float ox = ((float)(ix - tx * kTile) - kTileHalf) * G.dx;
-    const float oy = ((float)(iy - ty * kTile) - kTileHalf) * G.dy;
+    const int ixc = min(ix, G.nx - 1), iyc = min(iy, G.ny - 1);
+    const int atile = (iyc / kAnchor) * G.nax + ixc / kAnchor;
+    const int ntiles = G.nax * G.nay;
+    const float ox = ((float)(ixc - (ixc / kAnchor) * kAnchor) - kAnchorHalf) * G.dx;
+    const float oy = ((float)(iyc - (iyc / kAnchor) * kAnchor) - kAnchorHalf) * G.dy;
     float *qb = s_qb + tid;
     float *wq = s_w + tid;
     float rho = 1.0f;
@@ -587,10 +586,10 @@ __global__ void __launch_bounds__(kHxBpCols) bp_helix_kernel(FanDev G, HelixDev 
         for (int k = 0; k < nviews; k++) {
             const int v = __ldg(&views[k]);
             const float2 cs = __ldg(&G.view_cs[v]);
-            const float4 A = __ldg(&G.anchor[(size_t)v * ntiles + tile]);
+            const float4 A = __ldg(&G.anchor[(size_t)v * ntiles + atile]);
             const float2 zb = __ldg(&H.view_zb[v]);
             float eps;
-            const ColumnAxial Cx = column_axial<TT>(H, A, __ldg(&H.tile_ax[(size_t)v * ntiles + tile]), cs.x, cs.y,
+            const ColumnAxial Cx = column_axial<TT>(H, A, __ldg(&H.tile_ax[(size_t)v * ntiles + atile]), cs.x, cs.y,
                                                     ox, oy, G.dx, G.dy, eps);
             const float a = Cx.a_hi + Cx.a_lo;
             const float zbf = zb.x + zb.y;

@@ -55,9 +55,11 @@ __global__ void __launch_bounds__(256) matrix_foot_kernel(FanDev G, float4 *__re
     const int ntiles = G.ntx * G.nty;
     const int v = blockIdx.x / ntiles, tile = blockIdx.x - v * ntiles;
     const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    const int ty = tile / G.ntx, tx = tile - ty * G.ntx;
+    // pixels of a partial tile beyond the image get the edge pixel's (unused) record
+    const int ix = min(tx * kTile + lx, G.nx - 1), iy = min(ty * kTile + ly, G.ny - 1);
     const float2 cs = __ldg(&G.view_cs[v]);
-    const float4 A = __ldg(&G.anchor[(size_t)v * (G.ntx * G.nty) + tile]);
-    const Footprint F = sf_footprint(G, cs.x, cs.y, A, ((float)lx - kTileHalf) * G.dx, ((float)ly - kTileHalf) * G.dy);
+    const Footprint F = pixel_footprint(G, v, cs.x, cs.y, ix, iy);
     const size_t i = ((size_t)v * (G.ntx * G.nty) + tile) * (kTile * kTile) + threadIdx.x;
     // the footprint's cells, as cell_weight evaluates them (the same a_ij as the ray-major rows)
     const int j0 = (int)floorf(F.t0 - 0.5f) + 1, jl = (int)ceilf(F.t3 + 0.5f) - 1;

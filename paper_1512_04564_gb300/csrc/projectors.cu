@@ -22,10 +22,15 @@
 // the subset gradient (Eq. (ct_substitution)), and w (A 1) for the SQS
 // diagonal.
 //
-// Back-projector: one CTA per 16x16 pixel tile (one anchor per view), one
-// pixel per thread, gathering from the cells its footprint covers.  Fused
-// epilogues: plain x = scale A'r (+x), and the relaxed OS-LALM g/h updates of
-// Algorithm 1/2 (Sec. III-A).
+// * resident-matrix kernel (after ct_geom_precompute): one warp per ray
+//   streams the ray's stored (pixel, a_ij) entries and gathers x.
+//
+// Back-projector: one CTA per 16x16 pixel tile, two pixels per thread,
+// gathering from the cells its footprint covers: footprints evaluated on the
+// fly (each pixel relative to its 8x8 anchor tile), or the resident matrix's
+// per-(view, pixel) records of cell weights.  Fused epilogues: plain
+// x = scale A'r (+x), and the relaxed OS-LALM g/h updates of Algorithm 1/2
+// (Sec. III-A).
 #include <cstdio>
 
 #include "ct_internal.cuh"
@@ -365,6 +370,9 @@ __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const
     const int ix = blockIdx.x * kTile + lx, iy0 = blockIdx.y * kTile + ly, iy1 = iy0 + kTile / 2;
     const int tile = blockIdx.y * G.ntx + blockIdx.x;
     const int ntiles = G.ntx * G.nty;
+    // footprints are evaluated for in-image pixels only (a partial tile's outside pixels take the
+    // edge pixel's, and their results are not stored); rows ly and ly + 8 lie in two anchor tiles
+    const int ixc = min(ix, G.nx - 1), iy0c = min(iy0, G.ny - 1), iy1c = min(iy1, G.ny - 1);
     float rho = 1.0f;
     if (MODE == BP_SOLVE_UPDATE) rho = __ldcg(&S.rho_tab[__ldcg(&S.counter[0])]);
     float acc0 = 0.0f, acc1 = 0.0f;
@@ -391,25 +399,18 @@ __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const
             if (wide0 || wide1) {  // rare: a footprint wider than a record, evaluated on the fly
                 const int v = __ldg(&views[k]);
                 const float2 cs = __ldg(&G.view_cs[v]);
-                const float4 A = __ldg(&G.anchor[(size_t)v * ntiles + tile]);
-                const float ox = ((float)lx - kTileHalf) * G.dx;
-                if (wide0) acc0 += footprint_dot(sf_footprint(G, cs.x, cs.y, A, ox, ((float)ly - kTileHalf) * G.dy), row, G.ns);
-                if (wide1)
-                    acc1 += footprint_dot(sf_footprint(G, cs.x, cs.y, A, ox, ((float)(ly + kTile / 2) - kTileHalf) * G.dy),
-                                          row, G.ns);
+                if (wide0) acc0 += footprint_dot(pixel_footprint(G, v, cs.x, cs.y, ixc, iy0c), row, G.ns);
+                if (wide1) acc1 += footprint_dot(pixel_footprint(G, v, cs.x, cs.y, ixc, iy1c), row, G.ns);
             }
             if (!wide0) acc0 += record_dot(w0, b0, row, G.ns);
             if (!wide1) acc1 += record_dot(w1, b1, row, G.ns);
         }
     } else {
-        const float ox = ((float)lx - kTileHalf) * G.dx;
-        const float oy0 = ((float)ly - kTileHalf) * G.dy, oy1 = ((float)(ly + kTile / 2) - kTileHalf) * G.dy;
         for (int k = 0; k < nviews; k++) {
             const int v = __ldg(&views[k]);
             const float2 cs = __ldg(&G.view_cs[v]);
-            const float4 A = __ldg(&G.anchor[(size_t)v * ntiles + tile]);
-            const Footprint F0 = sf_footprint(G, cs.x, cs.y, A, ox, oy0);
-            const Footprint F1 = sf_footprint(G, cs.x, cs.y, A, ox, oy1);
+            const Footprint F0 = pixel_footprint(G, v, cs.x, cs.y, ixc, iy0c);
+            const Footprint F1 = pixel_footprint(G, v, cs.x, cs.y, ixc, iy1c);
             const float *row = sino + (size_t)k * G.ns;
             acc0 += footprint_dot(F0, row, G.ns);
             acc1 += footprint_dot(F1, row, G.ns);
