@@ -30,10 +30,11 @@ struct FanDev {
     float x_edge0, y_edge0;   // x of the left edge of column 0, y of the lower edge of row 0 (mm)
     float cxo, cyo;           // (nx-1)/2 - offset_x, (ny-1)/2 - offset_y (pixel index of the origin)
     int max_span;             // upper bound on the detector cells one pixel footprint overlaps
-    const float4 *anchor;     // [na][nay*nax]: view-frame (t_par, t_perp) of the anchor tile's centre
-                              // relative to the source, and its detector coordinate
-                              // u = gamma/dgamma + (ns-1)/2 - offset_s split into hi + lo floats
-                              // (FP64-derived)
+    const float4 *anchor;     // [na][nay*nax]: view-frame position of the anchor tile's centre relative
+                              // to the source, (t_par - dso, t_perp) (t_par kept as dso + a small
+                              // float, so the kernels see it with the small float's rounding), and
+                              // its detector coordinate u = gamma/dgamma + (ns-1)/2 - offset_s split
+                              // into hi + lo floats (FP64-derived)
     const float2 *view_cs;    // [na]: (cos beta, sin beta)
     const float *view_beta;   // [na]: beta in [0, 2 pi)
     // resident system matrix (ct_geom_precompute); null when footprints are computed on the fly
@@ -76,6 +77,7 @@ struct HelixDev {
     const float4 *tile_ax;   // [na][nay*nax]: at each anchor tile's centre, voxels per row 1/a = L/kA and
                              // rows per voxel a = kA/L, each as hi + lo floats (FP64-derived)
     int trap;                // axial footprint: 0 rectangle (SF-TR), 1 trapezoid (SF-TT)
+    float dso;               // source-to-isocentre distance (the FanDev's)
 };
 
 }  // namespace ct
@@ -161,11 +163,12 @@ __device__ __forceinline__ Footprint sf_footprint(const FanDev &G, float cb, flo
     // pixel centre relative to the anchor, in the view frame (small vector: accurate in FP32)
     const float dpar = fmaf(ox, cb, oy * sb);
     const float dperp = fmaf(oy, cb, -ox * sb);
-    const float cpar = A.x + dpar;
+    const float cpar = G.dso + (A.x + dpar);
     const float cperp = A.y + dperp;
     // fan angle of the centre relative to the anchor's: atan(cross(A, c) / dot(A, c))
-    const float crs = fmaf(A.x, dperp, -A.y * dpar);
-    const float dt = fmaf(A.x, cpar, A.y * cperp);
+    // (the anchor's t_par = dso + A.x stays an unevaluated sum: its rounding would dominate the error)
+    const float crs = fmaf(G.dso, dperp, fmaf(A.x, dperp, -A.y * dpar));
+    const float dt = fmaf(G.dso, G.dso + fmaf(2.0f, A.x, dpar), fmaf(A.x, A.x + dpar, A.y * cperp));
     const float du = atan_series(crs / dt) * G.inv_dg;
     const float nf = floorf(A.z + du);
     const float f = (A.z - nf) + (A.w + du);  // centre's detector coordinate relative to cell nf

@@ -228,8 +228,9 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
                 const double tperp = -X * sb + Y * cb;
                 const double u = std::atan2(tperp, tpar) / dg + c0;
                 const float uhi = (float)u;
+                // t_par as dso (the kernels' float) + a small float
                 anc[(size_t)v * ntiles + ty * F.nax + tx] =
-                    make_float4((float)tpar, (float)tperp, uhi, (float)(u - (double)uhi));
+                    make_float4((float)(tpar - (double)F.dso), (float)tperp, uhi, (float)(u - (double)uhi));
             }
     }
     std::vector<int> ident(na);
@@ -310,6 +311,7 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         g->hx.row_c = g->d_row_c;
         g->hx.tile_ax = g->d_tile_ax;
         g->hx.trap = d->axial == CT_AXIAL_TRAP ? 1 : 0;
+        g->hx.dso = F.dso;
     }
     F.anchor = g->d_anchor;
     F.view_cs = g->d_view_cs;

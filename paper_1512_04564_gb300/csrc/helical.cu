@@ -121,10 +121,10 @@ __device__ __forceinline__ ColumnAxial column_axial(const HelixDev &H, float4 A,
                                                     float ox, float oy, float pdx, float pdy, float &eps)
 {
     const float dpar = fmaf(ox, cb, oy * sb), dperp = fmaf(oy, cb, -ox * sb);
-    const float cpar = A.x + dpar, cperp = A.y + dperp;
+    const float cpar = H.dso + (A.x + dpar), cperp = A.y + dperp;  // A.x: the anchor's t_par - dso
     const float L = sqrtf(fmaf(cpar, cpar, cperp * cperp));
     const float LA = X.x * H.kA;
-    const float num = fmaf(2.0f, fmaf(A.x, dpar, A.y * dperp), fmaf(dpar, dpar, dperp * dperp));
+    const float num = fmaf(2.0f, fmaf(H.dso, dpar, fmaf(A.x, dpar, A.y * dperp)), fmaf(dpar, dpar, dperp * dperp));
     float dL = __fdividef(num, L + LA);
     float Lc = L;
     eps = 0.0f;
