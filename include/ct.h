@@ -253,9 +253,7 @@ typedef struct {
  * which needs a 360-degree scan) and the result on return.  The solve
  * runs on `stream` as CUDA-graph replays of one outer iteration and
  * synchronises the stream before returning.  Errors: CT_EINVAL, CT_ENOMEM,
- * CT_ECUDA, CT_ETIMEOUT (a bounded device-side wait of the resident-matrix
- * forward projector gave up, in this solve or an earlier asynchronous call
- * on the same geometry; the results are then undefined). */
+ * CT_ECUDA. */
 ct_status ct_relaxed_oslalm_solve(const ct_geom *g, const float *y, const float *w, const ct_solve_params *p,
                                   float *x_inout, ct_solve_report *report, void *stream);
 

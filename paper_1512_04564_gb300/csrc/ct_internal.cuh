@@ -42,12 +42,7 @@ struct FanDev {
     const float2 *foot_an;    // [na][ntiles][256]: a_ij of cell n0+4, and n0 as int bits (kWideRecord:
                               // the footprint covers more than kRecordCells cells; evaluate it on the fly)
     const long long *row_ptr; // [na*ns + 1]: start of each ray's entries
-    const int2 *row_ent;      // (pixel index, a_ij bits), ray-major, march order within a ray (padded
-                              // by 16 bytes, so that copies rounded out to 16 bytes stay inside)
-    int csr_stage;            // entries per shared-memory stage of the bulk-copy forward projector
-                              // (the widest 4-ray unit, rounded out to 16 bytes); 0: not set up
-    int csr_grid;             // its persistent grid (SMs x resident CTAs)
-    int *csr_err;             // its error flag (a bounded wait gave up)
+    const int2 *row_ent;      // (pixel index, a_ij bits), ray-major, march order within a ray
     int fp_variant;           // forward projector chosen by ct_geom_autotune (FP_AUTO: default order)
     int bp_variant;           // back-projector chosen by ct_geom_autotune (BP_AUTO)
 };
@@ -113,7 +108,6 @@ struct ct_geom {
     int2 *d_row_ent = nullptr;
     float4 *d_foot_t = nullptr;
     float2 *d_foot_an = nullptr;
-    int *d_csr_err = nullptr;
     unsigned long long matrix_bytes = 0;
     int device = 0;
 };
@@ -357,9 +351,6 @@ cudaError_t launch_fp(const FanDev &G, int mode, const float *x, const int *view
                       const float *y, const float *w, cudaStream_t st);
 cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *views, int nviews, float *x,
                       float scale, int accumulate, const SolveDev *S, cudaStream_t st);
-// Prepare the bulk-copy resident-matrix forward projector for stages of `stage` entries:
-// sets G.csr_stage and G.csr_grid (left 0 when the stage does not fit in shared memory).
-cudaError_t setup_fp_csr_bulk(FanDev &G, int stage);
 cudaError_t launch_reg_gradient(const FanDev &G, const float *x, const float *kappa, float beta, float delta,
                                 int potential, float *grad, float *curv, cudaStream_t st);
 cudaError_t launch_reg_update(const FanDev &G, const SolveDev &S, float beta, float delta, int potential,

@@ -82,7 +82,6 @@ static void free_geom(ct_geom *g)
     cudaFree(g->d_row_ent);
     cudaFree(g->d_foot_t);
     cudaFree(g->d_foot_an);
-    cudaFree(g->d_csr_err);
     cudaFree(g->d_view_zb);
     cudaFree(g->d_row_c);
     cudaFree(g->d_tile_ax);

@@ -13,7 +13,6 @@
 //     marked and evaluated on the fly).
 // Building it: count each ray's nonzero weights, exclusive-scan the counts
 // into row pointers, fill the rows, store the footprints.
-#include <algorithm>
 #include <vector>
 
 #include "ct_internal.cuh"
@@ -168,9 +167,7 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
         g->matrix_bytes = bytes;
         return fail(cudaSuccess);
     }
-    // two entries of padding: bulk copies are rounded out to 16-byte boundaries
-    if ((e = cudaMalloc(&ent, sizeof(int2) * (size_t)(nnz + 2))) != cudaSuccess) return fail(e);
-    if ((e = cudaMemsetAsync(ent + nnz, 0, 2 * sizeof(int2), st)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&ent, sizeof(int2) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&ft, sizeof(float4) * G.na * ntile_px)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&fan, sizeof(float2) * G.na * ntile_px)) != cudaSuccess) return fail(e);
     matrix_fill_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(G, rp, ent);
@@ -178,20 +175,6 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     matrix_foot_kernel<<<(unsigned)((size_t)G.ntx * G.nty * G.na), 256, 0, st>>>(G, ft, fan);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
-    // widest 4-ray unit of the bulk-copy forward projector, rounded out to 16 bytes
-    std::vector<long long> hp((size_t)R + 1);
-    if ((e = cudaMemcpy(hp.data(), rp, sizeof(long long) * (R + 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
-        return fail(e);
-    long long widest = 0;
-    for (int v = 0; v < G.na; v++)
-        for (int s0 = 0; s0 < G.ns; s0 += 4) {
-            const long long r0 = (long long)v * G.ns + s0, r1 = std::min(r0 + 4, (long long)(v + 1) * G.ns);
-            widest = std::max(widest, ((hp[r1] + 1) & ~1LL) - (hp[r0] & ~1LL));
-        }
-    if (!g->d_csr_err) {
-        if ((e = cudaMalloc(&g->d_csr_err, sizeof(int))) != cudaSuccess) return fail(e);
-        if ((e = cudaMemset(g->d_csr_err, 0, sizeof(int))) != cudaSuccess) return fail(e);
-    }
     g->d_row_ptr = rp;
     g->d_row_ent = ent;
     g->d_foot_t = ft;
@@ -201,8 +184,7 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     g->fan.row_ent = ent;
     g->fan.foot_t = ft;
     g->fan.foot_an = fan;
-    g->fan.csr_err = g->d_csr_err;
-    return setup_fp_csr_bulk(g->fan, widest > (1LL << 24) ? 0 : (int)widest);
+    return cudaSuccess;
 }
 
 }  // namespace ct

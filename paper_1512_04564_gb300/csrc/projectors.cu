@@ -22,13 +22,8 @@
 // the subset gradient (Eq. (ct_substitution)), and w (A 1) for the SQS
 // diagonal.
 //
-// * resident-matrix kernels (after ct_geom_precompute): one warp per ray
-//   walks the ray's stored (pixel, a_ij) entries and gathers x.  The
-//   persistent bulk-copy kernel streams each unit of 4 consecutive rays'
-//   entries (one contiguous run) into shared memory with the TMA engine,
-//   two units in flight per CTA and two CTAs per SM, so the HBM stream does
-//   not wait on the gathers (eight per lane in flight); the plain kernel loads
-//   the entries directly.
+// * resident-matrix kernel (after ct_geom_precompute): one warp per ray
+//   streams the ray's stored (pixel, a_ij) entries and gathers x.
 //
 // Back-projector: one CTA per 16x16 pixel tile, two pixels per thread,
 // gathering from the cells its footprint covers: footprints evaluated on the
@@ -39,7 +34,6 @@
 #include <cstdio>
 
 #include "ct_internal.cuh"
-#include "tc.cuh"
 
 namespace ct {
 
@@ -333,130 +327,6 @@ __global__ void __launch_bounds__(256) fp_csr_kernel(FanDev G, const float *__re
     else out[r] = __ldg(&w[r]) * acc;
 }
 
-constexpr int kCsrRays = 4;                   // rays per unit of the bulk-copy kernel (one warp each)
-constexpr int kCsrStages = 2;                 // units in flight per CTA (two CTAs per SM)
-constexpr int kCsrThreads = kCsrRays * 32;
-constexpr int kCsrHeader = 128;               // mbarriers and flags ahead of the stage buffers
-
-__host__ __device__ constexpr size_t csr_smem_bytes(int stage) { return kCsrHeader + (size_t)kCsrStages * stage * 8; }
-
-// Persistent: CTA b takes units b, b + grid, ...; unit u = (view k, 4-ray block) covers rays r0 .. r1-1 of
-// view views[k], whose entries [row_ptr[r0], row_ptr[r1]) are contiguous; the copy is rounded out to
-// 16-byte boundaries (row_ent is padded).  Thread 0 arms stage s's mbarrier with the byte count and
-// issues the copy; all threads wait on it (bounded: on a timeout the CTA sets G.csr_err, waits, again
-// bounded, for its copies in flight and returns), warp w reduces ray r0 + w from shared memory, and
-// after a CTA barrier the stage is refilled with the unit kCsrStages ahead.
-template <int MODE>
-__global__ void __launch_bounds__(kCsrThreads) fp_csr_bulk_kernel(FanDev G, const float *__restrict__ x,
-                                                                 const int *__restrict__ views, int nviews,
-                                                                 float *__restrict__ out, const float *__restrict__ y,
-                                                                 const float *__restrict__ w)
-{
-    extern __shared__ __align__(128) unsigned char csr_smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(csr_smem);
-    int *s_abort = reinterpret_cast<int *>(csr_smem + 64);
-    int2 *buf = reinterpret_cast<int2 *>(csr_smem + kCsrHeader);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int S = G.csr_stage;
-    const int nb = (G.ns + kCsrRays - 1) / kCsrRays;
-    const long units = (long)nviews * nb;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kCsrStages; s++) tc::mbar_init(&bar[s], 1);
-        *s_abort = 0;
-        tc::fence_mbar_init();
-    }
-    __syncthreads();
-    auto rows = [&](long u, int &k, long &r0, long &r1) {
-        k = (int)(u / nb);
-        const int v = __ldg(&views[k]);
-        r0 = (long)v * G.ns + (long)(u - (long)k * nb) * kCsrRays;
-        r1 = min(r0 + kCsrRays, (long)(v + 1) * G.ns);
-    };
-    auto issue = [&](long u, int s) {
-        int k;
-        long r0, r1;
-        rows(u, k, r0, r1);
-        const long long a0 = __ldg(&G.row_ptr[r0]) & ~1LL, a1 = (__ldg(&G.row_ptr[r1]) + 1) & ~1LL;
-        const uint32_t bytes = (uint32_t)(a1 - a0) * 8u;
-        tc::mbar_arrive_expect_tx(&bar[s], bytes);
-        if (bytes) tc::bulk_copy_g2s(buf + (size_t)s * S, G.row_ent + a0, bytes, &bar[s]);
-    };
-    if (threadIdx.x == 0)
-        for (int s = 0; s < kCsrStages; s++) {
-            const long u = blockIdx.x + (long)s * gridDim.x;
-            if (u < units) issue(u, s);
-        }
-    long it = 0, u = blockIdx.x;
-    for (; u < units; u += gridDim.x, it++) {
-        const int s = (int)(it % kCsrStages);
-        if (!tc::mbar_wait(&bar[s], (uint32_t)((it / kCsrStages) & 1), G.csr_err)) *s_abort = 1;
-        __syncthreads();
-        if (*s_abort) break;
-        int k;
-        long r0, r1;
-        rows(u, k, r0, r1);
-        const long r = r0 + warp;
-        if (r < r1) {
-            const long long a0 = __ldg(&G.row_ptr[r0]) & ~1LL;
-            const long long b = __ldg(&G.row_ptr[r]), e = __ldg(&G.row_ptr[r + 1]);
-            const int2 *ent = buf + (size_t)s * S;
-            float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, c3 = 0.0f;
-            int i = (int)(b - a0) + lane;
-            const int ie = (int)(e - a0);
-            for (; i + 224 < ie; i += 256) {
-                int2 q[8];
-#pragma unroll
-                for (int j = 0; j < 8; j++) q[j] = ent[i + 32 * j];
-                if (MODE == FP_ONES_W) {
-                    c0 += __int_as_float(q[0].y) + __int_as_float(q[4].y);
-                    c1 += __int_as_float(q[1].y) + __int_as_float(q[5].y);
-                    c2 += __int_as_float(q[2].y) + __int_as_float(q[6].y);
-                    c3 += __int_as_float(q[3].y) + __int_as_float(q[7].y);
-                } else {
-                    float xv[8];
-#pragma unroll
-                    for (int j = 0; j < 8; j++) xv[j] = __ldg(&x[q[j].x]);
-                    c0 = fmaf(__int_as_float(q[0].y), xv[0], c0);
-                    c1 = fmaf(__int_as_float(q[1].y), xv[1], c1);
-                    c2 = fmaf(__int_as_float(q[2].y), xv[2], c2);
-                    c3 = fmaf(__int_as_float(q[3].y), xv[3], c3);
-                    c0 = fmaf(__int_as_float(q[4].y), xv[4], c0);
-                    c1 = fmaf(__int_as_float(q[5].y), xv[5], c1);
-                    c2 = fmaf(__int_as_float(q[6].y), xv[6], c2);
-                    c3 = fmaf(__int_as_float(q[7].y), xv[7], c3);
-                }
-            }
-            for (; i < ie; i += 32) {
-                const int2 q = ent[i];
-                c0 = (MODE == FP_ONES_W) ? c0 + __int_as_float(q.y) : fmaf(__int_as_float(q.y), __ldg(&x[q.x]), c0);
-            }
-            float acc = (c0 + c1) + (c2 + c3);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) {
-                const int v = __ldg(&views[k]);
-                const long sc = r - (long)v * G.ns;
-                if (MODE == FP_PLAIN) out[(size_t)k * G.ns + sc] = acc;
-                else if (MODE == FP_RESID) out[(size_t)k * G.ns + sc] = __ldg(&w[r]) * (acc - __ldg(&y[r]));
-                else out[r] = __ldg(&w[r]) * acc;
-            }
-        }
-        __syncthreads();  // stage s is free again
-        if (threadIdx.x == 0) {
-            const long un = u + (long)kCsrStages * gridDim.x;
-            if (un < units) issue(un, s);
-        }
-    }
-    if (*s_abort && threadIdx.x == 0) {
-        // the copies of this and the next units may still be in flight: wait for them (bounded)
-        for (int q = 0; q < kCsrStages; q++) {
-            const long uq = u + (long)q * gridDim.x;
-            const long itq = it + q;
-            if (uq < units) tc::mbar_wait(&bar[itq % kCsrStages], (uint32_t)((itq / kCsrStages) & 1), nullptr);
-        }
-    }
-}
-
 template <int MODE>
 __device__ __forceinline__ void bp_epilogue(const FanDev &G, const SolveDev &S, float *__restrict__ xo, int ix,
                                             int iy, float acc, float rho, float scale, int accumulate)
@@ -574,17 +444,6 @@ cudaError_t launch_fp(const FanDev &G, int mode, const float *x, const int *view
     if (var == FP_VAR_CSR && !G.row_ptr) var = FP_AUTO;
     if (var == FP_VAR_BUNDLE && !bundle_ok) var = FP_AUTO;
     if (var == FP_AUTO) var = G.row_ptr ? FP_VAR_CSR : (bundle_ok ? FP_VAR_BUNDLE : FP_VAR_RAY);
-    if (var == FP_VAR_CSR && G.csr_stage > 0 && G.csr_grid > 0) {
-        const long units = (long)nviews * ((G.ns + kCsrRays - 1) / kCsrRays);
-        const unsigned blocks = (unsigned)min((long)G.csr_grid, units);
-        const size_t smem = csr_smem_bytes(G.csr_stage);
-        switch (mode) {
-        case FP_PLAIN: fp_csr_bulk_kernel<FP_PLAIN><<<blocks, kCsrThreads, smem, st>>>(G, x, views, nviews, out, y, w); break;
-        case FP_RESID: fp_csr_bulk_kernel<FP_RESID><<<blocks, kCsrThreads, smem, st>>>(G, x, views, nviews, out, y, w); break;
-        default: fp_csr_bulk_kernel<FP_ONES_W><<<blocks, kCsrThreads, smem, st>>>(G, x, views, nviews, out, y, w); break;
-        }
-        return cudaGetLastError();
-    }
     if (var == FP_VAR_CSR) {
         const unsigned blocks = (unsigned)(((long)nviews * G.ns + 7) / 8);
         switch (mode) {
@@ -612,28 +471,6 @@ cudaError_t launch_fp(const FanDev &G, int mode, const float *x, const int *view
     default: fp_ray_kernel<FP_ONES_W><<<blocks, kFpThreads, 0, st>>>(G, x, views, nviews, out, y, w); break;
     }
     return cudaGetLastError();
-}
-
-cudaError_t setup_fp_csr_bulk(FanDev &G, int stage)
-{
-    G.csr_stage = 0;
-    G.csr_grid = 0;
-    const size_t smem = csr_smem_bytes(stage);
-    if (stage <= 0 || smem > 200 * 1024) return cudaSuccess;  // the plain kernel serves such matrices
-    cudaError_t e = cudaFuncSetAttribute(fp_csr_bulk_kernel<FP_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fp_csr_bulk_kernel<FP_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fp_csr_bulk_kernel<FP_ONES_W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0, dev = 0, sms = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fp_csr_bulk_kernel<FP_RESID>, kCsrThreads, smem);
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess || per_sm < 1) return e;
-    G.csr_stage = stage;
-    G.csr_grid = per_sm * sms;
-    return cudaSuccess;
 }
 
 cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *views, int nviews, float *x,

@@ -315,15 +315,6 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
     CT_CUDA_TRY(cudaEventRecord(ev_in, ws), "event");
     CT_CUDA_TRY(cudaStreamWaitEvent(user, ev_in, 0), "ordering caller's stream");
     CT_CUDA_TRY(cudaStreamSynchronize(ws), "solve");
-    if (g->d_csr_err) {  // a bounded wait of the bulk-copy forward projector gave up
-        int flag = 0;
-        CT_CUDA_TRY(cudaMemcpy(&flag, g->d_csr_err, sizeof(int), cudaMemcpyDeviceToHost), "read projector status");
-        if (flag) {
-            cudaMemset(g->d_csr_err, 0, sizeof(int));
-            set_error("forward projector: an asynchronous copy did not complete in time; results are undefined");
-            return CT_ETIMEOUT;
-        }
-    }
 
     std::vector<float> trace(done > 0 ? done : 1, -1.0f);
     if (p->x_ref && done > 0)

@@ -1,8 +1,7 @@
 // Blackwell (sm_103a) tensor-core building blocks in inline PTX: tensor-memory
 // allocation, shared-memory matrix descriptors, the BF16 x BF16 -> FP32
 // tcgen05.mma, its completion via an mbarrier, tensor-memory loads, and the
-// fences that order them; mbarrier-tracked bulk asynchronous copies.  Used by
-// the U-Net convolution kernels and the resident-matrix forward projector.
+// fences that order them.  Used by the U-Net convolution kernels.
 //
 // Operand tiles live in shared memory in the canonical K-major layout without
 // swizzle: the tile is cut into "core matrices" of 8 rows x 16 bytes (8 BF16
@@ -140,24 +139,6 @@ __device__ __forceinline__ void cp_async16(uint32_t sdst, const void *gsrc, bool
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// Arm an mbarrier for one arrival plus `bytes` of asynchronous-copy traffic.
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// Bulk asynchronous copy (TMA engine, no tensor map) of `bytes` from global to
-// this CTA's shared memory, completing on the mbarrier's transaction count.
-// Both addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_copy_g2s(void *sdst, const void *gsrc, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(sdst)),
-                 "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
 
 }  // namespace tc
 }  // namespace ct
