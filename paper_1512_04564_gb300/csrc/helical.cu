@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
     __shared__ int2 s_kr[kHxWarps][32];     // voxel range [kmin, kmax] its rows reach
     __shared__ int s_k0[kHxWarps][32];      // lowest row boundary K + f
     __shared__ float s_f0[kHxWarps][32];
-    __shared__ float s_eps[kHxWarps][TT ? 32 : 1];  // TT: the column's ramp-width factor eps
+    __shared__ float2 s_eps[kHxWarps][TT ? 32 : 1];  // TT: the column's eps and its widest ramp (voxels)
     __shared__ float s_xw[kHxWarps][64];    // z-window of the column being profiled
     extern __shared__ float4 s_dyn4[];
     float *s_p = reinterpret_cast<float *>(s_dyn4);  // [warp][32][PS] profiles; later [warp][NT][32] partial sums
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
             const float4 X = __ldg(&H.tile_ax[ai]);
             float eps;
             const ColumnAxial C = column_axial<TT>(H, A, X, cs.x, cs.y, ox, oy, G.dx, G.dy, eps);
-            if (TT) s_eps[warp][lane] = eps;
+            if (TT) s_eps[warp][lane] = make_float2(eps, 0.0f);
             const float cz = fmaf(H.ofr, C.ia_hi + C.ia_lo, -zb.y);
             int K0, K1;
             float f0, f1;
@@ -324,9 +324,14 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
             row_boundary((float)nt - 0.5f - H.ct0i, C.ia_hi, C.ia_lo, zb.x, cz, nz, K1, f1);
             s_ax[warp][lane] = make_float4(C.ia_hi, C.ia_lo, C.a_hi + C.a_lo, cz);
             s_col[warp][lane] = iy * G.nx + ix;
-            s_kr[warp][lane] = make_int2(max(K0, 0), min(K1, nz - 1));
+            // (TT: one voxel more on each side, for the ramps at the outermost row boundaries)
+            s_kr[warp][lane] = TT ? make_int2(max(K0 - 1, 0), min(K1 + 1, nz - 1)) : make_int2(max(K0, 0), min(K1, nz - 1));
             s_k0[warp][lane] = K0;
             s_f0[warp][lane] = f0;
+            if (TT) {  // the widest ramp the column's row boundaries can meet (|z - z_src| is convex in K)
+                const float zbt = zb.x + zb.y;
+                s_eps[warp][lane].y = eps * fmaxf(fabsf((float)K0 + zbt), fabsf((float)(K1 + 1) + zbt));
+            }
         }
         scf[lane] = cf;
         sns[lane] = cnt;
@@ -365,7 +370,8 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
                     if (MODE == FP_ONES_W) return 1.0f;
                     return (kk >= kr.x && kk <= kr.y && kk - kr.x < 64) ? xw[kk] : __ldg(&xg_l[kk]);
                 };
-                const float eps_l = TT ? s_eps[warp][TT ? l : 0] : 0.0f;
+                const float eps_l = TT ? s_eps[warp][TT ? l : 0].x : 0.0f;
+                const float hcol = TT ? s_eps[warp][TT ? l : 0].y : 0.0f;
                 const float zbf = zb.x + zb.y;
                 float corr_c = TT ? ramp_correction(Kc, fc, eps_l, zbf, xv) : 0.0f;
 #pragma unroll
@@ -384,11 +390,14 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
                     fc = __shfl_sync(kFull, fh, 31);
                     float sacc = 0.0f;
                     if (TT) {  // + the ramps at the row's upper boundary, - those at its lower one
-                        const float ch = ramp_correction(Kh, fh, eps_l, zbf, xv);
-                        float cl = __shfl_up_sync(kFull, ch, 1);
-                        if (lane == 0) cl = corr_c;
-                        corr_c = __shfl_sync(kFull, ch, 31);
-                        sacc = ch - cl;
+                        const bool near = fminf(fh, 1.0f - fh) < hcol;  // only then can a ramp straddle it
+                        const float ch = near ? ramp_correction(Kh, fh, eps_l, zbf, xv) : 0.0f;
+                        if (__any_sync(kFull, near) || corr_c != 0.0f) {
+                            float cl = __shfl_up_sync(kFull, ch, 1);
+                            if (lane == 0) cl = corr_c;
+                            corr_c = __shfl_sync(kFull, ch, 31);
+                            sacc = ch - cl;
+                        }
                     }
                     if (r < nt && Kh >= 0 && Kl < nz) {
                         const int k0 = max(Kl, 0), k1 = min(Kh, nz - 1);
@@ -631,7 +640,8 @@ __global__ void __launch_bounds__(kHxBpCols) bp_helix_kernel(FanDev G, HelixDev 
             const float c_half = H.ct0i + 0.5f;
             RowPos pp = row_pos(z0, zb.x, Cx.a_hi, Cx.a_lo, cb0, c_half, nt);
             float Cp = row_cdf(qb, pp, t_lo, nr);
-            float Dp = TT ? ramp_adjoint(qb, pp, hwA, t_lo, nr) : 0.0f;
+            const float hw_max = fmaxf(hwA, hwB);  // the widest ramp of the chunk (rows)
+            float Dp = (TT && fminf(pp.fr, 1.0f - pp.fr) < hw_max) ? ramp_adjoint(qb, pp, hwA, t_lo, nr) : 0.0f;
 #pragma unroll
             for (int i = 0; i < ZC; i++) {
                 const RowPos p = row_pos(z0 + i + 1, zb.x, Cx.a_hi, Cx.a_lo, cb0, c_half, nt);
@@ -639,7 +649,9 @@ __global__ void __launch_bounds__(kHxBpCols) bp_helix_kernel(FanDev G, HelixDev 
                 acc[i] += C - Cp;
                 Cp = C;
                 if (TT) {
-                    const float D = ramp_adjoint(qb, p, ea * fabsf((float)(z0 + i + 1) + zbf), t_lo, nr);
+                    const float D = fminf(p.fr, 1.0f - p.fr) < hw_max
+                                        ? ramp_adjoint(qb, p, ea * fabsf((float)(z0 + i + 1) + zbf), t_lo, nr)
+                                        : 0.0f;
                     acc[i] += Dp - D;
                     Dp = D;
                 }
