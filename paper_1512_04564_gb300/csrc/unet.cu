@@ -239,7 +239,7 @@ struct WgradGemm {
 template <int NT, class Ld>
 cudaError_t launch_gemm(const Ld &L, int mtiles, int ntiles, int k_steps, int *err, cudaStream_t st)
 {
-    const int bytes = tc::GemmSmem<NT>::kBytes;
+    const int bytes = tc::GemmSmem<NT, tc::gemm_stages(NT)>::kBytes;
     cudaError_t e = cudaFuncSetAttribute(tc::gemm_kernel<NT, Ld>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     tc::gemm_kernel<NT, Ld><<<dim3(mtiles, ntiles), 128, bytes, st>>>(L, k_steps, err);
@@ -555,7 +555,7 @@ cudaError_t conv3x3_wgrad_tc(const ConvIn &in, const bf16 *gout, float *dw, floa
 #define CT_WG(NTV)                                                                                                     \
     {                                                                                                                  \
         using L = WgradGemm<NTV>;                                                                                      \
-        const int bytes = tc::GemmSmem<NTV>::kBytes;                                                                   \
+        const int bytes = tc::GemmSmem<NTV, tc::gemm_stages(NTV)>::kBytes;                                             \
         e = cudaFuncSetAttribute(tc::gemm_kernel<NTV, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);         \
         if (e != cudaSuccess) return e;                                                                                \
         tc::gemm_kernel<NTV, L><<<grid, 128, bytes, st>>>(                                                             \
