@@ -32,16 +32,19 @@ struct PlainGemm {
     __device__ void load(int s, uint32_t sa, uint32_t sb, const Ctx &x, int tid) const
     {
         const int k0 = s * tc::kStageK, m0 = x.m0, n0 = x.n0;
+        // a warp stages 16 rows x 2 adjacent 16-byte chunks: 32-byte sectors from global memory,
+        // and the 8 row residues mod 8 (the shared-memory bank groups of the core-matrix layout)
+        const int jr = 2 * (tid >> 5) + (tid & 1), rr = (tid >> 1) & 15;
 #pragma unroll
         for (int i = 0; i < 8; i++) {
-            const int c = tid + 128 * i, r = c >> 3, j = c & 7;
+            const int r = rr + 16 * i, j = jr;
             const int m = m0 + r, k = k0 + 8 * j;
             const bool ok = m < M && k < K;
             tc::cp_async16(sa + tc::tile_offset(r, 8 * j), ok ? A + (size_t)m * K + k : A, ok);
         }
 #pragma unroll
         for (int i = 0; i < NT / 16; i++) {
-            const int c = tid + 128 * i, r = c >> 3, j = c & 7;
+            const int r = rr + 16 * i, j = jr;
             const int n = n0 + r, k = k0 + 8 * j;
             const bool ok = n < N && k < K;
             tc::cp_async16(sb + tc::tile_offset(r, 8 * j), ok ? B + (size_t)n * K + k : B, ok);
@@ -105,7 +108,7 @@ struct ConvGemm {
         const int P = B * H * W;
 #pragma unroll
         for (int i = 0; i < 8; i++) {
-            const int p = m0 + (tid >> 3) + 16 * i;
+            const int p = m0 + ((tid >> 1) & 15) + 16 * i;  // the rows load() stages (see there)
             if (p < P) {
                 c.x[i] = p % W;
                 const int q = p / W;
@@ -120,20 +123,22 @@ struct ConvGemm {
     }
     __device__ void load(int s, uint32_t sa, uint32_t sb, const Ctx &c, int tid) const
     {
-        const int j = tid & 7, Kt = 9 * Ci;
+        // a warp stages 16 rows x 2 adjacent 16-byte chunks (32-byte global sectors; the 8 row
+        // residues mod 8 spread the shared-memory stores over all bank groups)
+        const int j = 2 * (tid >> 5) + (tid & 1), rr = (tid >> 1) & 15, Kt = 9 * Ci;
         const int k = s * tc::kStageK + 8 * j;
         const int tap = k / Ci, ci = k - tap * Ci;
         const int dy = tap / 3 - 1, dx = tap % 3 - 1;
 #pragma unroll
         for (int i = 0; i < 8; i++) {
-            const int r = (tid >> 3) + 16 * i;
+            const int r = rr + 16 * i;
             const int yy = c.y[i] + dy, xx = c.x[i] + dx;
             const bool ok = k < Kt && c.n[i] >= 0 && yy >= 0 && yy < H && xx >= 0 && xx < W;
             tc::cp_async16(sa + tc::tile_offset(r, 8 * j), ok ? in.at(c.n[i], yy, xx, ci, H, W) : in.t1, ok);
         }
 #pragma unroll
         for (int i = 0; i < NT / 16; i++) {
-            const int cc = tid + 128 * i, r = cc >> 3, jj = cc & 7;
+            const int r = rr + 16 * i, jj = j;
             const int n = c.n0 + r, kk = s * tc::kStageK + 8 * jj;
             const bool ok = n < N && kk < Kt;
             tc::cp_async16(sb + tc::tile_offset(r, 8 * jj), ok ? w + (size_t)n * Kt + kk : w, ok);
