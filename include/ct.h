@@ -34,8 +34,9 @@
  *   ct_last_error() then returns a message (thread-local, valid until the
  *   next call on the same thread).
  * - The library allocates device memory only for the workspace owned by a
- *   ct_geom (geometry tables at creation, solver state at the first solve);
- *   ct_geom_destroy frees it.  Calls that use one ct_geom must not run
+ *   ct_geom (geometry tables at creation, the ray sums A 1 at the first call
+ *   that needs them, solver state at the first solve); ct_geom_destroy frees
+ *   it.  Calls that use one ct_geom must not run
  *   concurrently on different streams.
  */
 #ifndef CT_H
@@ -116,7 +117,7 @@ void ct_geom_destroy(ct_geom *g);
  * pixel's cell weights for the voxel-driven back-projector.  Afterwards ct_forward,
  * ct_back, ct_sqs_diag and ct_relaxed_oslalm_solve stream it instead of
  * recomputing footprints; results stay within FP32 rounding of the
- * on-the-fly path.  max_bytes: refuse with CT_ENOMEM (nothing kept) when the
+ * on-the-fly path.  Also computes the ray sums A 1 from it (see ct_sqs_diag).  max_bytes: refuse with CT_ENOMEM (nothing kept) when the
  * matrix needs more; 0 means "whatever device memory allows".  bytes_out
  * (optional host pointer) receives the matrix size.  Runs on `stream` and
  * synchronises it.  Calling it again is a no-op.  Errors: CT_EINVAL,
@@ -149,8 +150,11 @@ ct_status ct_back(const ct_geom *g, const float *y, float *x, const int *views, 
 
 /* SQS majorizer of the data term, D_L = diag(A' W A 1) over all views
  * (Sec. III-A: the diagonal majorizing matrix of A'WA).  w: device [na][ns]
- * weights; d_l: device [ny][nx] output.  Uses the geometry's sinogram
- * workspace.  Errors: CT_EINVAL, CT_ENOMEM, CT_ECUDA. */
+ * weights; d_l: device [ny][nx] output.  A 1 depends on the geometry only: it
+ * is computed at the first call (or by ct_geom_precompute) and kept with the
+ * geometry, so a call costs one elementwise product and one back-projection.
+ * Uses the geometry's sinogram workspace.  Errors: CT_EINVAL, CT_ENOMEM,
+ * CT_ECUDA. */
 ct_status ct_sqs_diag(const ct_geom *g, const float *w, float *d_l, void *stream);
 
 /* Same result as ct_sqs_diag, without using or allocating any device memory

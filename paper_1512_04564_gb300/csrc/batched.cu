@@ -501,14 +501,15 @@ extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms
     if (per_sm < 1) { set_error("batched kernel cannot be resident"); return CT_ECUDA; }
     const int grid = nsm * per_sm;
 
+    // the geometries' ray sums A 1 (computed once per geometry, like the resident matrix)
+    for (int i = 0; i < nslices; i++) CT_CUDA_TRY(ensure_ray_sums(const_cast<ct_geom *>(geoms[i]), ws), "ray sums A 1");
     CT_CUDA_TRY(cudaEventRecord(ev0, ws), "event");
     for (int i = 0; i < nslices; i++) {
         const ct_geom *g = geoms[i];
         const ct_solve_params *p = &params[i];
         BatchSlice &B = hs[i];
         if (p->init_fbp) CT_CUDA_TRY(launch_fbp(g, y[i], x_inout[i], CT_FBP_HANN, ws), "initial FBP");
-        CT_CUDA_TRY(launch_fp(g->fan, FP_ONES_W, nullptr, g->d_views_all, g->fan.na, g->d_sino_ws, nullptr, w[i], ws),
-                    "D_L forward");
+        CT_CUDA_TRY(launch_weighted_ray_sums(g, w[i], g->d_sino_ws, ws), "D_L weights");
         CT_CUDA_TRY(launch_bp(g->fan, BP_PLAIN, g->d_sino_ws, g->d_views_all, g->fan.na, B.d_l,
                               p->dl_scale > 0.0f ? p->dl_scale : 1.0f, 0, nullptr, ws),
                     "D_L back");

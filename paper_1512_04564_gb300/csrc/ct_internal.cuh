@@ -98,6 +98,7 @@ struct ct_geom {
     float *d_view_beta = nullptr;
     int *d_views_all = nullptr;   // identity list [0, na)
     int *d_views_stage = nullptr; // caller view lists are staged here [na]
+    float *d_a1 = nullptr;        // ray sums A 1 over all views [na][nt][ns] (raysum.cu), or null
     float *d_sino_ws = nullptr;   // [na][nt][ns] sinogram workspace (D_L; nt = 1 in 2-D)
     // solver workspace (allocated at the first solve)
     size_t solve_bytes = 0;
@@ -357,6 +358,11 @@ cudaError_t launch_reg_update(const FanDev &G, const SolveDev &S, float beta, fl
                               int maxcurv, cudaStream_t st);
 
 cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t st, bool *too_big);
+// Ray sums A 1 of the geometry (raysum.cu): computed once and kept in g->d_a1; dropped when the
+// projector path changes (ct_geom_precompute, ct_geom_autotune).
+cudaError_t ensure_ray_sums(ct_geom *g, cudaStream_t st);
+void drop_ray_sums(ct_geom *g);
+cudaError_t launch_weighted_ray_sums(const ct_geom *g, const float *w, float *out, cudaStream_t st);  // w (A 1)
 cudaError_t launch_fbp(const ct_geom *g, const float *y, float *x, int window, cudaStream_t st);
 ct_status validate_fbp(const ct_geom *g, int window);
 

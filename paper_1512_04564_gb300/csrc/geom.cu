@@ -86,6 +86,7 @@ static void free_geom(ct_geom *g)
     cudaFree(g->d_row_c);
     cudaFree(g->d_tile_ax);
     cudaFree(g->d_vol_ws);
+    cudaFree(g->d_a1);
     delete g;
 }
 

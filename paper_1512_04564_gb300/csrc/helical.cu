@@ -1028,8 +1028,8 @@ ct_status helix_back(const ct_geom *g, const float *y, float *x, const int *view
 ct_status helix_sqs_diag(const ct_geom *g, const float *w, float *d_l, cudaStream_t st)
 {
     const int na = g->fan.na;
-    CT_CUDA_TRY(launch_fp_helix(g, FP_ONES_W, nullptr, g->d_views_all, na, g->d_sino_ws, nullptr, w, st),
-                "ct_sqs_diag forward");
+    CT_CUDA_TRY(ensure_ray_sums(const_cast<ct_geom *>(g), st), "ct_sqs_diag ray sums");
+    CT_CUDA_TRY(launch_weighted_ray_sums(g, w, g->d_sino_ws, st), "ct_sqs_diag weights");
     CT_CUDA_TRY(launch_bp_helix(g, BP_PLAIN, g->d_sino_ws, g->d_views_all, na, g->d_vol_ws, 1.0f, 0, nullptr, st),
                 "ct_sqs_diag back");
     CT_CUDA_TRY(launch_to_slices(g, g->d_vol_ws, d_l, 1.0f, 0, st), "ct_sqs_diag layout");

@@ -199,6 +199,7 @@ extern "C" ct_status ct_geom_precompute(ct_geom *g, unsigned long long max_bytes
         set_error("ct_geom_precompute: the resident matrix is built for 2-D fan-beam geometries only");
         return CT_ENOTSUP;
     }
+    const bool built_now = !g->d_row_ptr;
     if (!g->d_row_ptr) {
         bool too_big = false;
         cudaError_t e = build_matrix(g, max_bytes, (cudaStream_t)stream, &too_big);
@@ -209,6 +210,11 @@ extern "C" ct_status ct_geom_precompute(ct_geom *g, unsigned long long max_bytes
                       max_bytes);
             return CT_ENOMEM;
         }
+    }
+    if (built_now) {  // the ray sums A 1 from the resident matrix (the path every later D_L uses)
+        drop_ray_sums(g);
+        CT_CUDA_TRY(ensure_ray_sums(g, (cudaStream_t)stream), "ray sums A 1");
+        CT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream), "ray sums A 1");
     }
     if (bytes_out) *bytes_out = g->matrix_bytes;
     return CT_OK;

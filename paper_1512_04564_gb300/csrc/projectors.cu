@@ -535,9 +535,9 @@ extern "C" ct_status ct_sqs_diag(const ct_geom *g, const float *w, float *d_l, v
     if (!g || !w || !d_l) { set_error("ct_sqs_diag: null argument"); return CT_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     if (g->helical) return helix_sqs_diag(g, w, d_l, s);
-    // q = w (A 1) over all views, then D_L = A' q
-    CT_CUDA_TRY(launch_fp(g->fan, FP_ONES_W, nullptr, g->d_views_all, g->fan.na, g->d_sino_ws, nullptr, w, s),
-                "ct_sqs_diag forward");
+    // q = w (A 1) over all views (A 1 kept with the geometry), then D_L = A' q
+    CT_CUDA_TRY(ensure_ray_sums(const_cast<ct_geom *>(g), s), "ct_sqs_diag ray sums");
+    CT_CUDA_TRY(launch_weighted_ray_sums(g, w, g->d_sino_ws, s), "ct_sqs_diag weights");
     CT_CUDA_TRY(launch_bp(g->fan, BP_PLAIN, g->d_sino_ws, g->d_views_all, g->fan.na, d_l, 1.0f, 0, nullptr, s),
                 "ct_sqs_diag back");
     return CT_OK;

@@ -282,6 +282,8 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
         ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
     } eguard{exec};
 
+    // the geometry's ray sums A 1 (computed once per geometry, like the resident matrix)
+    CT_CUDA_TRY(ensure_ray_sums(g, ws), "ray sums A 1");
     CT_CUDA_TRY(cudaEventRecord(ev_start, ws), "event");
     if (p->init_fbp) CT_CUDA_TRY(launch_fbp(g, y, x, CT_FBP_HANN, ws), "initial FBP image");
     if (g->helical) {  // the kernels work on column-major volumes
@@ -289,8 +291,8 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
         if (p->x_ref) CT_CUDA_TRY(launch_to_columns(g, p->x_ref, W.xref_col, ws), "x_ref layout");
         if (p->kappa) CT_CUDA_TRY(launch_to_columns(g, p->kappa, W.kappa_col, ws), "kappa layout");
     }
-    // D_L = diag(A' W A 1) over all views
-    CT_CUDA_TRY(step_fp(g, FP_ONES_W, nullptr, g->d_views_all, na, g->d_sino_ws, nullptr, w, ws), "D_L forward");
+    // D_L = diag(A' W A 1) over all views: w (A 1), then one back-projection
+    CT_CUDA_TRY(launch_weighted_ray_sums(g, w, g->d_sino_ws, ws), "D_L weights");
     CT_CUDA_TRY(step_bp(g, BP_PLAIN, g->d_sino_ws, g->d_views_all, na, W.d_l, nullptr, ws,
                         p->dl_scale > 0.0f ? p->dl_scale : 1.0f), "D_L back");
     // rho = 1, zeta = g = M grad L_M(x), h = D_L x - zeta  (last subset)

@@ -95,6 +95,7 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, int views_per_launch, int *fp_
     }
     g->fan.fp_variant = best_fp;
     g->fan.bp_variant = best_bp;
+    drop_ray_sums(g);  // recomputed with the chosen forward projector when next needed
     if (fp_choice) *fp_choice = best_fp;
     if (bp_choice) *bp_choice = best_bp;
     return CT_OK;
