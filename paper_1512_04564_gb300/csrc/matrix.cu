@@ -13,6 +13,7 @@
 //     marked and evaluated on the fly).
 // Building it: count each ray's nonzero weights, exclusive-scan the counts
 // into row pointers, fill the rows, store the footprints.
+#include <algorithm>
 #include <vector>
 
 #include "ct_internal.cuh"
@@ -175,6 +176,26 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     matrix_foot_kernel<<<(unsigned)((size_t)G.ntx * G.nty * G.na), 256, 0, st>>>(G, ft, fan);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    // blocks of 8 adjacent cells by their entries over all views, most first: the forward projector
+    // launches them in that order, so that the short rays fill the end of the launch
+    const int nblk = (G.ns + 7) / 8;
+    {
+        std::vector<long long> hp((size_t)R + 1);
+        if ((e = cudaMemcpy(hp.data(), rp, sizeof(long long) * (R + 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return fail(e);
+        std::vector<long long> tot(nblk, 0);
+        for (int v = 0; v < G.na; v++)
+            for (int b = 0; b < nblk; b++) {
+                const long long r0 = (long long)v * G.ns + 8 * b, r1 = std::min(r0 + 8, (long long)(v + 1) * G.ns);
+                tot[b] += hp[r1] - hp[r0];
+            }
+        std::vector<int> order(nblk);
+        for (int b = 0; b < nblk; b++) order[b] = b;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tot[a] > tot[b]; });
+        if (!g->d_ray_order && (e = cudaMalloc(&g->d_ray_order, sizeof(int) * nblk)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpy(g->d_ray_order, order.data(), sizeof(int) * nblk, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(e);
+    }
     g->d_row_ptr = rp;
     g->d_row_ent = ent;
     g->d_foot_t = ft;
@@ -182,6 +203,7 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     g->matrix_bytes = bytes;
     g->fan.row_ptr = rp;
     g->fan.row_ent = ent;
+    g->fan.ray_order = g->d_ray_order;
     g->fan.foot_t = ft;
     g->fan.foot_an = fan;
     return cudaSuccess;

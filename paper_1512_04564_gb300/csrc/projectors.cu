@@ -282,7 +282,9 @@ __global__ void __launch_bounds__(kFpThreads) fp_ray_kernel(FanDev G, const floa
 // Resident-matrix forward projection: one warp per ray streams the ray's
 // (pixel, a_ij) entries (4 loads in flight per lane), gathers x from L1/L2 and
 // reduces by shuffles.  The 8 warps of a CTA take 8 adjacent cells of one view,
-// whose wedges cover nearly the same pixels.
+// whose wedges cover nearly the same pixels.  CTAs run the cell blocks in the
+// geometry's ray_order (most entries first, every view of the list for each
+// block), so that the end of the launch is made of short rays.
 template <int MODE>
 __global__ void __launch_bounds__(256) fp_csr_kernel(FanDev G, const float *__restrict__ x,
                                                      const int *__restrict__ views, int nviews,
@@ -290,10 +292,9 @@ __global__ void __launch_bounds__(256) fp_csr_kernel(FanDev G, const float *__re
                                                      const float *__restrict__ w)
 {
     const int lane = threadIdx.x & 31;
-    const long ray = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (ray >= (long)nviews * G.ns) return;  // whole warp
-    const int k = (int)(ray / G.ns);
-    const int s = (int)(ray - (long)k * G.ns);
+    const int rank = (int)(blockIdx.x / (unsigned)nviews), k = (int)(blockIdx.x - (unsigned)rank * nviews);
+    const int s = 8 * __ldg(&G.ray_order[rank]) + (threadIdx.x >> 5);
+    if (s >= G.ns) return;  // whole warp
     const int v = __ldg(&views[k]);
     const size_t r = (size_t)v * G.ns + s;
     const long long b = __ldg(&G.row_ptr[r]), e = __ldg(&G.row_ptr[r + 1]);
@@ -356,10 +357,14 @@ __device__ __forceinline__ void bp_epilogue(const FanDev &G, const SolveDev &S, 
     }
 }
 
-// One CTA per 16x16 tile, 128 threads, two pixels per thread (rows ly and
-// ly + 8 of the tile).  With the resident matrix each (view, pixel) is one
-// stored record of cell weights, and the next view's records are loaded
-// while the current view's are used.
+// One CTA per (16x16 tile, chunk of the view list), 128 threads, two pixels per
+// thread (rows ly and ly + 8 of the tile).  With the resident matrix each
+// (view, pixel) is one stored record of cell weights, and the next view's
+// records are loaded while the current view's are used.  With several chunks
+// (gridDim.z > 1; the tiles alone do not fill the GPU) each CTA leaves its
+// partial sums in G.bp_part; the last CTA of a tile to finish (a per-tile
+// counter) adds the chunks' partials in chunk order, so the result does not
+// depend on the finishing order, and runs the epilogue.
 template <int MODE, bool STORED>
 __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const float *__restrict__ sino,
                                                               const int *__restrict__ views, int nviews,
@@ -370,6 +375,8 @@ __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const
     const int ix = blockIdx.x * kTile + lx, iy0 = blockIdx.y * kTile + ly, iy1 = iy0 + kTile / 2;
     const int tile = blockIdx.y * G.ntx + blockIdx.x;
     const int ntiles = G.ntx * G.nty;
+    const int nch = (int)gridDim.z;
+    const int vb = (int)(((long)blockIdx.z * nviews) / nch), ve = (int)(((long)(blockIdx.z + 1) * nviews) / nch);
     // footprints are evaluated for in-image pixels only (a partial tile's outside pixels take the
     // edge pixel's, and their results are not stored); rows ly and ly + 8 lie in two anchor tiles
     const int ixc = min(ix, G.nx - 1), iy0c = min(iy0, G.ny - 1), iy1c = min(iy1, G.ny - 1);
@@ -381,15 +388,15 @@ __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const
         const size_t base = (size_t)tile * (kTile * kTile) + threadIdx.x;
         float4 tn0 = make_float4(0.f, 0.f, 0.f, 0.f), tn1 = tn0;
         float2 an0 = make_float2(0.f, 0.f), an1 = an0;
-        if (nviews > 0) {
-            const size_t i = (size_t)__ldg(&views[0]) * vstride + base;
+        if (vb < ve) {
+            const size_t i = (size_t)__ldg(&views[vb]) * vstride + base;
             tn0 = __ldcs(&G.foot_t[i]); an0 = __ldcs(&G.foot_an[i]);
             tn1 = __ldcs(&G.foot_t[i + kBpThreads]); an1 = __ldcs(&G.foot_an[i + kBpThreads]);
         }
-        for (int k = 0; k < nviews; k++) {
+        for (int k = vb; k < ve; k++) {
             const float4 w0 = tn0, w1 = tn1;
             const float2 b0 = an0, b1 = an1;
-            if (k + 1 < nviews) {
+            if (k + 1 < ve) {
                 const size_t i = (size_t)__ldg(&views[k + 1]) * vstride + base;
                 tn0 = __ldcs(&G.foot_t[i]); an0 = __ldcs(&G.foot_an[i]);
                 tn1 = __ldcs(&G.foot_t[i + kBpThreads]); an1 = __ldcs(&G.foot_an[i + kBpThreads]);
@@ -406,7 +413,7 @@ __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const
             if (!wide1) acc1 += record_dot(w1, b1, row, G.ns);
         }
     } else {
-        for (int k = 0; k < nviews; k++) {
+        for (int k = vb; k < ve; k++) {
             const int v = __ldg(&views[k]);
             const float2 cs = __ldg(&G.view_cs[v]);
             const Footprint F0 = pixel_footprint(G, v, cs.x, cs.y, ixc, iy0c);
@@ -416,10 +423,29 @@ __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const
             acc1 += footprint_dot(F1, row, G.ns);
         }
     }
+    if (nch > 1) {
+        const size_t pstride = (size_t)ntiles * (kTile * kTile), pi = (size_t)tile * (kTile * kTile) + threadIdx.x;
+        G.bp_part[blockIdx.z * pstride + pi] = acc0;
+        G.bp_part[blockIdx.z * pstride + pi + kBpThreads] = acc1;
+        __threadfence();
+        __syncthreads();
+        __shared__ int s_last;
+        if (threadIdx.x == 0) s_last = atomicAdd(&G.bp_count[tile], 1) == nch - 1;
+        __syncthreads();
+        if (!s_last) return;  // whole CTA
+        __threadfence();
+        acc0 = 0.0f;
+        acc1 = 0.0f;
+        for (int c = 0; c < nch; c++) {
+            acc0 += __ldcg(&G.bp_part[c * pstride + pi]);
+            acc1 += __ldcg(&G.bp_part[c * pstride + pi + kBpThreads]);
+        }
+        if (threadIdx.x == 0) G.bp_count[tile] = 0;  // for the next launch
+    }
     bp_epilogue<MODE>(G, S, xo, ix, iy0, acc0, rho, scale, accumulate);
     bp_epilogue<MODE>(G, S, xo, ix, iy1, acc1, rho, scale, accumulate);
     if (MODE == BP_SOLVE_UPDATE) {
-        // the last block to finish advances the subiteration counter (rho for the next one)
+        // the last tile to finish advances the subiteration counter (rho for the next one)
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -445,7 +471,7 @@ cudaError_t launch_fp(const FanDev &G, int mode, const float *x, const int *view
     if (var == FP_VAR_BUNDLE && !bundle_ok) var = FP_AUTO;
     if (var == FP_AUTO) var = G.row_ptr ? FP_VAR_CSR : (bundle_ok ? FP_VAR_BUNDLE : FP_VAR_RAY);
     if (var == FP_VAR_CSR) {
-        const unsigned blocks = (unsigned)(((long)nviews * G.ns + 7) / 8);
+        const unsigned blocks = (unsigned)nviews * (unsigned)((G.ns + 7) / 8);
         switch (mode) {
         case FP_PLAIN: fp_csr_kernel<FP_PLAIN><<<blocks, 256, 0, st>>>(G, x, views, nviews, out, y, w); break;
         case FP_RESID: fp_csr_kernel<FP_RESID><<<blocks, 256, 0, st>>>(G, x, views, nviews, out, y, w); break;
@@ -476,7 +502,14 @@ cudaError_t launch_fp(const FanDev &G, int mode, const float *x, const int *view
 cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *views, int nviews, float *x,
                       float scale, int accumulate, const SolveDev *S, cudaStream_t st)
 {
-    dim3 grid(G.ntx, G.nty);
+    // split the views into chunks when the tiles alone fill less than about five waves of
+    // 8 CTAs per SM (chunks of at least 4 views)
+    int nch = 1;
+    if (G.bp_part && G.bp_count) {
+        const int tiles = G.ntx * G.nty;
+        while (nch < kBpChunksMax && (long)tiles * nch < 6144 && nviews / (nch + 1) >= 4) nch++;
+    }
+    dim3 grid(G.ntx, G.nty, nch);
     SolveDev s0{};
     const SolveDev &SS = S ? *S : s0;
     const bool stored = G.foot_t && G.bp_variant != BP_VAR_FLY;
