@@ -13,7 +13,6 @@
 namespace ct {
 
 constexpr int kTile = 16;            // pixels per side of a back-projector tile (CTA) and record block
-constexpr int kBpChunksMax = 6;      // view chunks of one back-projection launch (partial sums per chunk)
 constexpr int kAnchor = 8;           // pixels per side of an anchor tile (FP64-derived reference point)
 constexpr float kAnchorHalf = 3.5f;  // offset of an anchor tile's centre from its first pixel, in pixels
 
@@ -45,8 +44,6 @@ struct FanDev {
     const long long *row_ptr; // [na*ns + 1]: start of each ray's entries
     const int2 *row_ent;      // (pixel index, a_ij bits), ray-major, march order within a ray
     const int *ray_order;     // [ceil(ns/8)]: blocks of 8 adjacent cells, most entries first
-    float *bp_part;           // [kBpChunksMax][ntiles][256]: back-projector partial sums per view chunk
-    int *bp_count;            // [ntiles]: chunks of each tile finished (0 between launches)
     int fp_variant;           // forward projector chosen by ct_geom_autotune (FP_AUTO: default order)
     int bp_variant;           // back-projector chosen by ct_geom_autotune (BP_AUTO)
 };
@@ -103,8 +100,6 @@ struct ct_geom {
     int *d_views_all = nullptr;   // identity list [0, na)
     int *d_views_stage = nullptr; // caller view lists are staged here [na]
     int *d_ray_order = nullptr;   // FanDev::ray_order
-    float *d_bp_part = nullptr;   // FanDev::bp_part (2-D)
-    int *d_bp_count = nullptr;    // FanDev::bp_count (2-D)
     float *d_a1 = nullptr;        // ray sums A 1 over all views [na][nt][ns] (raysum.cu), or null
     float *d_sino_ws = nullptr;   // [na][nt][ns] sinogram workspace (D_L; nt = 1 in 2-D)
     // solver workspace (allocated at the first solve)

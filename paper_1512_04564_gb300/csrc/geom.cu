@@ -88,8 +88,6 @@ static void free_geom(ct_geom *g)
     cudaFree(g->d_vol_ws);
     cudaFree(g->d_a1);
     cudaFree(g->d_ray_order);
-    cudaFree(g->d_bp_part);
-    cudaFree(g->d_bp_count);
     delete g;
 }
 
@@ -256,19 +254,6 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         ct_status st = cuda_fail(e, "ct_geom_create");
         free_geom(g);
         return st;
-    }
-    if (!helical) {  // back-projector partial sums per view chunk, and the per-tile chunk counters
-        const size_t tiles = (size_t)F.ntx * F.nty;
-        e = cudaMalloc(&g->d_bp_part, sizeof(float) * kBpChunksMax * tiles * kTile * kTile);
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_bp_count, sizeof(int) * tiles);
-        if (e == cudaSuccess) e = cudaMemset(g->d_bp_count, 0, sizeof(int) * tiles);
-        if (e != cudaSuccess) {
-            ct_status st = cuda_fail(e, "ct_geom_create (back-projector workspace)");
-            free_geom(g);
-            return st;
-        }
-        F.bp_part = g->d_bp_part;
-        F.bp_count = g->d_bp_count;
     }
     if (e == cudaSuccess && helical) {
         // axial tables (FP64 on the host): per view, the volume's lower face relative to the source

@@ -357,14 +357,10 @@ __device__ __forceinline__ void bp_epilogue(const FanDev &G, const SolveDev &S, 
     }
 }
 
-// One CTA per (16x16 tile, chunk of the view list), 128 threads, two pixels per
-// thread (rows ly and ly + 8 of the tile).  With the resident matrix each
-// (view, pixel) is one stored record of cell weights, and the next view's
-// records are loaded while the current view's are used.  With several chunks
-// (gridDim.z > 1; the tiles alone do not fill the GPU) each CTA leaves its
-// partial sums in G.bp_part; the last CTA of a tile to finish (a per-tile
-// counter) adds the chunks' partials in chunk order, so the result does not
-// depend on the finishing order, and runs the epilogue.
+// One CTA per 16x16 tile, 128 threads, two pixels per thread (rows ly and
+// ly + 8 of the tile).  With the resident matrix each (view, pixel) is one
+// stored record of cell weights, and the next view's records are loaded
+// while the current view's are used.
 template <int MODE, bool STORED>
 __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const float *__restrict__ sino,
                                                               const int *__restrict__ views, int nviews,
@@ -375,8 +371,6 @@ __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const
     const int ix = blockIdx.x * kTile + lx, iy0 = blockIdx.y * kTile + ly, iy1 = iy0 + kTile / 2;
     const int tile = blockIdx.y * G.ntx + blockIdx.x;
     const int ntiles = G.ntx * G.nty;
-    const int nch = (int)gridDim.z;
-    const int vb = (int)(((long)blockIdx.z * nviews) / nch), ve = (int)(((long)(blockIdx.z + 1) * nviews) / nch);
     // footprints are evaluated for in-image pixels only (a partial tile's outside pixels take the
     // edge pixel's, and their results are not stored); rows ly and ly + 8 lie in two anchor tiles
     const int ixc = min(ix, G.nx - 1), iy0c = min(iy0, G.ny - 1), iy1c = min(iy1, G.ny - 1);
@@ -388,15 +382,15 @@ __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const
         const size_t base = (size_t)tile * (kTile * kTile) + threadIdx.x;
         float4 tn0 = make_float4(0.f, 0.f, 0.f, 0.f), tn1 = tn0;
         float2 an0 = make_float2(0.f, 0.f), an1 = an0;
-        if (vb < ve) {
-            const size_t i = (size_t)__ldg(&views[vb]) * vstride + base;
+        if (nviews > 0) {
+            const size_t i = (size_t)__ldg(&views[0]) * vstride + base;
             tn0 = __ldcs(&G.foot_t[i]); an0 = __ldcs(&G.foot_an[i]);
             tn1 = __ldcs(&G.foot_t[i + kBpThreads]); an1 = __ldcs(&G.foot_an[i + kBpThreads]);
         }
-        for (int k = vb; k < ve; k++) {
+        for (int k = 0; k < nviews; k++) {
             const float4 w0 = tn0, w1 = tn1;
             const float2 b0 = an0, b1 = an1;
-            if (k + 1 < ve) {
+            if (k + 1 < nviews) {
                 const size_t i = (size_t)__ldg(&views[k + 1]) * vstride + base;
                 tn0 = __ldcs(&G.foot_t[i]); an0 = __ldcs(&G.foot_an[i]);
                 tn1 = __ldcs(&G.foot_t[i + kBpThreads]); an1 = __ldcs(&G.foot_an[i + kBpThreads]);
@@ -413,7 +407,7 @@ __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const
             if (!wide1) acc1 += record_dot(w1, b1, row, G.ns);
         }
     } else {
-        for (int k = vb; k < ve; k++) {
+        for (int k = 0; k < nviews; k++) {
             const int v = __ldg(&views[k]);
             const float2 cs = __ldg(&G.view_cs[v]);
             const Footprint F0 = pixel_footprint(G, v, cs.x, cs.y, ixc, iy0c);
@@ -423,29 +417,10 @@ __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const
             acc1 += footprint_dot(F1, row, G.ns);
         }
     }
-    if (nch > 1) {
-        const size_t pstride = (size_t)ntiles * (kTile * kTile), pi = (size_t)tile * (kTile * kTile) + threadIdx.x;
-        G.bp_part[blockIdx.z * pstride + pi] = acc0;
-        G.bp_part[blockIdx.z * pstride + pi + kBpThreads] = acc1;
-        __threadfence();
-        __syncthreads();
-        __shared__ int s_last;
-        if (threadIdx.x == 0) s_last = atomicAdd(&G.bp_count[tile], 1) == nch - 1;
-        __syncthreads();
-        if (!s_last) return;  // whole CTA
-        __threadfence();
-        acc0 = 0.0f;
-        acc1 = 0.0f;
-        for (int c = 0; c < nch; c++) {
-            acc0 += __ldcg(&G.bp_part[c * pstride + pi]);
-            acc1 += __ldcg(&G.bp_part[c * pstride + pi + kBpThreads]);
-        }
-        if (threadIdx.x == 0) G.bp_count[tile] = 0;  // for the next launch
-    }
     bp_epilogue<MODE>(G, S, xo, ix, iy0, acc0, rho, scale, accumulate);
     bp_epilogue<MODE>(G, S, xo, ix, iy1, acc1, rho, scale, accumulate);
     if (MODE == BP_SOLVE_UPDATE) {
-        // the last tile to finish advances the subiteration counter (rho for the next one)
+        // the last block to finish advances the subiteration counter (rho for the next one)
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -502,14 +477,7 @@ cudaError_t launch_fp(const FanDev &G, int mode, const float *x, const int *view
 cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *views, int nviews, float *x,
                       float scale, int accumulate, const SolveDev *S, cudaStream_t st)
 {
-    // split the views into chunks when the tiles alone fill less than about five waves of
-    // 8 CTAs per SM (chunks of at least 4 views)
-    int nch = 1;
-    if (G.bp_part && G.bp_count) {
-        const int tiles = G.ntx * G.nty;
-        while (nch < kBpChunksMax && (long)tiles * nch < 6144 && nviews / (nch + 1) >= 4) nch++;
-    }
-    dim3 grid(G.ntx, G.nty, nch);
+    dim3 grid(G.ntx, G.nty);
     SolveDev s0{};
     const SolveDev &SS = S ? *S : s0;
     const bool stored = G.foot_t && G.bp_variant != BP_VAR_FLY;
