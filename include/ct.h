@@ -112,16 +112,18 @@ void ct_geom_destroy(ct_geom *g);
 /* Build the resident system matrix of a 2-D geometry: the same SF weights
  * a_ij that the projectors otherwise evaluate on the fly (Sec. III: A is the
  * forward projection matrix of the scan), stored once in device memory
- * owned by g as (1) ray-major compressed rows of (pixel, a_ij) for the
- * ray-driven forward projector and (2) per-(view, pixel) records of the
- * pixel's cell weights for the voxel-driven back-projector.  Afterwards ct_forward,
+ * owned by g as (1) ray-major compressed rows (a_ij, and the pixel index
+ * as a 16-bit step from the previous entry's) for the ray-driven forward
+ * projector and (2) per-(view, pixel) records of the pixel's cell weights
+ * for the voxel-driven back-projector.  Afterwards ct_forward,
  * ct_back, ct_sqs_diag and ct_relaxed_oslalm_solve stream it instead of
  * recomputing footprints; results stay within FP32 rounding of the
  * on-the-fly path.  Also computes the ray sums A 1 from it (see ct_sqs_diag).  max_bytes: refuse with CT_ENOMEM (nothing kept) when the
  * matrix needs more; 0 means "whatever device memory allows".  bytes_out
  * (optional host pointer) receives the matrix size.  Runs on `stream` and
  * synchronises it.  Calling it again is a no-op.  Errors: CT_EINVAL,
- * CT_ENOMEM, CT_ECUDA. */
+ * CT_ENOMEM, CT_ENOTSUP (an image too wide for 16-bit steps, some 6000
+ * pixels), CT_ECUDA. */
 ct_status ct_geom_precompute(ct_geom *g, unsigned long long max_bytes, unsigned long long *bytes_out, void *stream);
 
 /* Projector autotuner (an implementation choice; the paper has no

@@ -250,22 +250,8 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const BatchSlice *__r
                 const size_t ri = (size_t)v * B.G.ns + sc;
                 float acc = 0.0f;
                 if (B.G.row_ptr) {
-                    const long long b0 = B.G.row_ptr[ri], e0 = B.G.row_ptr[ri + 1];
-                    float a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-                    long long i = b0 + lane;
-                    for (; i + 96 < e0; i += 128) {  // four loads in flight per lane
-                        const int2 q0 = __ldcs(&B.G.row_ent[i]), q1 = __ldcs(&B.G.row_ent[i + 32]);
-                        const int2 q2 = __ldcs(&B.G.row_ent[i + 64]), q3 = __ldcs(&B.G.row_ent[i + 96]);
-                        acc = fmaf(__int_as_float(q0.y), __ldcg(&B.x_new[q0.x]), acc);
-                        a1 = fmaf(__int_as_float(q1.y), __ldcg(&B.x_new[q1.x]), a1);
-                        a2 = fmaf(__int_as_float(q2.y), __ldcg(&B.x_new[q2.x]), a2);
-                        a3 = fmaf(__int_as_float(q3.y), __ldcg(&B.x_new[q3.x]), a3);
-                    }
-                    for (; i < e0; i += 32) {
-                        const int2 q = __ldcs(&B.G.row_ent[i]);
-                        acc = fmaf(__int_as_float(q.y), __ldcg(&B.x_new[q.x]), acc);
-                    }
-                    acc = (acc + a1) + (a2 + a3);
+                    acc = csr_ray_dot<false, true>(B.G, B.G.row_ptr[ri], B.G.row_ptr[ri + 1], B.G.row_first[ri],
+                                                   B.x_new, lane);
                 } else {
                     const float2 cs = __ldg(&B.G.view_cs[v]);
                     ray_visit(B.G, v, sc, lane, 32, [&](int ix, int iy) {

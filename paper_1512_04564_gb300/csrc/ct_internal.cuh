@@ -41,8 +41,10 @@ struct FanDev {
     const float4 *foot_t;     // [na][ntiles][256]: a_ij of the pixel's first four cells n0 .. n0+3
     const float2 *foot_an;    // [na][ntiles][256]: a_ij of cell n0+4, and n0 as int bits (kWideRecord:
                               // the footprint covers more than kRecordCells cells; evaluate it on the fly)
-    const long long *row_ptr; // [na*ns + 1]: start of each ray's entries
-    const int2 *row_ent;      // (pixel index, a_ij bits), ray-major, march order within a ray
+    const long long *row_ptr; // [na*ns + 1]: start of each ray's entries (ray-major, march order within a ray)
+    const float *row_w;       // [nnz]: a_ij of each entry
+    const short *row_d;       // [nnz]: pixel index minus the previous entry's (0 for a ray's first entry)
+    const int *row_first;     // [na*ns]: pixel index of each ray's first entry
     const int *ray_order;     // [ceil(ns/8)]: blocks of 8 adjacent cells, most entries first
     int fp_variant;           // forward projector chosen by ct_geom_autotune (FP_AUTO: default order)
     int bp_variant;           // back-projector chosen by ct_geom_autotune (BP_AUTO)
@@ -108,7 +110,9 @@ struct ct_geom {
     double fov_radius = 0.0;
     // resident system matrix (ct_geom_precompute)
     long long *d_row_ptr = nullptr;
-    int2 *d_row_ent = nullptr;
+    float *d_row_w = nullptr;
+    short *d_row_d = nullptr;
+    int *d_row_first = nullptr;
     float4 *d_foot_t = nullptr;
     float2 *d_foot_an = nullptr;
     unsigned long long matrix_bytes = 0;
@@ -340,6 +344,53 @@ __device__ __forceinline__ Footprint footprint_from(float4 t, float2 an)
     F.amp = an.x;
     F.n = __float_as_int(an.y);
     return F;
+}
+
+// One ray of the resident matrix, warp-cooperative (all 32 lanes call it with the same range):
+// sum of a_ij x_j over the entries [b, e).  Lane l takes entries b + l + 32 c; a chunk's pixel
+// indices are the running sum of its 16-bit steps (an inclusive warp scan) on top of the previous
+// chunks' total.  ONES: sum of a_ij (x = 1).  COHERENT: x read with L1-bypassing loads.
+template <bool ONES, bool COHERENT>
+__device__ __forceinline__ float csr_ray_dot(const FanDev &G, long long b, long long e, int first,
+                                             const float *__restrict__ x, int lane)
+{
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    int carry = first;
+    for (long long c0 = b; c0 < e; c0 += 128) {
+        float w[4];
+        int d[4];
+        bool ok[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {  // eight streaming loads in flight per lane
+            const long long i = c0 + 32 * q + lane;
+            ok[q] = i < e;
+            w[q] = ok[q] ? __ldcs(&G.row_w[i]) : 0.0f;
+            d[q] = (!ONES && ok[q]) ? (int)__ldcs(&G.row_d[i]) : 0;
+        }
+        if (ONES) {
+            a0 += w[0]; a1 += w[1]; a2 += w[2]; a3 += w[3];
+            continue;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, d[q], o);
+                if (lane >= o) d[q] += t;
+            }
+        float xv[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int p = carry + d[q];
+            carry += __shfl_sync(0xffffffffu, d[q], 31);
+            xv[q] = ok[q] ? (COHERENT ? __ldcg(&x[p]) : __ldg(&x[p])) : 0.0f;
+        }
+        a0 = fmaf(w[0], xv[0], a0);
+        a1 = fmaf(w[1], xv[1], a1);
+        a2 = fmaf(w[2], xv[2], a2);
+        a3 = fmaf(w[3], xv[3], a3);
+    }
+    return (a0 + a1) + (a2 + a3);
 }
 
 // ---------------------------------------------------------------- launchers (projectors.cu)

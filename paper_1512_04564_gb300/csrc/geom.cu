@@ -79,7 +79,9 @@ static void free_geom(ct_geom *g)
     cudaFree(g->d_sino_ws);
     cudaFree(g->d_solve);
     cudaFree(g->d_row_ptr);
-    cudaFree(g->d_row_ent);
+    cudaFree(g->d_row_w);
+    cudaFree(g->d_row_d);
+    cudaFree(g->d_row_first);
     cudaFree(g->d_foot_t);
     cudaFree(g->d_foot_an);
     cudaFree(g->d_view_zb);

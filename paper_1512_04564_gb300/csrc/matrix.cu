@@ -5,8 +5,10 @@
 // in HBM (about 15 GB for 512x512 pixels, 984 views x 888 cells), so it is
 // evaluated once with the same device functions the on-the-fly projectors
 // use and then streamed:
-//   * ray-major rows: for every ray, the (pixel, a_ij) pairs in the order the
-//     ray kernel visits them (march order), for the ray-driven projector;
+//   * ray-major rows: for every ray, its a_ij in the order the ray kernel
+//     visits the pixels (march order) and the pixel indices as 16-bit steps
+//     from the previous entry's (6 bytes per entry), for the ray-driven
+//     projector;
 //   * per-(view, pixel) records: the a_ij of the footprint's first five cells
 //     and the base cell, laid out tile by tile, for the voxel-driven
 //     back-projector (footprints wider than five cells, ~1% at 512x512, are
@@ -35,8 +37,11 @@ __global__ void __launch_bounds__(256) matrix_count_kernel(FanDev G, long long *
     counts[ray] = c;
 }
 
+// Entries of one ray in march order: a_ij, and the pixel index as a 16-bit step from the previous
+// entry's (the first entry's index in first[ray]); *too_far is set if a step does not fit.
 __global__ void __launch_bounds__(256) matrix_fill_kernel(FanDev G, const long long *__restrict__ row_ptr,
-                                                          int2 *__restrict__ ent)
+                                                          float *__restrict__ wts, short *__restrict__ steps,
+                                                          int *__restrict__ first, int *__restrict__ too_far)
 {
     const long ray = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (ray >= (long)G.na * G.ns) return;
@@ -44,11 +49,23 @@ __global__ void __launch_bounds__(256) matrix_fill_kernel(FanDev G, const long l
     const float2 cs = __ldg(&G.view_cs[v]);
     long long p = row_ptr[ray];
     const long long end = row_ptr[ray + 1];
+    int prev = -1;
     ray_visit(G, v, s, 0, 1, [&](int ix, int iy) {
         const Footprint F = pixel_footprint(G, v, cs.x, cs.y, ix, iy);
         const float wv = cell_weight(F, s);
-        if (wv != 0.0f && p < end) ent[p++] = make_int2(iy * G.nx + ix, __float_as_int(wv));
+        if (wv != 0.0f && p < end) {
+            const int j = iy * G.nx + ix;
+            int dj = 0;
+            if (prev < 0) first[ray] = j;
+            else dj = j - prev;
+            if (dj > 32767 || dj < -32768) atomicExch(too_far, 1);
+            wts[p] = wv;
+            steps[p] = (short)dj;
+            prev = j;
+            p++;
+        }
     });
+    if (prev < 0) first[ray] = 0;
 }
 
 __global__ void __launch_bounds__(256) matrix_foot_kernel(FanDev G, float4 *__restrict__ ft, float2 *__restrict__ fan)
@@ -141,14 +158,18 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     const long long R = (long long)G.na * G.ns;
     const size_t ntile_px = (size_t)G.ntx * G.nty * kTile * kTile;
     long long *rp = nullptr;
-    int2 *ent = nullptr;
+    float *wts = nullptr;
+    short *steps = nullptr;
+    int *first = nullptr;
     float4 *ft = nullptr;
     float2 *fan = nullptr;
     cudaError_t e = cudaMalloc(&rp, sizeof(long long) * (R + 1));
     if (e != cudaSuccess) return e;
     auto fail = [&](cudaError_t err) {
         cudaFree(rp);
-        cudaFree(ent);
+        cudaFree(wts);
+        cudaFree(steps);
+        cudaFree(first);
         cudaFree(ft);
         cudaFree(fan);
         return err;
@@ -159,8 +180,8 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     if ((e = exclusive_scan(rp, R + 1, st)) != cudaSuccess) return fail(e);
     long long nnz = 0;
     if ((e = cudaMemcpy(&nnz, rp + R, sizeof(long long), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
-    const unsigned long long bytes = (unsigned long long)(R + 1) * 8ull + (unsigned long long)nnz * 8ull +
-                                     (unsigned long long)G.na * ntile_px * 24ull;
+    const unsigned long long bytes = (unsigned long long)(R + 1) * 8ull + (unsigned long long)R * 4ull +
+                                     (unsigned long long)nnz * 6ull + (unsigned long long)G.na * ntile_px * 24ull;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     if ((max_bytes && bytes > max_bytes) || bytes > (unsigned long long)(0.9 * (double)free_b)) {
@@ -168,14 +189,23 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
         g->matrix_bytes = bytes;
         return fail(cudaSuccess);
     }
-    if ((e = cudaMalloc(&ent, sizeof(int2) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&wts, sizeof(float) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&steps, sizeof(short) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&first, sizeof(int) * (size_t)(R + 1))) != cudaSuccess) return fail(e);  // + the flag
     if ((e = cudaMalloc(&ft, sizeof(float4) * G.na * ntile_px)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&fan, sizeof(float2) * G.na * ntile_px)) != cudaSuccess) return fail(e);
-    matrix_fill_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(G, rp, ent);
+    if ((e = cudaMemsetAsync(first + R, 0, sizeof(int), st)) != cudaSuccess) return fail(e);
+    matrix_fill_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(G, rp, wts, steps, first, first + R);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     matrix_foot_kernel<<<(unsigned)((size_t)G.ntx * G.nty * G.na), 256, 0, st>>>(G, ft, fan);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    int far = 0;
+    if ((e = cudaMemcpy(&far, first + R, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
+    if (far) {  // pixel-index steps beyond 16 bits (an image some 6000 pixels wide): no resident matrix
+        g->matrix_bytes = 0;
+        return fail(cudaErrorNotSupported);
+    }
     // blocks of 8 adjacent cells by their entries over all views, most first: the forward projector
     // launches them in that order, so that the short rays fill the end of the launch
     const int nblk = (G.ns + 7) / 8;
@@ -197,12 +227,16 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
             return fail(e);
     }
     g->d_row_ptr = rp;
-    g->d_row_ent = ent;
+    g->d_row_w = wts;
+    g->d_row_d = steps;
+    g->d_row_first = first;
     g->d_foot_t = ft;
     g->d_foot_an = fan;
     g->matrix_bytes = bytes;
     g->fan.row_ptr = rp;
-    g->fan.row_ent = ent;
+    g->fan.row_w = wts;
+    g->fan.row_d = steps;
+    g->fan.row_first = first;
     g->fan.ray_order = g->d_ray_order;
     g->fan.foot_t = ft;
     g->fan.foot_an = fan;
@@ -225,6 +259,10 @@ extern "C" ct_status ct_geom_precompute(ct_geom *g, unsigned long long max_bytes
     if (!g->d_row_ptr) {
         bool too_big = false;
         cudaError_t e = build_matrix(g, max_bytes, (cudaStream_t)stream, &too_big);
+        if (e == cudaErrorNotSupported) {
+            set_error("ct_geom_precompute: the image is too wide for the matrix's 16-bit pixel steps");
+            return CT_ENOTSUP;
+        }
         if (e != cudaSuccess) return cuda_fail(e, "building the system matrix");
         if (too_big) {
             if (bytes_out) *bytes_out = g->matrix_bytes;

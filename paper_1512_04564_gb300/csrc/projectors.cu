@@ -280,8 +280,8 @@ __global__ void __launch_bounds__(kFpThreads) fp_ray_kernel(FanDev G, const floa
 }
 
 // Resident-matrix forward projection: one warp per ray streams the ray's
-// (pixel, a_ij) entries (4 loads in flight per lane), gathers x from L1/L2 and
-// reduces by shuffles.  The 8 warps of a CTA take 8 adjacent cells of one view,
+// entries (a_ij and the 16-bit pixel-index steps, eight loads in flight per
+// lane), gathers x from L1/L2 and reduces by shuffles.  The 8 warps of a CTA take 8 adjacent cells of one view,
 // whose wedges cover nearly the same pixels.  CTAs run the cell blocks in the
 // geometry's ray_order (most entries first, every view of the list for each
 // block), so that the end of the launch is made of short rays.
@@ -298,28 +298,7 @@ __global__ void __launch_bounds__(256) fp_csr_kernel(FanDev G, const float *__re
     const int v = __ldg(&views[k]);
     const size_t r = (size_t)v * G.ns + s;
     const long long b = __ldg(&G.row_ptr[r]), e = __ldg(&G.row_ptr[r + 1]);
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    long long i = b + lane;
-    for (; i + 96 < e; i += 128) {
-        const int2 q0 = __ldcs(&G.row_ent[i]);
-        const int2 q1 = __ldcs(&G.row_ent[i + 32]);
-        const int2 q2 = __ldcs(&G.row_ent[i + 64]);
-        const int2 q3 = __ldcs(&G.row_ent[i + 96]);
-        if (MODE == FP_ONES_W) {
-            a0 += __int_as_float(q0.y); a1 += __int_as_float(q1.y);
-            a2 += __int_as_float(q2.y); a3 += __int_as_float(q3.y);
-        } else {
-            a0 = fmaf(__int_as_float(q0.y), __ldg(&x[q0.x]), a0);
-            a1 = fmaf(__int_as_float(q1.y), __ldg(&x[q1.x]), a1);
-            a2 = fmaf(__int_as_float(q2.y), __ldg(&x[q2.x]), a2);
-            a3 = fmaf(__int_as_float(q3.y), __ldg(&x[q3.x]), a3);
-        }
-    }
-    for (; i < e; i += 32) {
-        const int2 q = __ldcs(&G.row_ent[i]);
-        a0 = (MODE == FP_ONES_W) ? a0 + __int_as_float(q.y) : fmaf(__int_as_float(q.y), __ldg(&x[q.x]), a0);
-    }
-    float acc = (a0 + a1) + (a2 + a3);
+    float acc = csr_ray_dot<MODE == FP_ONES_W, false>(G, b, e, __ldg(&G.row_first[r]), x, lane);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane != 0) return;
