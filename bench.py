@@ -945,10 +945,11 @@ def kernel_roofline(ct, G, g, M, y, w, x, matrix_bytes):
     ntile_px = ((g.nx + 15) // 16) * ((g.ny + 15) // 16) * 256
     if matrix_bytes:
         R = g.na * g.ns
-        nnz_total = (matrix_bytes - 8 * (R + 1) - 4 * R - 24 * g.na * ntile_px) // 6
+        # the rows' entries (6 B each: a_ij + 16-bit offset) and chunk bases (4 B per 32 entries)
+        entry_bytes = matrix_bytes - 8 * (R + 1) - 4 * (R + 2) - 24 * g.na * ntile_px
         # FP: the subset's (pixel, a_ij) rows + row pointers, x once, y written
-        # 6 B per nonzero (a_ij + 16-bit pixel step), 12 B per ray (row pointer, first pixel), image, output
-        fp_bytes = 6 * nnz_total * nv / g.na + 12 * nv * g.ns + 4 * npix + 4 * nv * g.ns
+        # the subset's share of the entries, 12 B per ray (row and chunk pointers), image, output
+        fp_bytes = entry_bytes * nv / g.na + 12 * nv * g.ns + 4 * npix + 4 * nv * g.ns
         # BP: one stored footprint (24 B) per (view, pixel slot), the residual rows, x written
         bp_bytes = 24 * ntile_px * nv + 4 * nv * g.ns + 4 * npix
     else:

@@ -43,8 +43,10 @@ struct FanDev {
                               // the footprint covers more than kRecordCells cells; evaluate it on the fly)
     const long long *row_ptr; // [na*ns + 1]: start of each ray's entries (ray-major, march order within a ray)
     const float *row_w;       // [nnz]: a_ij of each entry
-    const short *row_d;       // [nnz]: pixel index minus the previous entry's (0 for a ray's first entry)
-    const int *row_first;     // [na*ns]: pixel index of each ray's first entry
+    const short *row_d;       // [nnz]: pixel index minus the index of the first entry of its chunk (the
+                              // ray's entries in runs of 32 from its first)
+    const int *row_first;     // [na*ns + 1]: first chunk of each ray in row_base
+    const int *row_base;      // [chunks]: pixel index of each chunk's first entry
     const int *ray_order;     // [ceil(ns/8)]: blocks of 8 adjacent cells, most entries first
     int fp_variant;           // forward projector chosen by ct_geom_autotune (FP_AUTO: default order)
     int bp_variant;           // back-projector chosen by ct_geom_autotune (BP_AUTO)
@@ -113,6 +115,7 @@ struct ct_geom {
     float *d_row_w = nullptr;
     short *d_row_d = nullptr;
     int *d_row_first = nullptr;
+    int *d_row_base = nullptr;
     float4 *d_foot_t = nullptr;
     float2 *d_foot_an = nullptr;
     unsigned long long matrix_bytes = 0;
@@ -347,44 +350,34 @@ __device__ __forceinline__ Footprint footprint_from(float4 t, float2 an)
 }
 
 // One ray of the resident matrix, warp-cooperative (all 32 lanes call it with the same range):
-// sum of a_ij x_j over the entries [b, e).  Lane l takes entries b + l + 32 c; a chunk's pixel
-// indices are the running sum of its 16-bit steps (an inclusive warp scan) on top of the previous
-// chunks' total.  ONES: sum of a_ij (x = 1).  COHERENT: x read with L1-bypassing loads.
+// sum of a_ij x_j over the entries [b, e).  Lane l takes entries b + l + 32 c, so each warp load
+// covers one chunk of the ray: the chunk's base pixel index (one broadcast load) plus the entry's
+// 16-bit offset.  chunk0: the ray's first chunk in row_base.  ONES: sum of a_ij (x = 1).  COHERENT:
+// x read with L1-bypassing loads.
 template <bool ONES, bool COHERENT>
-__device__ __forceinline__ float csr_ray_dot(const FanDev &G, long long b, long long e, int first,
+__device__ __forceinline__ float csr_ray_dot(const FanDev &G, long long b, long long e, int chunk0,
                                              const float *__restrict__ x, int lane)
 {
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    int carry = first;
-    for (long long c0 = b; c0 < e; c0 += 128) {
+    int c = chunk0;
+    for (long long c0 = b; c0 < e; c0 += 128, c += 4) {
         float w[4];
-        int d[4];
+        int p[4];
         bool ok[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {  // eight streaming loads in flight per lane
+        for (int q = 0; q < 4; q++) {  // twelve loads in flight per lane (weights, offsets, bases)
             const long long i = c0 + 32 * q + lane;
             ok[q] = i < e;
             w[q] = ok[q] ? __ldcs(&G.row_w[i]) : 0.0f;
-            d[q] = (!ONES && ok[q]) ? (int)__ldcs(&G.row_d[i]) : 0;
+            if (!ONES) p[q] = ok[q] ? __ldg(&G.row_base[c + q]) + (int)__ldcs(&G.row_d[i]) : 0;
         }
         if (ONES) {
             a0 += w[0]; a1 += w[1]; a2 += w[2]; a3 += w[3];
             continue;
         }
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, d[q], o);
-                if (lane >= o) d[q] += t;
-            }
         float xv[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int p = carry + d[q];
-            carry += __shfl_sync(0xffffffffu, d[q], 31);
-            xv[q] = ok[q] ? (COHERENT ? __ldcg(&x[p]) : __ldg(&x[p])) : 0.0f;
-        }
+        for (int q = 0; q < 4; q++) xv[q] = ok[q] ? (COHERENT ? __ldcg(&x[p[q]]) : __ldg(&x[p[q]])) : 0.0f;
         a0 = fmaf(w[0], xv[0], a0);
         a1 = fmaf(w[1], xv[1], a1);
         a2 = fmaf(w[2], xv[2], a2);

@@ -82,6 +82,7 @@ static void free_geom(ct_geom *g)
     cudaFree(g->d_row_w);
     cudaFree(g->d_row_d);
     cudaFree(g->d_row_first);
+    cudaFree(g->d_row_base);
     cudaFree(g->d_foot_t);
     cudaFree(g->d_foot_an);
     cudaFree(g->d_view_zb);

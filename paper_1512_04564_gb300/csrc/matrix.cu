@@ -6,9 +6,9 @@
 // evaluated once with the same device functions the on-the-fly projectors
 // use and then streamed:
 //   * ray-major rows: for every ray, its a_ij in the order the ray kernel
-//     visits the pixels (march order) and the pixel indices as 16-bit steps
-//     from the previous entry's (6 bytes per entry), for the ray-driven
-//     projector;
+//     visits the pixels (march order), each pixel index as a 16-bit offset
+//     from the first index of its run of 32 entries, and one 32-bit base
+//     index per run (6.1 bytes per entry), for the ray-driven projector;
 //   * per-(view, pixel) records: the a_ij of the footprint's first five cells
 //     and the base cell, laid out tile by tile, for the voxel-driven
 //     back-projector (footprints wider than five cells, ~1% at 512x512, are
@@ -37,35 +37,37 @@ __global__ void __launch_bounds__(256) matrix_count_kernel(FanDev G, long long *
     counts[ray] = c;
 }
 
-// Entries of one ray in march order: a_ij, and the pixel index as a 16-bit step from the previous
-// entry's (the first entry's index in first[ray]); *too_far is set if a step does not fit.
+// Entries of one ray in march order: a_ij, and the pixel index as a 16-bit offset from the index of
+// the first entry of its chunk (the ray's entries in runs of 32), chunk bases in base[chunk0[ray] ..];
+// *too_far is set if an offset does not fit.
 __global__ void __launch_bounds__(256) matrix_fill_kernel(FanDev G, const long long *__restrict__ row_ptr,
-                                                          float *__restrict__ wts, short *__restrict__ steps,
-                                                          int *__restrict__ first, int *__restrict__ too_far)
+                                                          const int *__restrict__ chunk0, float *__restrict__ wts,
+                                                          short *__restrict__ offs, int *__restrict__ base,
+                                                          int *__restrict__ too_far)
 {
     const long ray = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (ray >= (long)G.na * G.ns) return;
     const int v = (int)(ray / G.ns), s = (int)(ray - (long)v * G.ns);
     const float2 cs = __ldg(&G.view_cs[v]);
-    long long p = row_ptr[ray];
-    const long long end = row_ptr[ray + 1];
-    int prev = -1;
+    const long long b = row_ptr[ray], end = row_ptr[ray + 1];
+    long long p = b;
+    int cur = 0, c = chunk0[ray];
     ray_visit(G, v, s, 0, 1, [&](int ix, int iy) {
         const Footprint F = pixel_footprint(G, v, cs.x, cs.y, ix, iy);
         const float wv = cell_weight(F, s);
         if (wv != 0.0f && p < end) {
             const int j = iy * G.nx + ix;
-            int dj = 0;
-            if (prev < 0) first[ray] = j;
-            else dj = j - prev;
+            if ((p - b) % 32 == 0) {
+                cur = j;
+                base[c++] = j;
+            }
+            const int dj = j - cur;
             if (dj > 32767 || dj < -32768) atomicExch(too_far, 1);
             wts[p] = wv;
-            steps[p] = (short)dj;
-            prev = j;
+            offs[p] = (short)dj;
             p++;
         }
     });
-    if (prev < 0) first[ray] = 0;
 }
 
 __global__ void __launch_bounds__(256) matrix_foot_kernel(FanDev G, float4 *__restrict__ ft, float2 *__restrict__ fan)
@@ -161,6 +163,7 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     float *wts = nullptr;
     short *steps = nullptr;
     int *first = nullptr;
+    int *base = nullptr;
     float4 *ft = nullptr;
     float2 *fan = nullptr;
     cudaError_t e = cudaMalloc(&rp, sizeof(long long) * (R + 1));
@@ -170,6 +173,7 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
         cudaFree(wts);
         cudaFree(steps);
         cudaFree(first);
+        cudaFree(base);
         cudaFree(ft);
         cudaFree(fan);
         return err;
@@ -180,8 +184,10 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     if ((e = exclusive_scan(rp, R + 1, st)) != cudaSuccess) return fail(e);
     long long nnz = 0;
     if ((e = cudaMemcpy(&nnz, rp + R, sizeof(long long), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
+    // rows: pointers, chunk pointers, 6 bytes per entry, a base index per 32 entries (bounded by nnz/32 + R)
     const unsigned long long bytes = (unsigned long long)(R + 1) * 8ull + (unsigned long long)R * 4ull +
-                                     (unsigned long long)nnz * 6ull + (unsigned long long)G.na * ntile_px * 24ull;
+                                     (unsigned long long)nnz * 6ull + ((unsigned long long)nnz / 32 + R) * 4ull +
+                                     (unsigned long long)G.na * ntile_px * 24ull;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     if ((max_bytes && bytes > max_bytes) || bytes > (unsigned long long)(0.9 * (double)free_b)) {
@@ -191,17 +197,32 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     }
     if ((e = cudaMalloc(&wts, sizeof(float) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&steps, sizeof(short) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&first, sizeof(int) * (size_t)(R + 1))) != cudaSuccess) return fail(e);  // + the flag
+    // chunk pointers (runs of 32 entries of each ray), on the host from the row pointers
+    std::vector<long long> hp((size_t)R + 1);
+    if ((e = cudaMemcpy(hp.data(), rp, sizeof(long long) * (R + 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return fail(e);
+    std::vector<int> hc((size_t)R + 2);
+    long long nchunks = 0;
+    for (long long r = 0; r < R; r++) {
+        hc[r] = (int)nchunks;
+        nchunks += (hp[r + 1] - hp[r] + 31) / 32;
+    }
+    hc[R] = (int)nchunks;
+    hc[R + 1] = 0;  // the too-far flag
+    if (nchunks >= (1LL << 31) - 4) return fail(cudaErrorNotSupported);
+    if ((e = cudaMalloc(&first, sizeof(int) * (size_t)(R + 2))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&base, sizeof(int) * (size_t)(nchunks + 4))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(first, hc.data(), sizeof(int) * (R + 2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e);
     if ((e = cudaMalloc(&ft, sizeof(float4) * G.na * ntile_px)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&fan, sizeof(float2) * G.na * ntile_px)) != cudaSuccess) return fail(e);
-    if ((e = cudaMemsetAsync(first + R, 0, sizeof(int), st)) != cudaSuccess) return fail(e);
-    matrix_fill_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(G, rp, wts, steps, first, first + R);
+    matrix_fill_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(G, rp, first, wts, steps, base, first + R + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     matrix_foot_kernel<<<(unsigned)((size_t)G.ntx * G.nty * G.na), 256, 0, st>>>(G, ft, fan);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
     int far = 0;
-    if ((e = cudaMemcpy(&far, first + R, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(&far, first + R + 1, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
     if (far) {  // pixel-index steps beyond 16 bits (an image some 6000 pixels wide): no resident matrix
         g->matrix_bytes = 0;
         return fail(cudaErrorNotSupported);
@@ -210,9 +231,6 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     // launches them in that order, so that the short rays fill the end of the launch
     const int nblk = (G.ns + 7) / 8;
     {
-        std::vector<long long> hp((size_t)R + 1);
-        if ((e = cudaMemcpy(hp.data(), rp, sizeof(long long) * (R + 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
-            return fail(e);
         std::vector<long long> tot(nblk, 0);
         for (int v = 0; v < G.na; v++)
             for (int b = 0; b < nblk; b++) {
@@ -226,17 +244,22 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
         if ((e = cudaMemcpy(g->d_ray_order, order.data(), sizeof(int) * nblk, cudaMemcpyHostToDevice)) != cudaSuccess)
             return fail(e);
     }
+    // the exact size: row pointers, chunk pointers (+ flag), entries, chunk bases, records
+    g->matrix_bytes = (unsigned long long)(R + 1) * 8ull + (unsigned long long)(R + 2) * 4ull +
+                      (unsigned long long)nnz * 6ull + (unsigned long long)(nchunks + 4) * 4ull +
+                      (unsigned long long)G.na * ntile_px * 24ull;
     g->d_row_ptr = rp;
     g->d_row_w = wts;
     g->d_row_d = steps;
     g->d_row_first = first;
+    g->d_row_base = base;
     g->d_foot_t = ft;
     g->d_foot_an = fan;
-    g->matrix_bytes = bytes;
     g->fan.row_ptr = rp;
     g->fan.row_w = wts;
     g->fan.row_d = steps;
     g->fan.row_first = first;
+    g->fan.row_base = base;
     g->fan.ray_order = g->d_ray_order;
     g->fan.foot_t = ft;
     g->fan.foot_an = fan;
