@@ -41,10 +41,11 @@ struct FanDev {
     const float4 *foot_t;     // [na][ntiles][256]: a_ij of the pixel's first four cells n0 .. n0+3
     const float2 *foot_an;    // [na][ntiles][256]: a_ij of cell n0+4, and n0 as int bits (kWideRecord:
                               // the footprint covers more than kRecordCells cells; evaluate it on the fly)
-    const long long *row_ptr; // [na*ns + 1]: start of each ray's entries (ray-major, march order within a ray)
-    const float *row_w;       // [nnz]: a_ij of each entry
-    const short *row_d;       // [nnz]: pixel index minus the index of the first entry of its chunk (the
-                              // ray's entries in runs of 32 from its first)
+    const long long *row_ptr; // [na*ns + 1]: start of each ray's entry pairs (ray-major; the entries in march
+                              // order, two per pair, a ray with an odd count padded by a zero entry)
+    const float2 *row_w;      // [pairs]: a_ij of the pair's two entries
+    const int *row_d;         // [pairs]: the two pixel indices as 16-bit offsets (low, high) from the first
+                              // index of the pair's chunk (the ray's pairs in runs of 32 from its first)
     const int *row_first;     // [na*ns + 1]: first chunk of each ray in row_base
     const int *row_base;      // [chunks]: pixel index of each chunk's first entry
     const int *ray_order;     // [ceil(ns/8)]: blocks of 8 adjacent cells, most entries first
@@ -112,8 +113,8 @@ struct ct_geom {
     double fov_radius = 0.0;
     // resident system matrix (ct_geom_precompute)
     long long *d_row_ptr = nullptr;
-    float *d_row_w = nullptr;
-    short *d_row_d = nullptr;
+    float2 *d_row_w = nullptr;
+    int *d_row_d = nullptr;
     int *d_row_first = nullptr;
     int *d_row_base = nullptr;
     float4 *d_foot_t = nullptr;
@@ -350,38 +351,43 @@ __device__ __forceinline__ Footprint footprint_from(float4 t, float2 an)
 }
 
 // One ray of the resident matrix, warp-cooperative (all 32 lanes call it with the same range):
-// sum of a_ij x_j over the entries [b, e).  Lane l takes entries b + l + 32 c, so each warp load
-// covers one chunk of the ray: the chunk's base pixel index (one broadcast load) plus the entry's
-// 16-bit offset.  chunk0: the ray's first chunk in row_base.  ONES: sum of a_ij (x = 1).  COHERENT:
-// x read with L1-bypassing loads.
+// sum of a_ij x_j over the entry pairs [b, e).  Lane l takes pairs b + l + 32 c, so each warp load
+// covers one chunk of the ray: one 8-byte load of two weights, one 4-byte load of two 16-bit offsets,
+// and the chunk's base pixel index (a broadcast load).  chunk0: the ray's first chunk in row_base.
+// ONES: sum of a_ij (x = 1).  COHERENT: x read with L1-bypassing loads.
 template <bool ONES, bool COHERENT>
 __device__ __forceinline__ float csr_ray_dot(const FanDev &G, long long b, long long e, int chunk0,
                                              const float *__restrict__ x, int lane)
 {
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
     int c = chunk0;
-    for (long long c0 = b; c0 < e; c0 += 128, c += 4) {
-        float w[4];
+    for (long long c0 = b; c0 < e; c0 += 64, c += 2) {
+        float2 w[2];
         int p[4];
-        bool ok[4];
+        bool ok[2];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {  // twelve loads in flight per lane (weights, offsets, bases)
+        for (int q = 0; q < 2; q++) {  // two pairs (four entries) in flight per lane
             const long long i = c0 + 32 * q + lane;
             ok[q] = i < e;
-            w[q] = ok[q] ? __ldcs(&G.row_w[i]) : 0.0f;
-            if (!ONES) p[q] = ok[q] ? __ldg(&G.row_base[c + q]) + (int)__ldcs(&G.row_d[i]) : 0;
+            w[q] = ok[q] ? __ldcs(&G.row_w[i]) : make_float2(0.0f, 0.0f);
+            if (!ONES) {
+                const int d = ok[q] ? __ldcs(&G.row_d[i]) : 0;
+                const int base = ok[q] ? __ldg(&G.row_base[c + q]) : 0;
+                p[2 * q] = base + (int)(short)(d & 0xffff);
+                p[2 * q + 1] = base + (d >> 16);
+            }
         }
         if (ONES) {
-            a0 += w[0]; a1 += w[1]; a2 += w[2]; a3 += w[3];
+            a0 += w[0].x; a1 += w[0].y; a2 += w[1].x; a3 += w[1].y;
             continue;
         }
         float xv[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) xv[q] = ok[q] ? (COHERENT ? __ldcg(&x[p[q]]) : __ldg(&x[p[q]])) : 0.0f;
-        a0 = fmaf(w[0], xv[0], a0);
-        a1 = fmaf(w[1], xv[1], a1);
-        a2 = fmaf(w[2], xv[2], a2);
-        a3 = fmaf(w[3], xv[3], a3);
+        for (int q = 0; q < 4; q++) xv[q] = ok[q >> 1] ? (COHERENT ? __ldcg(&x[p[q]]) : __ldg(&x[p[q]])) : 0.0f;
+        a0 = fmaf(w[0].x, xv[0], a0);
+        a1 = fmaf(w[0].y, xv[1], a1);
+        a2 = fmaf(w[1].x, xv[2], a2);
+        a3 = fmaf(w[1].y, xv[3], a3);
     }
     return (a0 + a1) + (a2 + a3);
 }

@@ -6,9 +6,10 @@
 // evaluated once with the same device functions the on-the-fly projectors
 // use and then streamed:
 //   * ray-major rows: for every ray, its a_ij in the order the ray kernel
-//     visits the pixels (march order), each pixel index as a 16-bit offset
-//     from the first index of its run of 32 entries, and one 32-bit base
-//     index per run (6.1 bytes per entry), for the ray-driven projector;
+//     visits the pixels (march order), two per 12-byte pair (two weights, two
+//     16-bit pixel-index offsets from the first index of the pair's run of 32
+//     pairs) plus one 32-bit base index per run, for the ray-driven
+//     projector;
 //   * per-(view, pixel) records: the a_ij of the footprint's first five cells
 //     and the base cell, laid out tile by tile, for the voxel-driven
 //     back-projector (footprints wider than five cells, ~1% at 512x512, are
@@ -34,12 +35,12 @@ __global__ void __launch_bounds__(256) matrix_count_kernel(FanDev G, long long *
         const Footprint F = pixel_footprint(G, v, cs.x, cs.y, ix, iy);
         if (cell_weight(F, s) != 0.0f) c++;
     });
-    counts[ray] = c;
+    counts[ray] = (c + 1) / 2;  // entry pairs
 }
 
-// Entries of one ray in march order: a_ij, and the pixel index as a 16-bit offset from the index of
-// the first entry of its chunk (the ray's entries in runs of 32), chunk bases in base[chunk0[ray] ..];
-// *too_far is set if an offset does not fit.
+// Entries of one ray in march order, two per pair: a_ij, and the pixel index as a 16-bit offset from
+// the first index of its chunk (the ray's pairs in runs of 32), chunk bases in base[chunk0[ray] ..];
+// an odd count ends with a zero entry; *too_far is set if an offset does not fit.
 __global__ void __launch_bounds__(256) matrix_fill_kernel(FanDev G, const long long *__restrict__ row_ptr,
                                                           const int *__restrict__ chunk0, float *__restrict__ wts,
                                                           short *__restrict__ offs, int *__restrict__ base,
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(256) matrix_fill_kernel(FanDev G, const long l
     if (ray >= (long)G.na * G.ns) return;
     const int v = (int)(ray / G.ns), s = (int)(ray - (long)v * G.ns);
     const float2 cs = __ldg(&G.view_cs[v]);
-    const long long b = row_ptr[ray], end = row_ptr[ray + 1];
+    const long long b = 2 * row_ptr[ray], end = 2 * row_ptr[ray + 1];  // entry slots
     long long p = b;
     int cur = 0, c = chunk0[ray];
     ray_visit(G, v, s, 0, 1, [&](int ix, int iy) {
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(256) matrix_fill_kernel(FanDev G, const long l
         const float wv = cell_weight(F, s);
         if (wv != 0.0f && p < end) {
             const int j = iy * G.nx + ix;
-            if ((p - b) % 32 == 0) {
+            if ((p - b) % 64 == 0) {
                 cur = j;
                 base[c++] = j;
             }
@@ -68,6 +69,10 @@ __global__ void __launch_bounds__(256) matrix_fill_kernel(FanDev G, const long l
             p++;
         }
     });
+    if (p < end) {  // pad the last pair
+        wts[p] = 0.0f;
+        offs[p] = 0;
+    }
 }
 
 __global__ void __launch_bounds__(256) matrix_foot_kernel(FanDev G, float4 *__restrict__ ft, float2 *__restrict__ fan)
@@ -160,8 +165,8 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     const long long R = (long long)G.na * G.ns;
     const size_t ntile_px = (size_t)G.ntx * G.nty * kTile * kTile;
     long long *rp = nullptr;
-    float *wts = nullptr;
-    short *steps = nullptr;
+    float2 *wts = nullptr;
+    int *steps = nullptr;
     int *first = nullptr;
     int *base = nullptr;
     float4 *ft = nullptr;
@@ -182,11 +187,11 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     matrix_count_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(G, rp);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     if ((e = exclusive_scan(rp, R + 1, st)) != cudaSuccess) return fail(e);
-    long long nnz = 0;
+    long long nnz = 0;  // entry pairs
     if ((e = cudaMemcpy(&nnz, rp + R, sizeof(long long), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
-    // rows: pointers, chunk pointers, 6 bytes per entry, a base index per 32 entries (bounded by nnz/32 + R)
+    // rows: pointers, chunk pointers, 12 bytes per pair, a base index per 32 pairs (bounded by nnz/32 + R)
     const unsigned long long bytes = (unsigned long long)(R + 1) * 8ull + (unsigned long long)R * 4ull +
-                                     (unsigned long long)nnz * 6ull + ((unsigned long long)nnz / 32 + R) * 4ull +
+                                     (unsigned long long)nnz * 12ull + ((unsigned long long)nnz / 32 + R) * 4ull +
                                      (unsigned long long)G.na * ntile_px * 24ull;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
@@ -195,9 +200,9 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
         g->matrix_bytes = bytes;
         return fail(cudaSuccess);
     }
-    if ((e = cudaMalloc(&wts, sizeof(float) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&steps, sizeof(short) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) return fail(e);
-    // chunk pointers (runs of 32 entries of each ray), on the host from the row pointers
+    if ((e = cudaMalloc(&wts, sizeof(float2) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&steps, sizeof(int) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) return fail(e);
+    // chunk pointers (runs of 32 pairs of each ray), on the host from the row pointers
     std::vector<long long> hp((size_t)R + 1);
     if ((e = cudaMemcpy(hp.data(), rp, sizeof(long long) * (R + 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return fail(e);
@@ -216,7 +221,8 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
         return fail(e);
     if ((e = cudaMalloc(&ft, sizeof(float4) * G.na * ntile_px)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&fan, sizeof(float2) * G.na * ntile_px)) != cudaSuccess) return fail(e);
-    matrix_fill_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(G, rp, first, wts, steps, base, first + R + 1);
+    matrix_fill_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(G, rp, first, reinterpret_cast<float *>(wts),
+                                                                    reinterpret_cast<short *>(steps), base, first + R + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     matrix_foot_kernel<<<(unsigned)((size_t)G.ntx * G.nty * G.na), 256, 0, st>>>(G, ft, fan);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
@@ -246,7 +252,7 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     }
     // the exact size: row pointers, chunk pointers (+ flag), entries, chunk bases, records
     g->matrix_bytes = (unsigned long long)(R + 1) * 8ull + (unsigned long long)(R + 2) * 4ull +
-                      (unsigned long long)nnz * 6ull + (unsigned long long)(nchunks + 4) * 4ull +
+                      (unsigned long long)nnz * 12ull + (unsigned long long)(nchunks + 4) * 4ull +
                       (unsigned long long)G.na * ntile_px * 24ull;
     g->d_row_ptr = rp;
     g->d_row_w = wts;
