@@ -353,20 +353,23 @@ __device__ __forceinline__ Footprint footprint_from(float4 t, float2 an)
 // One ray of the resident matrix, warp-cooperative (all 32 lanes call it with the same range):
 // sum of a_ij x_j over the entry pairs [b, e).  Lane l takes pairs b + l + 32 c, so each warp load
 // covers one chunk of the ray: one 8-byte load of two weights, one 4-byte load of two 16-bit offsets,
-// and the chunk's base pixel index (a broadcast load).  chunk0: the ray's first chunk in row_base.
-// ONES: sum of a_ij (x = 1).  COHERENT: x read with L1-bypassing loads.
+// and the chunk's base pixel index (a broadcast load); two pairs are in flight per lane.  chunk0: the
+// ray's first chunk in row_base.  ONES: sum of a_ij (x = 1).  COHERENT: x read with L1-bypassing loads.
 template <bool ONES, bool COHERENT>
 __device__ __forceinline__ float csr_ray_dot(const FanDev &G, long long b, long long e, int chunk0,
                                              const float *__restrict__ x, int lane)
 {
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    int c = chunk0;
-    for (long long c0 = b; c0 < e; c0 += 64, c += 2) {
-        float2 w[2];
-        int p[4];
-        bool ok[2];
+    constexpr int U = 2;  // pairs in flight per lane (four: 40 registers, fewer warps, slower)
+    float acc[2 * U];
 #pragma unroll
-        for (int q = 0; q < 2; q++) {  // two pairs (four entries) in flight per lane
+    for (int q = 0; q < 2 * U; q++) acc[q] = 0.0f;
+    int c = chunk0;
+    for (long long c0 = b; c0 < e; c0 += 32 * U, c += U) {
+        float2 w[U];
+        int p[2 * U];
+        bool ok[U];
+#pragma unroll
+        for (int q = 0; q < U; q++) {
             const long long i = c0 + 32 * q + lane;
             ok[q] = i < e;
             w[q] = ok[q] ? __ldcs(&G.row_w[i]) : make_float2(0.0f, 0.0f);
@@ -377,19 +380,22 @@ __device__ __forceinline__ float csr_ray_dot(const FanDev &G, long long b, long 
                 p[2 * q + 1] = base + (d >> 16);
             }
         }
-        if (ONES) {
-            a0 += w[0].x; a1 += w[0].y; a2 += w[1].x; a3 += w[1].y;
-            continue;
-        }
-        float xv[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) xv[q] = ok[q >> 1] ? (COHERENT ? __ldcg(&x[p[q]]) : __ldg(&x[p[q]])) : 0.0f;
-        a0 = fmaf(w[0].x, xv[0], a0);
-        a1 = fmaf(w[0].y, xv[1], a1);
-        a2 = fmaf(w[1].x, xv[2], a2);
-        a3 = fmaf(w[1].y, xv[3], a3);
+        for (int q = 0; q < U; q++) {
+            if (ONES) {
+                acc[2 * q] += w[q].x;
+                acc[2 * q + 1] += w[q].y;
+            } else if (ok[q]) {
+                acc[2 * q] = fmaf(w[q].x, COHERENT ? __ldcg(&x[p[2 * q]]) : __ldg(&x[p[2 * q]]), acc[2 * q]);
+                acc[2 * q + 1] = fmaf(w[q].y, COHERENT ? __ldcg(&x[p[2 * q + 1]]) : __ldg(&x[p[2 * q + 1]]),
+                                      acc[2 * q + 1]);
+            }
+        }
     }
-    return (a0 + a1) + (a2 + a3);
+    float t = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 2 * U; q++) t += acc[q];
+    return t;
 }
 
 // ---------------------------------------------------------------- launchers (projectors.cu)
