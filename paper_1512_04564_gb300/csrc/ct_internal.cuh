@@ -380,16 +380,21 @@ __device__ __forceinline__ float csr_ray_dot(const FanDev &G, long long b, long 
                 p[2 * q + 1] = base + (d >> 16);
             }
         }
+        if (ONES) {
 #pragma unroll
-        for (int q = 0; q < U; q++) {
-            if (ONES) {
+            for (int q = 0; q < U; q++) {
                 acc[2 * q] += w[q].x;
                 acc[2 * q + 1] += w[q].y;
-            } else if (ok[q]) {
-                acc[2 * q] = fmaf(w[q].x, COHERENT ? __ldcg(&x[p[2 * q]]) : __ldg(&x[p[2 * q]]), acc[2 * q]);
-                acc[2 * q + 1] = fmaf(w[q].y, COHERENT ? __ldcg(&x[p[2 * q + 1]]) : __ldg(&x[p[2 * q + 1]]),
-                                      acc[2 * q + 1]);
             }
+            continue;
+        }
+        float xv[2 * U];  // all gathers issued before the multiply-adds
+#pragma unroll
+        for (int q = 0; q < 2 * U; q++) xv[q] = ok[q >> 1] ? (COHERENT ? __ldcg(&x[p[q]]) : __ldg(&x[p[q]])) : 0.0f;
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+            acc[2 * q] = fmaf(w[q].x, xv[2 * q], acc[2 * q]);
+            acc[2 * q + 1] = fmaf(w[q].y, xv[2 * q + 1], acc[2 * q + 1]);
         }
     }
     float t = 0.0f;

@@ -340,6 +340,66 @@ __device__ __forceinline__ void bp_epilogue(const FanDev &G, const SolveDev &S, 
 // ly + 8 of the tile).  With the resident matrix each (view, pixel) is one
 // stored record of cell weights, and the next view's records are loaded
 // while the current view's are used.
+// Resident-matrix back-projection, one CTA per half tile (16 x 8 pixels, the first or last 128
+// records of a tile's block), one pixel per thread: twice the CTAs and warps of the two-pixel
+// kernel, which with 1024 tiles at 512 x 512 left the SMs 60% empty.  The next view's record is
+// loaded while the current view's is used; footprints wider than a record are evaluated on the fly.
+template <int MODE>
+__global__ void __launch_bounds__(kBpThreads, 16) bp_records_kernel(FanDev G, const float *__restrict__ sino,
+                                                                  const int *__restrict__ views, int nviews,
+                                                                  float *__restrict__ xo, float scale,
+                                                                  int accumulate, SolveDev S)
+{
+    const int half = blockIdx.y & 1, ty = blockIdx.y >> 1;
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile + half * (kTile / 2);
+    const int ix = blockIdx.x * kTile + lx, iy = ty * kTile + ly;
+    const int tile = ty * G.ntx + blockIdx.x;
+    const int ixc = min(ix, G.nx - 1), iyc = min(iy, G.ny - 1);
+    float rho = 1.0f;
+    if (MODE == BP_SOLVE_UPDATE) rho = __ldcg(&S.rho_tab[__ldcg(&S.counter[0])]);
+    float acc = 0.0f;
+    const size_t vstride = (size_t)G.ntx * G.nty * (kTile * kTile);
+    const size_t base = (size_t)tile * (kTile * kTile) + half * kBpThreads + threadIdx.x;
+    float4 tn = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 an = make_float2(0.f, 0.f);
+    if (nviews > 0) {
+        const size_t i = (size_t)__ldg(&views[0]) * vstride + base;
+        tn = __ldcs(&G.foot_t[i]);
+        an = __ldcs(&G.foot_an[i]);
+    }
+    for (int k = 0; k < nviews; k++) {
+        const float4 w = tn;
+        const float2 b = an;
+        if (k + 1 < nviews) {
+            const size_t i = (size_t)__ldg(&views[k + 1]) * vstride + base;
+            tn = __ldcs(&G.foot_t[i]);
+            an = __ldcs(&G.foot_an[i]);
+        }
+        const float *row = sino + (size_t)k * G.ns;
+        if (__float_as_int(b.y) == kWideRecord) {  // rare: a footprint wider than a record
+            const int v = __ldg(&views[k]);
+            const float2 cs = __ldg(&G.view_cs[v]);
+            acc += footprint_dot(pixel_footprint(G, v, cs.x, cs.y, ixc, iyc), row, G.ns);
+        } else {
+            acc += record_dot(w, b, row, G.ns);
+        }
+    }
+    bp_epilogue<MODE>(G, S, xo, ix, iy, acc, rho, scale, accumulate);
+    if (MODE == BP_SOLVE_UPDATE) {
+        // the last block to finish advances the subiteration counter (rho for the next one)
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const int done = atomicAdd(&S.counter[1], 1);
+            if (done == (int)(gridDim.x * gridDim.y) - 1) {
+                S.counter[1] = 0;
+                S.counter[0] += 1;
+                __threadfence();
+            }
+        }
+    }
+}
+
 template <int MODE, bool STORED>
 __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const float *__restrict__ sino,
                                                               const int *__restrict__ views, int nviews,
@@ -461,10 +521,11 @@ cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *v
     const SolveDev &SS = S ? *S : s0;
     const bool stored = G.foot_t && G.bp_variant != BP_VAR_FLY;
     if (stored) {
+        const dim3 hgrid(G.ntx, 2 * G.nty);  // half tiles
         switch (mode) {
-        case BP_PLAIN: bp_fan2d_kernel<BP_PLAIN, true><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
-        case BP_SOLVE_INIT: bp_fan2d_kernel<BP_SOLVE_INIT, true><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
-        default: bp_fan2d_kernel<BP_SOLVE_UPDATE, true><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+        case BP_PLAIN: bp_records_kernel<BP_PLAIN><<<hgrid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+        case BP_SOLVE_INIT: bp_records_kernel<BP_SOLVE_INIT><<<hgrid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+        default: bp_records_kernel<BP_SOLVE_UPDATE><<<hgrid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
         }
         return cudaGetLastError();
     }
