@@ -57,28 +57,32 @@ __global__ void __launch_bounds__(kFiltThreads) fbp_filter_kernel(FanDev G, cons
     }
 }
 
-// Pixel-driven distance-weighted back-projection with linear interpolation.
+// Pixel-driven distance-weighted back-projection with linear interpolation.  The
+// fan angle of the pixel centre is its anchor's FP64-derived detector coordinate
+// plus the small angle between anchor and pixel (the footprint code's series),
+// instead of a full atan2 per (pixel, view).
 __global__ void __launch_bounds__(256) fbp_backproject_kernel(FanDev G, const float *__restrict__ q,
                                                               float *__restrict__ x, float dbeta)
 {
     const int ix = blockIdx.x * 32 + (threadIdx.x & 31), iy = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (ix >= G.nx || iy >= G.ny) return;
-    const float X = ((float)ix - G.cxo) * G.dx, Y = ((float)iy - G.cyo) * G.dy;
-    const float c0 = -G.gamma0 * G.inv_dg;  // detector coordinate of gamma = 0
     float acc = 0.0f;
     for (int v = 0; v < G.na; v++) {
         const float2 cs = __ldg(&G.view_cs[v]);
-        const float tpar = G.dso + X * cs.x + Y * cs.y;
-        const float tperp = fmaf(Y, cs.x, -X * cs.y);
-        const float L2 = fmaf(tpar, tpar, tperp * tperp);
-        const float u = fmaf(atan2f(tperp, tpar), G.inv_dg, c0);
-        const float fl = floorf(u);
+        float ox, oy;
+        const float4 A = pixel_anchor(G, v, ix, iy, ox, oy);
+        const float dpar = fmaf(ox, cs.x, oy * cs.y), dperp = fmaf(oy, cs.x, -ox * cs.y);
+        const float cpar = G.dso + (A.x + dpar), cperp = A.y + dperp;
+        const float crs = fmaf(G.dso, dperp, fmaf(A.x, dperp, -A.y * dpar));
+        const float dt = fmaf(G.dso, G.dso + fmaf(2.0f, A.x, dpar), fmaf(A.x, A.x + dpar, A.y * cperp));
+        const float du = atan_series(__fdividef(crs, dt)) * G.inv_dg;
+        const float fl = floorf(A.z + du);
         const int i0 = (int)fl;
-        const float f = u - fl;
+        const float f = (A.z - fl) + (A.w + du);
         const float *row = q + (size_t)v * G.ns;
         const float v0 = ((unsigned)i0 < (unsigned)G.ns) ? __ldg(&row[i0]) : 0.0f;
         const float v1 = ((unsigned)(i0 + 1) < (unsigned)G.ns) ? __ldg(&row[i0 + 1]) : 0.0f;
-        acc += fmaf(f, v1 - v0, v0) / L2;
+        acc = fmaf(fmaf(f, v1 - v0, v0), __frcp_rn(fmaf(cpar, cpar, cperp * cperp)), acc);
     }
     x[(size_t)iy * G.nx + ix] = dbeta * acc;
 }
