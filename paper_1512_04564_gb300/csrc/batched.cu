@@ -173,8 +173,8 @@ __device__ void rmsd_units(const BatchSlice &B, int iter, int chunk)
     }
 }
 
-__global__ void __launch_bounds__(kThreads) batched_kernel(const BatchSlice *__restrict__ SL, int nsl, int Tmax,
-                                                          BatchCtl *ctl)
+__global__ void __launch_bounds__(kThreads, 5) batched_kernel(const BatchSlice *__restrict__ SL, int nsl, int Tmax,
+                                                             BatchCtl *ctl)
 {
     __shared__ int s_pre[kMaxSlices + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
