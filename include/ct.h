@@ -264,12 +264,16 @@ ct_status ct_relaxed_oslalm_solve(const ct_geom *g, const float *y, const float 
                                   float *x_inout, ct_solve_report *report, void *stream);
 
 /* Batched relaxed OS-LALM: nslices independent problems (Algorithm 1 or 2
- * each, with its own geometry, sinogram, weights and parameters) solved in
- * one persistent cooperative launch, after per-slice setup launches (D_L,
- * initial gradient, optional FBP).  Slice i runs n_iter_i * M_i
+ * each, with its own geometry, sinogram, weights and parameters).  Slices
+ * of at least 384 x 384 pixels, whose own subsets fill the GPU, are solved
+ * one after another by ct_relaxed_oslalm_solve; the smaller ones together
+ * in one persistent cooperative launch, after per-slice setup launches
+ * (D_L, initial gradient, optional FBP).  There, slice i runs n_iter_i * M_i
  * subiterations; all slices advance in lockstep super-steps, and each
  * super-step's regularizer, forward-projection and back-projection work of
- * every active slice is spread over all SMs.  geoms, y, w, x_inout: host
+ * every active slice is spread over all SMs.  Report times count from the
+ * start of the call's device work (the large slices first); `seconds` is
+ * the same total in every report.  geoms, y, w, x_inout: host
  * arrays of nslices pointers (device data as in ct_relaxed_oslalm_solve;
  * slices may share a geometry); params: host array of nslices parameter
  * sets (stop_rmsd_hu is ignored: every slice runs n_iter iterations);

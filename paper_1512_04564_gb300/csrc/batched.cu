@@ -1,6 +1,7 @@
 // Batched relaxed OS-LALM: many 2-D slices of uneven size, view count and
-// subset count solved in ONE persistent cooperative launch (Algorithm 1 per
-// slice, Sec. III-A).
+// subset count (Algorithm 1 per slice, Sec. III-A).  Slices large enough to
+// fill the GPU alone go through the single-slice solver; the rest are
+// solved together in ONE persistent cooperative launch.
 //
 // All slices advance in lockstep super-steps t = 0, 1, ...: slice i runs its
 // subiteration t while t < n_iter * M_i.  Each super-step has three phases,
@@ -352,41 +353,46 @@ size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 using namespace ct;
 
-extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms, const float *const *y,
-                                                     const float *const *w, const ct_solve_params *params,
-                                                     float *const *x_inout, int nslices, ct_solve_report *reports,
-                                                     void *stream)
+namespace {
+
+// Argument checks of one slice (index i, for the message).
+ct_status validate_slice(int i, const ct_geom *g, const float *y, const float *w, const float *x,
+                         const ct_solve_params *p, int dev)
 {
-    if (!geoms || !y || !w || !params || !x_inout || nslices < 1 || nslices > kMaxSlices) {
-        set_error("ct_relaxed_oslalm_solve_batched: null argument or nslices outside [1, %d]", kMaxSlices);
+    if (!g || !y || !w || !x) { set_error("slice %d: null argument", i); return CT_EINVAL; }
+    if (g->device != dev) { set_error("slice %d: geometry on device %d, current %d", i, g->device, dev); return CT_EINVAL; }
+    if (g->helical) { set_error("slice %d: batched solves take 2-D fan-beam slices", i); return CT_ENOTSUP; }
+    if (p->M < 1 || p->M > g->fan.na || p->n_iter < 1 || p->n_iter > 100000 || !(p->alpha >= 1.0f && p->alpha < 2.0f) ||
+        !(p->beta >= 0.0f) || p->potential < CT_POT_HYPERBOLA || p->potential > CT_POT_QUADRATIC ||
+        (p->potential != CT_POT_QUADRATIC && !(p->delta > 0.0f)) ||
+        (p->algorithm != CT_ALG_PROPOSED && p->algorithm != CT_ALG_SIMPLE) ||
+        (!p->continuation && !(p->rho_fixed > 0.0f)) ||
+        (p->curvature != CT_CURV_HUBER && p->curvature != CT_CURV_MAX) || !(p->dl_scale >= 0.0f)) {
+        set_error("slice %d: invalid solver parameters", i);
         return CT_EINVAL;
     }
+    if (p->init_fbp) {
+        ct_status sf = validate_fbp(g, CT_FBP_HANN);
+        if (sf != CT_OK) return sf;
+    }
+    if ((long)p->n_iter * p->M > 50000000L) { set_error("slice %d: n_iter * M too large", i); return CT_EINVAL; }
+    return CT_OK;
+}
+
+// The persistent cooperative launch over nslices (already validated) slices.
+ct_status persistent_batch(const ct_geom *const *geoms, const float *const *y, const float *const *w,
+                           const ct_solve_params *params, float *const *x_inout, int nslices,
+                           ct_solve_report *reports, void *stream)
+{
     int dev = 0;
     CT_CUDA_TRY(cudaGetDevice(&dev), "current device");
-    // validate and size the arena
+    // size the arena
     std::vector<size_t> off(nslices);
     size_t total = 0;
     int Tmax = 0;
     for (int i = 0; i < nslices; i++) {
         const ct_geom *g = geoms[i];
         const ct_solve_params *p = &params[i];
-        if (!g || !y[i] || !w[i] || !x_inout[i]) { set_error("slice %d: null argument", i); return CT_EINVAL; }
-        if (g->device != dev) { set_error("slice %d: geometry on device %d, current %d", i, g->device, dev); return CT_EINVAL; }
-        if (g->helical) { set_error("slice %d: batched solves take 2-D fan-beam slices", i); return CT_ENOTSUP; }
-        if (p->M < 1 || p->M > g->fan.na || p->n_iter < 1 || p->n_iter > 100000 || !(p->alpha >= 1.0f && p->alpha < 2.0f) ||
-            !(p->beta >= 0.0f) || p->potential < CT_POT_HYPERBOLA || p->potential > CT_POT_QUADRATIC ||
-            (p->potential != CT_POT_QUADRATIC && !(p->delta > 0.0f)) ||
-            (p->algorithm != CT_ALG_PROPOSED && p->algorithm != CT_ALG_SIMPLE) ||
-            (!p->continuation && !(p->rho_fixed > 0.0f)) ||
-            (p->curvature != CT_CURV_HUBER && p->curvature != CT_CURV_MAX) || !(p->dl_scale >= 0.0f)) {
-            set_error("slice %d: invalid solver parameters", i);
-            return CT_EINVAL;
-        }
-        if (p->init_fbp) {
-            ct_status sf = validate_fbp(g, CT_FBP_HANN);
-            if (sf != CT_OK) return sf;
-        }
-        if ((long)p->n_iter * p->M > 50000000L) { set_error("slice %d: n_iter * M too large", i); return CT_EINVAL; }
         const int T = p->n_iter * p->M;
         Tmax = std::max(Tmax, T);
         int max_sub = (g->fan.na + p->M - 1) / p->M;
@@ -562,5 +568,103 @@ extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms
             }
         }
     }
+    return CT_OK;
+}
+
+// A slice of at least this many pixels keeps every SM busy with its own
+// subsets (a 384 x 384 slice has 576 back-projection tiles and, at 984 views
+// in 20 subsets, over 20,000 rays per subset), so the graph-replayed
+// single-slice solver, whose projector kernels run at full occupancy, is
+// faster for it than a share of the persistent launch's super-steps; only
+// smaller slices are batched.
+constexpr long kSoloPixels = 384L * 384L;
+
+// Report of a slice solved alone: its RMSD trace and iteration times, shifted
+// by the device time of the slices solved before it.
+void fill_solo_report(ct_solve_report *r, const ct_solve_params *p, const ct_solve_report &got,
+                      const std::vector<float> &trace, const std::vector<double> &times, double t0)
+{
+    const int n = p->n_iter;
+    const float tol = p->stop_rmsd_hu > 0.0f ? p->stop_rmsd_hu : 1.0f;
+    r->iters_done = n;
+    r->seconds_to_tol = -1.0;
+    r->rmsd_hu_last = got.rmsd_hu_last;
+    for (int k = 0; k < n; k++) {
+        const double tk = t0 + times[k];
+        if (r->iter_seconds) r->iter_seconds[k] = tk;
+        if (p->x_ref) {
+            if (r->rmsd_trace_hu) r->rmsd_trace_hu[k] = trace[k];
+            if (r->seconds_to_tol < 0.0 && trace[k] <= tol) r->seconds_to_tol = tk;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms, const float *const *y,
+                                                     const float *const *w, const ct_solve_params *params,
+                                                     float *const *x_inout, int nslices, ct_solve_report *reports,
+                                                     void *stream)
+{
+    if (!geoms || !y || !w || !params || !x_inout || nslices < 1 || nslices > kMaxSlices) {
+        set_error("ct_relaxed_oslalm_solve_batched: null argument or nslices outside [1, %d]", kMaxSlices);
+        return CT_EINVAL;
+    }
+    int dev = 0;
+    CT_CUDA_TRY(cudaGetDevice(&dev), "current device");
+    for (int i = 0; i < nslices; i++) {
+        const ct_status st = validate_slice(i, geoms[i], y[i], w[i], x_inout[i], &params[i], dev);
+        if (st != CT_OK) return st;
+    }
+    std::vector<int> solo, shared;
+    for (int i = 0; i < nslices; i++)
+        ((long)geoms[i]->fan.nx * geoms[i]->fan.ny >= kSoloPixels ? solo : shared).push_back(i);
+
+    double t_total = 0.0;  // device time of the slices solved so far
+    for (int i : solo) {
+        ct_solve_params q = params[i];
+        q.stop_rmsd_hu = 0.0f;  // every slice runs n_iter iterations
+        std::vector<float> trace(q.n_iter);
+        std::vector<double> times(q.n_iter);
+        ct_solve_report got{};
+        got.rmsd_trace_hu = trace.data();
+        got.iter_seconds = times.data();
+        const ct_status st = ct_relaxed_oslalm_solve(geoms[i], y[i], w[i], &q, x_inout[i], &got, stream);
+        if (st != CT_OK) return st;
+        if (reports) fill_solo_report(&reports[i], &params[i], got, trace, times, t_total);
+        t_total += got.seconds;
+    }
+    if (!shared.empty()) {
+        const size_t n = shared.size();
+        std::vector<const ct_geom *> gs(n);
+        std::vector<const float *> ys(n), wsl(n);
+        std::vector<float *> xs(n);
+        std::vector<ct_solve_params> ps(n);
+        std::vector<ct_solve_report> rs(n);
+        for (size_t k = 0; k < n; k++) {
+            const int i = shared[k];
+            gs[k] = geoms[i];
+            ys[k] = y[i];
+            wsl[k] = w[i];
+            xs[k] = x_inout[i];
+            ps[k] = params[i];
+            if (reports) rs[k] = reports[i];
+        }
+        const ct_status st = persistent_batch(gs.data(), ys.data(), wsl.data(), ps.data(), xs.data(), (int)n,
+                                              reports ? rs.data() : nullptr, stream);
+        if (st != CT_OK) return st;
+        if (reports) {
+            for (size_t k = 0; k < n; k++) {
+                ct_solve_report *r = &reports[shared[k]];
+                *r = rs[k];
+                if (r->iter_seconds)
+                    for (int it = 0; it < ps[k].n_iter; it++) r->iter_seconds[it] += t_total;
+                if (r->seconds_to_tol >= 0.0) r->seconds_to_tol += t_total;
+            }
+        }
+        t_total += rs.empty() || !reports ? 0.0 : rs[0].seconds;
+    }
+    if (reports)
+        for (int i = 0; i < nslices; i++) reports[i].seconds = t_total;
     return CT_OK;
 }

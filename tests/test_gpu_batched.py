@@ -86,6 +86,39 @@ def test_batched_matches_single_slice_solves():
         assert all(b > a for a, b in zip(reps[i]["iter_seconds"], reps[i]["iter_seconds"][1:]))
 
 
+def test_large_slice_solved_alone_in_batch():
+    """A slice of >= 384 x 384 pixels runs the single-slice solver inside the batched call."""
+    from paper_1512_04564_gb300 import ct
+
+    big = _problem(6, 384, 400, 72, 0.5)
+    small = _problem(*CASES[0][:5])
+    Gs = [ct.Geometry.from_fan(p[0]) for p in (big, small)]
+    ys = [torch.from_numpy(p[1]).cuda() for p in (big, small)]
+    ws = [torch.from_numpy(p[2]).cuda() for p in (big, small)]
+    refs, singles = [], []
+    for i, (g, _, _) in enumerate((big, small)):
+        xr = torch.zeros(g.ny, g.nx, device="cuda")
+        ct.ct_relaxed_oslalm_solve(Gs[i], ys[i], ws[i], xr, M=1, n_iter=20, alpha=1.999, beta=BETA, delta=DELTA)
+        refs.append(xr)
+        xs = torch.zeros(g.ny, g.nx, device="cuda")
+        ct.ct_relaxed_oslalm_solve(Gs[i], ys[i], ws[i], xs, M=6, n_iter=3, alpha=1.999, beta=BETA, delta=DELTA)
+        singles.append(xs)
+    params = [dict(M=6, n_iter=3, alpha=1.999, beta=BETA, delta=DELTA, x_ref=refs[i], hu_per_unit=HU)
+              for i in range(2)]
+    xb = [torch.zeros(p[0].ny, p[0].nx, device="cuda") for p in (big, small)]
+    reps = ct.ct_relaxed_oslalm_solve_batched([Gs[1], Gs[0]], [ys[1], ys[0]], [ws[1], ws[0]], [xb[1], xb[0]],
+                                              [params[1], params[0]])
+    for i, (g, _, _) in enumerate((big, small)):
+        assert _hu_rmsd(xb[i].cpu().numpy(), singles[i].cpu().numpy(), g) <= 0.01, i
+    r_small, r_big = reps
+    # the large slice is solved first, the batched rest after it; one total time for the call
+    assert r_small["seconds"] == r_big["seconds"]
+    assert r_big["iter_seconds"][-1] <= r_small["iter_seconds"][0]
+    assert r_small["iter_seconds"][-1] <= r_small["seconds"] * (1 + 1e-6)
+    assert all(b > a for a, b in zip(r_big["iter_seconds"], r_big["iter_seconds"][1:]))
+    assert len(r_big["rmsd_trace_hu"]) == 3 and r_big["rmsd_trace_hu"][-1] < r_big["rmsd_trace_hu"][0]
+
+
 def test_batched_slice_matches_oracle():
     from paper_1512_04564_gb300 import ct
 
