@@ -960,7 +960,7 @@ def kernel_roofline(ct, G, g, M, y, w, x, matrix_bytes):
     kernels = {
         "fp": {"kernel": "fp_csr_kernel" if matrix_bytes else "fp_bundle_kernel", "ms": fp_s * 1e3,
                "algorithmic_bytes": fp_bytes, "gbs": fp_bytes / fp_s / 1e9},
-        "bp": {"kernel": "bp_fan2d_kernel<stored>" if matrix_bytes else "bp_fan2d_kernel<on the fly>",
+        "bp": {"kernel": "bp_records_kernel" if matrix_bytes else "bp_fan2d_kernel<on the fly>",
                "ms": bp_s * 1e3, "algorithmic_bytes": bp_bytes, "gbs": bp_bytes / bp_s / 1e9},
     }
     dom = "bp" if bp_s >= fp_s else "fp"
