@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--M", type=int, default=None)
     ap.add_argument("--n-iter", type=int, default=None)
     ap.add_argument("--xstar-iters", type=int, default=2000)
-    ap.add_argument("--xstar-iters-batch", type=int, default=300)
+    ap.add_argument("--xstar-iters-batch", type=int, default=500,
+                    help="batch workload x*: M = 1 iterations after 20 ordered-subsets iterations from the FBP")
     ap.add_argument("--tol-hu", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-matrix", action="store_true", help="footprints on the fly instead of the resident matrix")
@@ -255,15 +256,23 @@ def run_batch(args):
     G_l = [geoms[(g.nx, g.ns, g.na)] for g, _, _, _ in slices]
     ys = [torch.from_numpy(y).cuda() for _, y, _, _ in slices]
     ws = [torch.from_numpy(w).cuda() for _, _, w, _ in slices]
-    # relaxed OS-LALM: half the named subsets (Sec. III-A), but at least 40 views per subset (with fewer,
-    # 18-25 views per subset, the ordered subsets diverge on these scans)
-    Ms = [max(1, min(M // 2, g.na // 40)) for g, _, _, M in slices]
+    # relaxed OS-LALM: half the named subsets (Sec. III-A), but at most 10, of at least 40 views each: with
+    # fewer views per subset, or 20 subsets of 49 views on the 256 x 256 slices, the iterates diverge (the
+    # FP64 oracle's as well)
+    Ms = [max(1, min(M // 2, g.na // 40, 10)) for g, _, _, M in slices]
     common = dict(alpha=1.999, beta=beta, delta=delta)
-    # x* per slice: M = 1, batched
+    # x* per slice: 20 ordered-subsets iterations from the FBP, then M = 1 iterations; the change over the
+    # last 100 of those measures how far x* still is from converged
     xst = [torch.zeros(g.ny, g.nx, device="cuda") for g, _, _, _ in slices]
     t0 = time.perf_counter()
-    ct.ct_relaxed_oslalm_solve_batched(G_l, ys, ws, xst, [dict(M=1, n_iter=args.xstar_iters_batch, **common)] * n)
+    ct.ct_relaxed_oslalm_solve_batched(G_l, ys, ws, xst, [dict(M=Ms[i], n_iter=20, init_fbp=True, **common)
+                                                          for i in range(n)])
+    ct.ct_relaxed_oslalm_solve_batched(G_l, ys, ws, xst,
+                                       [dict(M=1, n_iter=max(1, args.xstar_iters_batch - 100), **common)] * n)
+    x_prev = [x.clone() for x in xst]
+    ct.ct_relaxed_oslalm_solve_batched(G_l, ys, ws, xst, [dict(M=1, n_iter=100, **common)] * n)
     t_xstar = time.perf_counter() - t0
+    xstar_last100 = [float(((a - b) ** 2).mean().sqrt()) * hu for a, b in zip(xst, x_prev)]
     params = [dict(M=Ms[i], n_iter=20, x_ref=xst[i], hu_per_unit=hu, init_fbp=True, **common) for i in range(n)]
     for _ in range(max(1, args.warmup)):
         xs = [torch.zeros_like(x) for x in xst]
@@ -290,8 +299,11 @@ def run_batch(args):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(bt) * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch64", "sizes": BATCH_SIZES, "bins": BATCH_BINS, "views": BATCH_VIEWS,
-                   "M_named": BATCH_M, "M_rule": "min(M//2, views//40)", "alpha": 1.999, "n_iter": 20,
-                   "x0": "fbp", "xstar_iters": args.xstar_iters_batch, "geometries": len(geoms),
+                   "M_named": BATCH_M, "M_rule": "min(M//2, views//40, 10)", "alpha": 1.999, "n_iter": 20,
+                   "x0": "fbp", "xstar": f"20 its M from FBP + {args.xstar_iters_batch} its M=1",
+                   "xstar_change_last100_hu": {"median": statistics.median(xstar_last100),
+                                               "max": max(xstar_last100)},
+                   "geometries": len(geoms),
                    "resident_matrix_bytes": mat_bytes, "geometry_setup_s": round(t_geo, 3),
                    "autotuned": tuned},
         "loop_of_single_solves_s": statistics.mean(lt),
