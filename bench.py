@@ -947,7 +947,11 @@ def kernel_roofline(ct, G, g, M, y, w, x, matrix_bytes):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps * 1e-3
 
-    fp_s = timed(lambda: ct.ct_forward(G, x, out, views=views))
+    # the forward projector on the packed image [x | x^T] (the solver's update kernel writes it; ct_forward
+    # would add one packing launch)
+    xp = torch.empty(2 * x.numel(), device="cuda")
+    ct.ct_pack_image(G, x, xp)
+    fp_s = timed(lambda: ct.ct_forward_packed(G, xp, out, views=views))
     bp_s = timed(lambda: ct.ct_back(G, out, xb, views=views))
     peaks = {}
     try:

@@ -112,18 +112,21 @@ void ct_geom_destroy(ct_geom *g);
 /* Build the resident system matrix of a 2-D geometry: the same SF weights
  * a_ij that the projectors otherwise evaluate on the fly (Sec. III: A is the
  * forward projection matrix of the scan), stored once in device memory
- * owned by g as (1) ray-major compressed rows (a_ij, and the pixel index
- * as a 16-bit step from the previous entry's) for the ray-driven forward
- * projector and (2) per-(view, pixel) records of the pixel's cell weights
- * for the voxel-driven back-projector.  Afterwards ct_forward,
+ * owned by g as (1) ray-major compressed rows (a_ij in pairs, and the pixel
+ * indices as 16-bit offsets from a 32-bit base per run of 32 pairs) for the
+ * ray-driven forward projector, whose steep rays index a transposed copy of
+ * the image (the projector packs [x | x^T] into a 2 nx ny scratch that g
+ * also owns, or the solver's update kernel writes it) and (2) per-(view,
+ * pixel) records of the pixel's cell weights for the voxel-driven
+ * back-projector.  Afterwards ct_forward,
  * ct_back, ct_sqs_diag and ct_relaxed_oslalm_solve stream it instead of
  * recomputing footprints; results stay within FP32 rounding of the
  * on-the-fly path.  Also computes the ray sums A 1 from it (see ct_sqs_diag).  max_bytes: refuse with CT_ENOMEM (nothing kept) when the
  * matrix needs more; 0 means "whatever device memory allows".  bytes_out
  * (optional host pointer) receives the matrix size.  Runs on `stream` and
  * synchronises it.  Calling it again is a no-op.  Errors: CT_EINVAL,
- * CT_ENOMEM, CT_ENOTSUP (an image too wide for 16-bit steps, some 6000
- * pixels), CT_ECUDA. */
+ * CT_ENOMEM, CT_ENOTSUP (an image too wide for the 16-bit offsets),
+ * CT_ECUDA. */
 ct_status ct_geom_precompute(ct_geom *g, unsigned long long max_bytes, unsigned long long *bytes_out, void *stream);
 
 /* Projector autotuner (an implementation choice; the paper has no
@@ -143,6 +146,20 @@ ct_status ct_geom_autotune(ct_geom *g, int views_per_launch, int *fp_choice, int
  * na views in order (then nviews must be na).  1 <= nviews <= na.  Output
  * rows are overwritten.  Errors: CT_EINVAL, CT_ECUDA. */
 ct_status ct_forward(const ct_geom *g, const float *x, float *y, const int *views, int nviews, void *stream);
+
+/* The packed image [x | x^T] of a 2-D geometry: xpack[j] = x[j] and
+ * xpack[nx ny + ix ny + iy] = x[iy nx + ix] (device, 2 nx ny floats, caller-
+ * owned).  It is what the resident matrix's rows index (steep rays read the
+ * transposed copy, where their consecutive pixels are adjacent);
+ * ct_forward packs its x this way itself.  Errors: CT_EINVAL (null
+ * argument, helical geometry), CT_ECUDA. */
+ct_status ct_pack_image(const ct_geom *g, const float *x, float *xpack, void *stream);
+
+/* ct_forward of an image already packed by ct_pack_image (2-D geometries):
+ * the same y, without the packing pass, for callers that project one image
+ * many times.  Errors: as ct_forward, and CT_EINVAL for a helical geometry. */
+ct_status ct_forward_packed(const ct_geom *g, const float *xpack, float *y, const int *views, int nviews,
+                            void *stream);
 
 /* Back-projection x = scale * A_V' y (+ x if accumulate != 0), with the same
  * a_ij as ct_forward (voxel-driven, no atomics).  y: device [nviews][ns];

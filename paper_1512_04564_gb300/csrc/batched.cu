@@ -30,7 +30,7 @@ constexpr long long kMaxSpins = 1ll << 24;  // x ~100 ns sleep: ~2 s per barrier
 
 struct BatchSlice {
     FanDev G;
-    float *x, *x_new, *g, *h, *d_l, *resid;
+    float *x, *x_new, *g, *h, *d_l, *resid;  // x_new: packed [x+ | x+^T] (2 nx ny floats)
     const float *y, *w, *x_ref;
     const float *kappa;  // regularizer voxel weights, or nullptr for kappa = 1
     const int *perm;     // views in subset order
@@ -226,6 +226,8 @@ __global__ void __launch_bounds__(kThreads, 5) batched_kernel(const BatchSlice *
                 float xn = den > 0.0f ? xj - (sv + gr) / den : xj;
                 if (B.nonneg) xn = fmaxf(xn, 0.0f);
                 B.x_new[j] = xn;
+                if (B.G.row_ptr)  // the transposed half of the packed image the resident rows index
+                    B.x_new[(size_t)B.G.nx * B.G.ny + (size_t)ix * B.G.ny + iy] = xn;
             }
         }
         if (t == Tmax) break;
@@ -398,7 +400,7 @@ ct_status persistent_batch(const ct_geom *const *geoms, const float *const *y, c
         int max_sub = (g->fan.na + p->M - 1) / p->M;
         const size_t npix = (size_t)g->fan.nx * g->fan.ny;
         off[i] = total;
-        total += al256(npix * 4) * 4 + al256((size_t)max_sub * g->fan.ns * 4) + al256((size_t)g->fan.na * 4) +
+        total += al256(npix * 8) + al256(npix * 4) * 3 + al256((size_t)max_sub * g->fan.ns * 4) + al256((size_t)g->fan.na * 4) +
                  al256((size_t)(p->M + 1) * 4) + al256((size_t)T * 4) + al256((size_t)p->n_iter * 16) +
                  al256((size_t)p->n_iter * 8);
     }
@@ -441,7 +443,7 @@ ct_status persistent_batch(const ct_geom *const *geoms, const float *const *y, c
         BatchSlice &B = hs[i];
         B.G = g->fan;
         B.x = x_inout[i];
-        B.x_new = (float *)b; b += al256(npix * 4);
+        B.x_new = (float *)b; b += al256(npix * 8);  // packed [x+ | x+^T]
         B.g = (float *)b; b += al256(npix * 4);
         B.h = (float *)b; b += al256(npix * 4);
         B.d_l = (float *)b; b += al256(npix * 4);

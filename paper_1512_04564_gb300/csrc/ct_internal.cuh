@@ -48,6 +48,11 @@ struct FanDev {
                               // index of the pair's chunk (the ray's pairs in runs of 32 from its first)
     const int *row_first;     // [na*ns + 1]: first chunk of each ray in row_base
     const int *row_base;      // [chunks]: pixel index of each chunk's first entry
+                              // Pixel indices of the rows address the packed image [x | x^T] (2 nx ny
+                              // floats): a shallow ray's entries (marched column by column) index x,
+                              // iy nx + ix; a steep ray's (marched row by row) index x^T, nx ny + ix ny + iy,
+                              // so that consecutive entries of either kind are near each other in memory.
+    float *xpack;             // [2 nx ny]: packing scratch of the forward projector (with the matrix)
     const int *ray_order;     // [ceil(ns/8)]: blocks of 8 adjacent cells, most entries first
     int fp_variant;           // forward projector chosen by ct_geom_autotune (FP_AUTO: default order)
     int bp_variant;           // back-projector chosen by ct_geom_autotune (BP_AUTO)
@@ -119,6 +124,7 @@ struct ct_geom {
     int *d_row_base = nullptr;
     float4 *d_foot_t = nullptr;
     float2 *d_foot_an = nullptr;
+    float *d_xpack = nullptr;     // FanDev::xpack
     unsigned long long matrix_bytes = 0;
     int device = 0;
 };
@@ -289,6 +295,16 @@ __device__ __forceinline__ float cell_weight(const Footprint &F, int s)
 
 constexpr float kRangePad = 0.02f;  // pixels of padding on a wedge's row/column range
 
+// Whether ray (v, s) is steep (|sin phi| > |cos phi|): ray_visit then marches it row by row, else
+// column by column.  The same arithmetic as ray_visit's test.
+__device__ __forceinline__ bool ray_steep(const FanDev &G, int v, int s)
+{
+    const float phi = __ldg(&G.view_beta[v]) + fmaf((float)s, G.dgamma, G.gamma0);
+    float sp, cp;
+    sincosf(phi, &sp, &cp);
+    return !(fabsf(cp) >= fabsf(sp));
+}
+
 // Visit the pixels whose squares can meet the fan wedge of cell s in view v:
 // shallow rays march the columns (steep rays the rows) in [seg/nseg, (seg+1)/nseg)
 // of the image and visit, in each, the rows (columns) between the wedge's two
@@ -354,7 +370,8 @@ __device__ __forceinline__ Footprint footprint_from(float4 t, float2 an)
 // sum of a_ij x_j over the entry pairs [b, e).  Lane l takes pairs b + l + 32 c, so each warp load
 // covers one chunk of the ray: one 8-byte load of two weights, one 4-byte load of two 16-bit offsets,
 // and the chunk's base pixel index (a broadcast load); two pairs are in flight per lane.  chunk0: the
-// ray's first chunk in row_base.  ONES: sum of a_ij (x = 1).  COHERENT: x read with L1-bypassing loads.
+// ray's first chunk in row_base.  x: the packed image [x | x^T] the row indices address.  ONES: sum of
+// a_ij (x = 1).  COHERENT: x read with L1-bypassing loads.
 template <bool ONES, bool COHERENT>
 __device__ __forceinline__ float csr_ray_dot(const FanDev &G, long long b, long long e, int chunk0,
                                              const float *__restrict__ x, int lane)
@@ -403,6 +420,17 @@ __device__ __forceinline__ float csr_ray_dot(const FanDev &G, long long b, long 
     return t;
 }
 
+// Second half of the packed image [x | x^T] for one block of 32 columns x 8 rows (block (blockIdx.x,
+// blockIdx.y), 256 threads), whose values the block has staged in t[row][column]: thread i writes column
+// 32 bx + i / 8, rows 8 by .. 8 by + 7 of the block going to consecutive addresses of x^T.  With rows of
+// 36 floats both the staging and this read are free of shared-memory bank conflicts.
+__device__ __forceinline__ void write_transposed_block(const FanDev &G, const float (*t)[36], float *xp)
+{
+    const int c = threadIdx.x >> 3, r = threadIdx.x & 7;
+    const int ix = blockIdx.x * 32 + c, iy = blockIdx.y * 8 + r;
+    if (ix < G.nx && iy < G.ny) xp[(size_t)G.nx * G.ny + (size_t)ix * G.ny + iy] = t[r][c];
+}
+
 // ---------------------------------------------------------------- launchers (projectors.cu)
 
 enum FpMode { FP_PLAIN = 0, FP_RESID = 1, FP_ONES_W = 2 };
@@ -410,9 +438,13 @@ enum FpVariant { FP_AUTO = 0, FP_VAR_CSR = 1, FP_VAR_BUNDLE = 2, FP_VAR_RAY = 3 
 enum BpVariant { BP_AUTO = 0, BP_VAR_STORED = 1, BP_VAR_FLY = 2 };
 enum BpMode { BP_PLAIN = 0, BP_SOLVE_INIT = 1, BP_SOLVE_UPDATE = 2 };
 
-// out rows follow `views` (device list of nviews view indices).
+// out rows follow `views` (device list of nviews view indices).  With the resident rows the forward
+// projector reads the packed image [x | x^T]: xpack, if the caller has it (e.g. written by the update
+// kernel), else x is packed into G.xpack first.
 cudaError_t launch_fp(const FanDev &G, int mode, const float *x, const int *views, int nviews, float *out,
-                      const float *y, const float *w, cudaStream_t st);
+                      const float *y, const float *w, cudaStream_t st, const float *xpack = nullptr);
+// [x | x^T] of an nx x ny image into xp (2 nx ny floats).
+cudaError_t launch_pack(const FanDev &G, const float *x, float *xp, cudaStream_t st);
 cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *views, int nviews, float *x,
                       float scale, int accumulate, const SolveDev *S, cudaStream_t st);
 cudaError_t launch_reg_gradient(const FanDev &G, const float *x, const float *kappa, float beta, float delta,

@@ -9,7 +9,10 @@
 //     visits the pixels (march order), two per 12-byte pair (two weights, two
 //     16-bit pixel-index offsets from the first index of the pair's run of 32
 //     pairs) plus one 32-bit base index per run, for the ray-driven
-//     projector;
+//     projector.  The indices address the packed image [x | x^T]: a steep
+//     ray, marched row by row, indexes the transposed copy, so that the 64
+//     entries a warp gathers at once lie on a few columns of x^T instead of
+//     some twenty rows of x;
 //   * per-(view, pixel) records: the a_ij of the footprint's first five cells
 //     and the base cell, laid out tile by tile, for the voxel-driven
 //     back-projector (footprints wider than five cells, ~1% at 512x512, are
@@ -53,11 +56,12 @@ __global__ void __launch_bounds__(256) matrix_fill_kernel(FanDev G, const long l
     const long long b = 2 * row_ptr[ray], end = 2 * row_ptr[ray + 1];  // entry slots
     long long p = b;
     int cur = 0, c = chunk0[ray];
+    const bool steep = ray_steep(G, v, s);
     ray_visit(G, v, s, 0, 1, [&](int ix, int iy) {
         const Footprint F = pixel_footprint(G, v, cs.x, cs.y, ix, iy);
         const float wv = cell_weight(F, s);
         if (wv != 0.0f && p < end) {
-            const int j = iy * G.nx + ix;
+            const int j = steep ? G.nx * G.ny + ix * G.ny + iy : iy * G.nx + ix;
             if ((p - b) % 64 == 0) {
                 cur = j;
                 base[c++] = j;
@@ -171,9 +175,12 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     int *base = nullptr;
     float4 *ft = nullptr;
     float2 *fan = nullptr;
+    float *xp = nullptr;
+    if (2LL * G.nx * G.ny >= (1LL << 31)) return cudaErrorNotSupported;  // packed-image indices are 32-bit
     cudaError_t e = cudaMalloc(&rp, sizeof(long long) * (R + 1));
     if (e != cudaSuccess) return e;
     auto fail = [&](cudaError_t err) {
+        cudaFree(xp);
         cudaFree(rp);
         cudaFree(wts);
         cudaFree(steps);
@@ -221,6 +228,7 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
         return fail(e);
     if ((e = cudaMalloc(&ft, sizeof(float4) * G.na * ntile_px)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&fan, sizeof(float2) * G.na * ntile_px)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&xp, sizeof(float) * 2 * (size_t)G.nx * G.ny)) != cudaSuccess) return fail(e);
     matrix_fill_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(G, rp, first, reinterpret_cast<float *>(wts),
                                                                     reinterpret_cast<short *>(steps), base, first + R + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
@@ -229,7 +237,7 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
     int far = 0;
     if ((e = cudaMemcpy(&far, first + R + 1, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
-    if (far) {  // pixel-index steps beyond 16 bits (an image some 6000 pixels wide): no resident matrix
+    if (far) {  // pixel-index steps beyond 16 bits (an image too wide for them): no resident matrix
         g->matrix_bytes = 0;
         return fail(cudaErrorNotSupported);
     }
@@ -261,6 +269,8 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     g->d_row_base = base;
     g->d_foot_t = ft;
     g->d_foot_an = fan;
+    g->d_xpack = xp;
+    g->fan.xpack = xp;
     g->fan.row_ptr = rp;
     g->fan.row_w = wts;
     g->fan.row_d = steps;

@@ -473,10 +473,33 @@ __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const
     }
 }
 
+// The packed image [x | x^T] the resident rows index: xp[j] = x[j] and xp[nx ny + ix ny + iy] = x[iy nx + ix].
+// 32 x 8 pixel blocks, transposed through shared memory so that both halves are written in whole sectors.
+__global__ void __launch_bounds__(256) pack_kernel(FanDev G, const float *__restrict__ x, float *__restrict__ xp)
+{
+    __shared__ float t[8][36];
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    const int ix = blockIdx.x * 32 + lx, iy = blockIdx.y * 8 + ly;
+    if (ix < G.nx && iy < G.ny) {
+        const float v = __ldg(&x[(size_t)iy * G.nx + ix]);
+        xp[(size_t)iy * G.nx + ix] = v;
+        t[ly][lx] = v;
+    }
+    __syncthreads();
+    write_transposed_block(G, t, xp);
+}
+
 }  // namespace
 
+cudaError_t launch_pack(const FanDev &G, const float *x, float *xp, cudaStream_t st)
+{
+    dim3 grid((G.nx + 31) / 32, (G.ny + 7) / 8);
+    pack_kernel<<<grid, 256, 0, st>>>(G, x, xp);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fp(const FanDev &G, int mode, const float *x, const int *views, int nviews, float *out,
-                      const float *y, const float *w, cudaStream_t st)
+                      const float *y, const float *w, cudaStream_t st, const float *xpack)
 {
     if (nviews <= 0) return cudaSuccess;
     const bool bundle_ok = G.max_span <= kMaxSpan && G.nx <= kMaxMarch && G.ny <= kMaxMarch;
@@ -486,6 +509,14 @@ cudaError_t launch_fp(const FanDev &G, int mode, const float *x, const int *view
     if (var == FP_AUTO) var = G.row_ptr ? FP_VAR_CSR : (bundle_ok ? FP_VAR_BUNDLE : FP_VAR_RAY);
     if (var == FP_VAR_CSR) {
         const unsigned blocks = (unsigned)nviews * (unsigned)((G.ns + 7) / 8);
+        if (mode != FP_ONES_W) {  // the rows index the packed image
+            if (!xpack) {
+                const cudaError_t e = launch_pack(G, x, G.xpack, st);
+                if (e != cudaSuccess) return e;
+                xpack = G.xpack;
+            }
+            x = xpack;
+        }
         switch (mode) {
         case FP_PLAIN: fp_csr_kernel<FP_PLAIN><<<blocks, 256, 0, st>>>(G, x, views, nviews, out, y, w); break;
         case FP_RESID: fp_csr_kernel<FP_RESID><<<blocks, 256, 0, st>>>(G, x, views, nviews, out, y, w); break;
@@ -554,6 +585,30 @@ extern "C" ct_status ct_forward(const ct_geom *g, const float *x, float *y, cons
     const int *dv = nullptr;
     if ((st = stage_views(g, views, nviews, &dv, s)) != CT_OK) return st;
     CT_CUDA_TRY(launch_fp(g->fan, FP_PLAIN, x, dv, nviews, y, nullptr, nullptr, s), "ct_forward launch");
+    return CT_OK;
+}
+
+extern "C" ct_status ct_pack_image(const ct_geom *g, const float *x, float *xpack, void *stream)
+{
+    if (!g || !x || !xpack) { set_error("ct_pack_image: null argument"); return CT_EINVAL; }
+    if (g->helical) { set_error("ct_pack_image: 2-D geometries only"); return CT_EINVAL; }
+    CT_CUDA_TRY(launch_pack(g->fan, x, xpack, (cudaStream_t)stream), "ct_pack_image launch");
+    return CT_OK;
+}
+
+extern "C" ct_status ct_forward_packed(const ct_geom *g, const float *xpack, float *y, const int *views, int nviews,
+                                       void *stream)
+{
+    if (!g || !xpack || !y) { set_error("ct_forward_packed: null argument"); return CT_EINVAL; }
+    if (g->helical) { set_error("ct_forward_packed: 2-D geometries only"); return CT_EINVAL; }
+    ct_status st = validate_views(g, views, nviews);
+    if (st != CT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int *dv = nullptr;
+    if ((st = stage_views(g, views, nviews, &dv, s)) != CT_OK) return st;
+    // the first half is x itself, for the projectors that do not index the packed image
+    CT_CUDA_TRY(launch_fp(g->fan, FP_PLAIN, xpack, dv, nviews, y, nullptr, nullptr, s, xpack),
+                "ct_forward_packed launch");
     return CT_OK;
 }
 

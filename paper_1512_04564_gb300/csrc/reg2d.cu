@@ -32,22 +32,31 @@ __global__ void __launch_bounds__(256) reg_gradient_kernel(FanDev G, const float
     if (curv) curv[j] = cv;
 }
 
+// x+ into S.x_new; with the resident matrix also its transposed half of the packed image [x+ | x+^T]
+// that the forward projector's rows index (S.x_new then holds 2 nx ny floats).
 template <bool KAPPA>
 __global__ void __launch_bounds__(256) reg_update_kernel(FanDev G, SolveDev S, float beta, Pot P)
 {
-    const int ix = blockIdx.x * 32 + (threadIdx.x & 31), iy = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (ix >= G.nx || iy >= G.ny) return;
-    const float rho = __ldcg(&S.rho_tab[__ldcg(&S.counter[0])]);
-    float gr, cv;
-    reg_terms<false, KAPPA>(G, S.x, ix, iy, beta, P, gr, cv, S.kappa);
-    const size_t j = (size_t)iy * G.nx + ix;
-    const float xj = S.x[j], dl = S.d_l[j], g = S.g[j], h = S.h[j];
-    const float s = (S.algorithm == CT_ALG_PROPOSED) ? fmaf(rho, fmaf(dl, xj, -h), (1.0f - rho) * g)
-                                                     : fmaf(rho, h, (1.0f - rho) * g);
-    const float den = fmaf(rho, dl, cv);
-    float xn = den > 0.0f ? xj - (s + gr) / den : xj;
-    if (S.nonneg) xn = fmaxf(xn, 0.0f);
-    S.x_new[j] = xn;
+    __shared__ float t[8][36];
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    const int ix = blockIdx.x * 32 + lx, iy = blockIdx.y * 8 + ly;
+    if (ix < G.nx && iy < G.ny) {
+        const float rho = __ldcg(&S.rho_tab[__ldcg(&S.counter[0])]);
+        float gr, cv;
+        reg_terms<false, KAPPA>(G, S.x, ix, iy, beta, P, gr, cv, S.kappa);
+        const size_t j = (size_t)iy * G.nx + ix;
+        const float xj = S.x[j], dl = S.d_l[j], g = S.g[j], h = S.h[j];
+        const float s = (S.algorithm == CT_ALG_PROPOSED) ? fmaf(rho, fmaf(dl, xj, -h), (1.0f - rho) * g)
+                                                         : fmaf(rho, h, (1.0f - rho) * g);
+        const float den = fmaf(rho, dl, cv);
+        float xn = den > 0.0f ? xj - (s + gr) / den : xj;
+        if (S.nonneg) xn = fmaxf(xn, 0.0f);
+        S.x_new[j] = xn;
+        t[ly][lx] = xn;
+    }
+    if (!G.row_ptr) return;  // the same for the whole grid
+    __syncthreads();
+    write_transposed_block(G, t, S.x_new);
 }
 
 __global__ void __launch_bounds__(256) fill_kernel(float *__restrict__ p, long long n, float v)

@@ -84,7 +84,8 @@ ct_status ensure_workspace(ct_geom *g, int max_sub, int T, int n_iter, bool kapp
     const size_t view_len = (size_t)g->fan.ns * (g->helical ? g->hx.nt : 1);
     const size_t vol_h = g->helical ? npix * 4 : 0;
     size_t off[13], sz = 0;
-    const size_t sizes[13] = {npix * 4, npix * 4, npix * 4, npix * 4, (size_t)max_sub * view_len * 4,
+    // x_new holds the packed image [x+ | x+^T] in 2-D (the resident rows index it)
+    const size_t sizes[13] = {npix * (g->helical ? 4 : 8), npix * 4, npix * 4, npix * 4, (size_t)max_sub * view_len * 4,
                               (size_t)T * 4, (size_t)(n_iter > 0 ? n_iter : 1) * 4, (size_t)g->fan.na * 4, 16 * 4,
                               (size_t)kRmsdBlocks * 2 * 8, vol_h, vol_h, kappa ? vol_h : 0};
     for (int i = 0; i < 13; i++) {
@@ -130,10 +131,10 @@ cudaError_t step_update(const ct_geom *g, const SolveDev &S, const ct_solve_para
 }
 
 cudaError_t step_fp(const ct_geom *g, int mode, const float *x, const int *views, int nviews, float *out,
-                    const float *y, const float *w, cudaStream_t st)
+                    const float *y, const float *w, cudaStream_t st, const float *xpack = nullptr)
 {
     return g->helical ? launch_fp_helix(g, mode, x, views, nviews, out, y, w, st)
-                      : launch_fp(g->fan, mode, x, views, nviews, out, y, w, st);
+                      : launch_fp(g->fan, mode, x, views, nviews, out, y, w, st, xpack);
 }
 
 cudaError_t step_bp(const ct_geom *g, int mode, const float *sino, const int *views, int nviews, float *x,
@@ -256,7 +257,8 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
         cudaError_t e = cudaSuccess;
         for (int m = 0; m < M && e == cudaSuccess; m++) {
             e = step_update(g, S, p, ws);
-            if (e == cudaSuccess) e = step_fp(g, FP_RESID, W.x_new, W.perm + off[m], cnt[m], W.resid, y, w, ws);
+            if (e == cudaSuccess)  // the update kernel wrote x+ packed
+                e = step_fp(g, FP_RESID, W.x_new, W.perm + off[m], cnt[m], W.resid, y, w, ws, W.x_new);
             if (e == cudaSuccess) e = step_bp(g, BP_SOLVE_UPDATE, W.resid, W.perm + off[m], cnt[m], nullptr, &S, ws);
         }
         if (e == cudaSuccess && p->x_ref) {

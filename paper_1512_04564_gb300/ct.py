@@ -79,6 +79,8 @@ def _load():
     sigs = {
         "ct_geom_create": [ctypes.POINTER(ct_geom_desc), ctypes.POINTER(vp)],
         "ct_forward": [vp, vp, vp, ip, cint, vp],
+        "ct_pack_image": [vp, vp, vp, vp],
+        "ct_forward_packed": [vp, vp, vp, ip, cint, vp],
         "ct_back": [vp, vp, vp, ip, cint, cfl, cint, vp],
         "ct_sqs_diag": [vp, vp, vp, vp],
         "ct_sqs_diag_noalloc": [vp, vp, vp, vp],
@@ -124,7 +126,8 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_geom_precompute", "ct_geom_autotune", "ct_forward", "ct_back", "ct_sqs_diag",
+EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_geom_precompute", "ct_geom_autotune", "ct_forward",
+            "ct_pack_image", "ct_forward_packed", "ct_back", "ct_sqs_diag",
             "ct_sqs_diag_noalloc", "ct_fbp", "ct_reg_gradient", "ct_kappa", "ct_relaxed_oslalm_solve",
             "ct_relaxed_oslalm_solve_batched", "ct_last_error", "ct_version", "ct_gemm_bf16", "ct_conv3x3_bf16",
             "ct_conv3x3_bf16_dgrad", "ct_conv3x3_wgrad_workspace", "ct_conv3x3_bf16_wgrad", "ct_unet_create",
@@ -268,6 +271,21 @@ def ct_forward(geom: Geometry, x: torch.Tensor, y: torch.Tensor, views=None, str
     arr, nv = _views(views, geom.na)
     _check(_lib.ct_forward(geom.handle, _ptr(x, "x", geom.nvox), _ptr(y, "y", nv * geom.view_len), arr, nv,
                            _stream(stream)))
+    return y
+
+
+def ct_pack_image(geom: Geometry, x: torch.Tensor, xpack: torch.Tensor, stream=None) -> torch.Tensor:
+    """[x | x^T] (2 nx ny floats) of a 2-D image, the layout the resident matrix's rows index."""
+    _check(_lib.ct_pack_image(geom.handle, _ptr(x, "x", geom.nvox), _ptr(xpack, "xpack", 2 * geom.nvox),
+                              _stream(stream)))
+    return xpack
+
+
+def ct_forward_packed(geom: Geometry, xpack: torch.Tensor, y: torch.Tensor, views=None, stream=None) -> torch.Tensor:
+    """ct_forward of an image packed by ct_pack_image."""
+    arr, nv = _views(views, geom.na)
+    _check(_lib.ct_forward_packed(geom.handle, _ptr(xpack, "xpack", 2 * geom.nvox),
+                                  _ptr(y, "y", nv * geom.view_len), arr, nv, _stream(stream)))
     return y
 
 

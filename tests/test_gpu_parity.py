@@ -177,6 +177,27 @@ def test_zero_image_and_bad_views(ct):
         ct.ct_forward(G, torch.zeros(g.ny, g.nx, device="cuda"), torch.empty(0, g.ns, device="cuda"), views=[])
 
 
+def test_packed_image_and_forward(ct, make_geom):
+    """ct_pack_image writes [x | x^T]; projecting the packed image gives ct_forward's rays exactly
+    (with the resident matrix its steep rays read the transposed half)."""
+    g = SMALL  # not square: nx != ny
+    G = make_geom(g)
+    x = dev(phantom_image(g))
+    xp = torch.empty(2 * g.nx * g.ny, device="cuda")
+    ct.ct_pack_image(G, x, xp)
+    ref = torch.cat([x.reshape(-1), x.t().contiguous().reshape(-1)])
+    assert torch.equal(xp, ref)
+    y1 = torch.empty(g.na, g.ns, device="cuda")
+    y2 = torch.empty_like(y1)
+    ct.ct_forward(G, x, y1)
+    ct.ct_forward_packed(G, xp, y2)
+    assert torch.equal(y1, y2)
+    views = [3, 44, 0, 21]
+    y3 = torch.empty(len(views), g.ns, device="cuda")
+    ct.ct_forward_packed(G, xp, y3, views=views)
+    assert rel_err(y3.cpu().numpy(), y1[views].cpu().numpy()) <= 1e-6
+
+
 def test_sqs_diag_parity(ct, make_geom):
     c = synth.fan2d_128()
     d = synth.make_scan(c)
