@@ -807,7 +807,9 @@ def main():
            "d2h_bytes_per_step": x_h.numel() * 4}
 
     roof = kernel_roofline(ct, G, g, M, y, w, xstar, matrix_bytes)
-    launches = 4 + (2 if fbp0 else 0) + n_iter * (3 * M + 1)
+    # setup: D_L weights and back-projection, initial FP (+ packing [x | x^T] for the resident rows) and BP,
+    # the FBP's filter and back-projection; then 3 launches per subiteration and the RMSD per iteration
+    launches = 4 + (1 if matrix_bytes else 0) + (2 if fbp0 else 0) + n_iter * (3 * M + 1)
     # the workload's own subset count, for the record (untimed)
     m41 = {}
     if M != cfg.M:
