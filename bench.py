@@ -42,6 +42,20 @@ import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The slowest rank's value, the same on every rank (None, a run that did not reach the tolerance,
+    counts as infinitely slow and stays None).  dist: torch.distributed or None for one process; device:
+    where the reduction tensor lives ("cuda" under NCCL, "cpu" under gloo)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value if value is not None else float("inf")], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    v = float(t.item())
+    return v if math.isfinite(v) else None
+
+
 METRIC = "time to RMSD<=1 HU vs x* (s)"
 UNIT = "s"
 # outer iterations to RMSD <= 1 HU measured by the GPU arm (config.iters_to_tol), keyed by (workload, M, alpha, x0)
@@ -781,10 +795,7 @@ def main():
     if reached:
         tr = reps[-1]["rmsd_trace_hu"]
         iters_to_tol = next(i + 1 for i, r in enumerate(tr) if r <= args.tol_hu)
-    if dist is not None:
-        t = torch.tensor([value if value is not None else float("inf")], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        value = float(t.item()) if math.isfinite(t.item()) else None
+    value = max_over_ranks(value, dist, "cuda")
 
     # e2e: host buffers in, result out, through the public API
     y_h = torch.from_numpy(data.y.astype(np.float32)).pin_memory()
@@ -803,7 +814,8 @@ def main():
         x_h.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
-    e2e = {"value": statistics.mean(e2e_times), "unit": UNIT, "h2d_bytes_per_step": 2 * y_h.numel() * 4,
+    e2e = {"value": max_over_ranks(statistics.mean(e2e_times), dist, "cuda"), "unit": UNIT,
+           "h2d_bytes_per_step": 2 * y_h.numel() * 4,
            "d2h_bytes_per_step": x_h.numel() * 4}
 
     roof = kernel_roofline(ct, G, g, M, y, w, xstar, matrix_bytes)
@@ -823,8 +835,8 @@ def main():
                                     "last_rmsd_hu": round(tr[-1], 3)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": statistics.mean(step_ms), "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "ms_per_step": max_over_ranks(statistics.mean(step_ms), dist, "cuda"), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": cfg.name, "image": [g.ny, g.nx], "views": g.na, "bins": g.ns, "M": M,
                    "alpha": alpha, "n_iter": n_iter, "M_named": cfg.M, "beta_water_units": cfg.beta,
                    "x0": args.x0, "xstar_iters": args.xstar_iters,

@@ -1,0 +1,95 @@
+"""The benchmark's multi-rank host logic on CPU: two gloo ranks, no GPU.
+
+With N replicas (one seeded problem per rank, no data-path collective) the
+benchmark reports the slowest rank's time; a rank that missed the tolerance
+makes the whole job's value None.  The reference arm runs on rank 0 only.
+"""
+
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, values, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+
+    try:
+        got = [bench.max_over_ranks(v[rank], dist, "cpu") for v in values]
+        out.put((rank, got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_two_ranks():
+    values = [(0.5, 0.25), (0.1, 0.9), (None, 0.3), (0.2, None), (None, None)]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, values, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    want = [0.5, 0.9, None, None, None]
+    assert res[0] == want and res[1] == want
+
+
+def test_max_over_ranks_single_process():
+    import bench
+
+    assert bench.max_over_ranks(0.3) == 0.3
+    assert bench.max_over_ranks(None) is None
+
+
+@pytest.mark.parametrize("rank", ["1", "3"])
+def test_reference_arm_other_ranks_exit_without_work(rank):
+    env = dict(os.environ, RANK=rank, WORLD_SIZE="4", LOCAL_RANK=rank)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "4"],
+                       env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
+
+
+def test_reference_arm_line_contract(monkeypatch, capsys):
+    """Rank 0 prints one JSON line with the contract's keys (the oracle timing itself is replaced by a
+    stub here: it takes tens of seconds of CPU work)."""
+    import bench
+
+    calls = []
+
+    def fake(cfg, data, alpha, M, iters, budget_s=20.0, x0="fbp"):
+        calls.append(iters)
+        return {"value": 1.5, "unit": "s", "cores": 1, "kind": "oracle", "sample": "stub"}
+
+    monkeypatch.setattr(bench, "cpu_oracle_time_to_tol", fake)
+    monkeypatch.setattr(bench, "make_problem", lambda args, rank: (type("C", (), {"name": "fan2d_512"})(), 1.999,
+                                                                     20, 30, None))
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3"])
+    args = bench.parse()
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] == 1.5 and line["unit"] == "s"
+    assert line["higher_is_better"] is False and line["steps"] == 2 and line["warmup"] == 3
+    assert line["e2e"] == {"value": 1.5, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert calls == [bench.REFERENCE_ITERS_TO_TOL[("fan2d_512", 20, 1.999, "fbp")]] * 5
