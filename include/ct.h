@@ -296,8 +296,9 @@ ct_status ct_relaxed_oslalm_solve(const ct_geom *g, const float *y, const float 
  * sets (stop_rmsd_hu is ignored: every slice runs n_iter iterations);
  * reports: optional host array of nslices reports, whose per-iteration times
  * come from the device clock at each slice's iteration ends.  Allocates one
- * device arena for the batch per call.  1 <= nslices <= 1024.  Synchronises
- * the stream.  Errors: CT_EINVAL, CT_ENOTSUP, CT_ENOMEM, CT_ECUDA,
+ * device arena per call for the batched slices; a large slice's solve
+ * allocates its geometry's solver workspace as ct_relaxed_oslalm_solve
+ * does.  1 <= nslices <= 1024.  Synchronises the stream.  Errors: CT_EINVAL, CT_ENOTSUP, CT_ENOMEM, CT_ECUDA,
  * CT_ETIMEOUT (a bounded grid-barrier wait gave up; the results are then
  * undefined). */
 ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms, const float *const *y, const float *const *w,
