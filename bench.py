@@ -922,19 +922,29 @@ def kkt_rms_hu(ct, G, g, y, w, x, beta, delta, potential, hu):
     return float(torch.sqrt((res[mask].double() ** 2).mean()) * hu)
 
 
-def _source_digest():
+def _code_only(src):
+    """C++ source without its comments and with whitespace runs collapsed (a comment edit keeps the digest)."""
+    import re
+
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
+def _source_digest(csrc=None):
     """Digest of the code of the profiled projector kernels: the kernel part of projectors.cu and the
-    device-arithmetic section of ct_internal.cuh (the footprint, CDF and traversal functions they inline)."""
+    device-arithmetic section of ct_internal.cuh (the footprint, CDF and traversal functions they inline),
+    comments left out."""
     import hashlib
 
-    csrc = os.path.join(ROOT, "paper_1512_04564_gb300", "csrc")
+    csrc = csrc or os.path.join(ROOT, "paper_1512_04564_gb300", "csrc")
     h = hashlib.sha256()
     src = open(os.path.join(csrc, "projectors.cu")).read()
-    h.update(src[:src.index("cudaError_t launch_fp(")].encode())  # the kernels, not the launchers
+    h.update(_code_only(src[:src.index("cudaError_t launch_fp(")]).encode())  # the kernels, not the launchers
     hdr = open(os.path.join(csrc, "ct_internal.cuh")).read()
     a = hdr.index("// ---------------------------------------------------------------- device arithmetic")
     b = hdr.index("// ---------------------------------------------------------------- launchers")
-    h.update(hdr[a:b].encode())
+    h.update(_code_only(hdr[a:b]).encode())
     return h.hexdigest()[:16]
 
 

@@ -336,10 +336,6 @@ __device__ __forceinline__ void bp_epilogue(const FanDev &G, const SolveDev &S, 
     }
 }
 
-// One CTA per 16x16 tile, 128 threads, two pixels per thread (rows ly and
-// ly + 8 of the tile).  With the resident matrix each (view, pixel) is one
-// stored record of cell weights, and the next view's records are loaded
-// while the current view's are used.
 // Resident-matrix back-projection, one CTA per half tile (16 x 8 pixels, the first or last 128
 // records of a tile's block), one pixel per thread: twice the CTAs and warps of the two-pixel
 // kernel, which with 1024 tiles at 512 x 512 left the SMs 60% empty.  The next view's record is
@@ -400,6 +396,10 @@ __global__ void __launch_bounds__(kBpThreads, 16) bp_records_kernel(FanDev G, co
     }
 }
 
+// One CTA per 16x16 tile, 128 threads, two pixels per thread (rows ly and
+// ly + 8 of the tile).  STORED: each (view, pixel) is one stored record of
+// cell weights, the next view's records loaded while the current view's are
+// used; else the footprints are evaluated on the fly.
 template <int MODE, bool STORED>
 __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const float *__restrict__ sino,
                                                               const int *__restrict__ views, int nviews,
