@@ -932,15 +932,17 @@ def _code_only(src):
 
 
 def _source_digest(csrc=None):
-    """Digest of the code of the profiled projector kernels: the kernel part of projectors.cu and the
-    device-arithmetic section of ct_internal.cuh (the footprint, CDF and traversal functions they inline),
+    """Digest of the code of the profiled projector kernels: fp_csr_kernel through bp_records_kernel in
+    projectors.cu and the device-arithmetic section of ct_internal.cuh (the functions they inline),
     comments left out."""
     import hashlib
 
     csrc = csrc or os.path.join(ROOT, "paper_1512_04564_gb300", "csrc")
     h = hashlib.sha256()
     src = open(os.path.join(csrc, "projectors.cu")).read()
-    h.update(_code_only(src[:src.index("cudaError_t launch_fp(")]).encode())  # the kernels, not the launchers
+    a = src.rfind("template", 0, src.index("fp_csr_kernel(FanDev G"))
+    b = src.rfind("template", 0, src.index("bp_fan2d_kernel(FanDev G"))
+    h.update(_code_only(src[a:b]).encode())  # fp_csr_kernel .. bp_records_kernel (with bp_epilogue)
     hdr = open(os.path.join(csrc, "ct_internal.cuh")).read()
     a = hdr.index("// ---------------------------------------------------------------- device arithmetic")
     b = hdr.index("// ---------------------------------------------------------------- launchers")

@@ -396,11 +396,9 @@ __global__ void __launch_bounds__(kBpThreads, 16) bp_records_kernel(FanDev G, co
     }
 }
 
-// One CTA per 16x16 tile, 128 threads, two pixels per thread (rows ly and
-// ly + 8 of the tile).  STORED: each (view, pixel) is one stored record of
-// cell weights, the next view's records loaded while the current view's are
-// used; else the footprints are evaluated on the fly.
-template <int MODE, bool STORED>
+// Back-projection with the footprints evaluated on the fly: one CTA per 16x16 tile, 128 threads, two
+// pixels per thread (rows ly and ly + 8 of the tile).
+template <int MODE>
 __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const float *__restrict__ sino,
                                                               const int *__restrict__ views, int nviews,
                                                               float *__restrict__ xo, float scale, int accumulate,
@@ -408,53 +406,20 @@ __global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const
 {
     const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
     const int ix = blockIdx.x * kTile + lx, iy0 = blockIdx.y * kTile + ly, iy1 = iy0 + kTile / 2;
-    const int tile = blockIdx.y * G.ntx + blockIdx.x;
-    const int ntiles = G.ntx * G.nty;
     // footprints are evaluated for in-image pixels only (a partial tile's outside pixels take the
     // edge pixel's, and their results are not stored); rows ly and ly + 8 lie in two anchor tiles
     const int ixc = min(ix, G.nx - 1), iy0c = min(iy0, G.ny - 1), iy1c = min(iy1, G.ny - 1);
     float rho = 1.0f;
     if (MODE == BP_SOLVE_UPDATE) rho = __ldcg(&S.rho_tab[__ldcg(&S.counter[0])]);
     float acc0 = 0.0f, acc1 = 0.0f;
-    if (STORED) {
-        const size_t vstride = (size_t)ntiles * (kTile * kTile);
-        const size_t base = (size_t)tile * (kTile * kTile) + threadIdx.x;
-        float4 tn0 = make_float4(0.f, 0.f, 0.f, 0.f), tn1 = tn0;
-        float2 an0 = make_float2(0.f, 0.f), an1 = an0;
-        if (nviews > 0) {
-            const size_t i = (size_t)__ldg(&views[0]) * vstride + base;
-            tn0 = __ldcs(&G.foot_t[i]); an0 = __ldcs(&G.foot_an[i]);
-            tn1 = __ldcs(&G.foot_t[i + kBpThreads]); an1 = __ldcs(&G.foot_an[i + kBpThreads]);
-        }
-        for (int k = 0; k < nviews; k++) {
-            const float4 w0 = tn0, w1 = tn1;
-            const float2 b0 = an0, b1 = an1;
-            if (k + 1 < nviews) {
-                const size_t i = (size_t)__ldg(&views[k + 1]) * vstride + base;
-                tn0 = __ldcs(&G.foot_t[i]); an0 = __ldcs(&G.foot_an[i]);
-                tn1 = __ldcs(&G.foot_t[i + kBpThreads]); an1 = __ldcs(&G.foot_an[i + kBpThreads]);
-            }
-            const float *row = sino + (size_t)k * G.ns;
-            const bool wide0 = __float_as_int(b0.y) == kWideRecord, wide1 = __float_as_int(b1.y) == kWideRecord;
-            if (wide0 || wide1) {  // rare: a footprint wider than a record, evaluated on the fly
-                const int v = __ldg(&views[k]);
-                const float2 cs = __ldg(&G.view_cs[v]);
-                if (wide0) acc0 += footprint_dot(pixel_footprint(G, v, cs.x, cs.y, ixc, iy0c), row, G.ns);
-                if (wide1) acc1 += footprint_dot(pixel_footprint(G, v, cs.x, cs.y, ixc, iy1c), row, G.ns);
-            }
-            if (!wide0) acc0 += record_dot(w0, b0, row, G.ns);
-            if (!wide1) acc1 += record_dot(w1, b1, row, G.ns);
-        }
-    } else {
-        for (int k = 0; k < nviews; k++) {
-            const int v = __ldg(&views[k]);
-            const float2 cs = __ldg(&G.view_cs[v]);
-            const Footprint F0 = pixel_footprint(G, v, cs.x, cs.y, ixc, iy0c);
-            const Footprint F1 = pixel_footprint(G, v, cs.x, cs.y, ixc, iy1c);
-            const float *row = sino + (size_t)k * G.ns;
-            acc0 += footprint_dot(F0, row, G.ns);
-            acc1 += footprint_dot(F1, row, G.ns);
-        }
+    for (int k = 0; k < nviews; k++) {
+        const int v = __ldg(&views[k]);
+        const float2 cs = __ldg(&G.view_cs[v]);
+        const Footprint F0 = pixel_footprint(G, v, cs.x, cs.y, ixc, iy0c);
+        const Footprint F1 = pixel_footprint(G, v, cs.x, cs.y, ixc, iy1c);
+        const float *row = sino + (size_t)k * G.ns;
+        acc0 += footprint_dot(F0, row, G.ns);
+        acc1 += footprint_dot(F1, row, G.ns);
     }
     bp_epilogue<MODE>(G, S, xo, ix, iy0, acc0, rho, scale, accumulate);
     bp_epilogue<MODE>(G, S, xo, ix, iy1, acc1, rho, scale, accumulate);
@@ -561,9 +526,9 @@ cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *v
         return cudaGetLastError();
     }
     switch (mode) {
-    case BP_PLAIN: bp_fan2d_kernel<BP_PLAIN, false><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
-    case BP_SOLVE_INIT: bp_fan2d_kernel<BP_SOLVE_INIT, false><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
-    default: bp_fan2d_kernel<BP_SOLVE_UPDATE, false><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+    case BP_PLAIN: bp_fan2d_kernel<BP_PLAIN><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+    case BP_SOLVE_INIT: bp_fan2d_kernel<BP_SOLVE_INIT><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+    default: bp_fan2d_kernel<BP_SOLVE_UPDATE><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
     }
     return cudaGetLastError();
 }
