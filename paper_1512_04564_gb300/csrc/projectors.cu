@@ -280,8 +280,10 @@ __global__ void __launch_bounds__(kFpThreads) fp_ray_kernel(FanDev G, const floa
 }
 
 // Resident-matrix forward projection: one warp per ray streams the ray's
-// entries (a_ij and the 16-bit pixel-index steps, eight loads in flight per
-// lane), gathers x from L1/L2 and reduces by shuffles.  The 8 warps of a CTA take 8 adjacent cells of one view,
+// entry pairs (two a_ij and two 16-bit pixel-index offsets each, two pairs in
+// flight per lane), gathers from the packed image [x | x^T] (x itself for a
+// shallow ray, the transposed copy for a steep one) through L1/L2 and reduces
+// by shuffles.  The 8 warps of a CTA take 8 adjacent cells of one view,
 // whose wedges cover nearly the same pixels.  CTAs run the cell blocks in the
 // geometry's ray_order (most entries first, every view of the list for each
 // block), so that the end of the launch is made of short rays.
