@@ -144,7 +144,9 @@ ct_status ct_geom_autotune(ct_geom *g, int views_per_launch, int *fp_choice, int
  * ray-driven).  x: device [ny][nx]; y: device [nviews][ns], row k is view
  * views[k].  views: host array of nviews indices in [0, na), or NULL for all
  * na views in order (then nviews must be na).  1 <= nviews <= na.  Output
- * rows are overwritten.  Errors: CT_EINVAL, CT_ECUDA. */
+ * rows are overwritten.  With the resident matrix (ct_geom_precompute) x is
+ * first packed as [x | x^T] into a scratch image g owns (one extra small
+ * launch; see ct_pack_image).  Errors: CT_EINVAL, CT_ECUDA. */
 ct_status ct_forward(const ct_geom *g, const float *x, float *y, const int *views, int nviews, void *stream);
 
 /* The packed image [x | x^T] of a 2-D geometry: xpack[j] = x[j] and
