@@ -923,12 +923,12 @@ def kkt_rms_hu(ct, G, g, y, w, x, beta, delta, potential, hu):
 
 
 def _code_only(src):
-    """C++ source without its comments and with whitespace runs collapsed (a comment edit keeps the digest)."""
+    """C++ source without its comments and whitespace (a comment or layout edit keeps the digest)."""
     import re
 
     src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
     src = re.sub(r"//[^\n]*", " ", src)
-    return " ".join(src.split())
+    return "".join(src.split())
 
 
 def _source_digest(csrc=None):

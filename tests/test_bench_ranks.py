@@ -93,3 +93,23 @@ def test_reference_arm_line_contract(monkeypatch, capsys):
     assert line["e2e"] == {"value": 1.5, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert calls == [bench.REFERENCE_ITERS_TO_TOL[("fan2d_512", 20, 1.999, "fbp")]] * 5
+
+
+def test_kernel_digest_ignores_comments_only(tmp_path):
+    """The DRAM-traffic record is reported only while the profiled kernels' code is unchanged: a comment
+    edit keeps the digest, a code edit in the forward or back projector changes it."""
+    import shutil
+
+    import bench
+
+    src = os.path.join(ROOT, "paper_1512_04564_gb300", "csrc")
+    for f in ("projectors.cu", "ct_internal.cuh"):
+        shutil.copy(os.path.join(src, f), tmp_path / f)
+    d0 = bench._source_digest(str(tmp_path))
+    assert d0 == bench._source_digest()
+    p = tmp_path / "projectors.cu"
+    text = p.read_text()
+    p.write_text(text.replace("fp_csr_kernel(FanDev G", "fp_csr_kernel(FanDev G /* a comment */", 1))
+    assert bench._source_digest(str(tmp_path)) == d0
+    p.write_text(text.replace("const int lane = threadIdx.x & 31;", "const int lane = threadIdx.x % 32;", 1))
+    assert bench._source_digest(str(tmp_path)) != d0
