@@ -111,5 +111,8 @@ def test_kernel_digest_ignores_comments_only(tmp_path):
     text = p.read_text()
     p.write_text(text.replace("fp_csr_kernel(FanDev G", "fp_csr_kernel(FanDev G /* a comment */", 1))
     assert bench._source_digest(str(tmp_path)) == d0
-    p.write_text(text.replace("const int lane = threadIdx.x & 31;", "const int lane = threadIdx.x % 32;", 1))
-    assert bench._source_digest(str(tmp_path)) != d0
+    for old, new in (("8 * __ldg(&G.ray_order[rank])", "8 * __ldg(&G.ray_order[rank + 0])"),  # forward
+                     ("half * kBpThreads + threadIdx.x", "threadIdx.x + half * kBpThreads")):  # back
+        assert text.count(old) == 1
+        p.write_text(text.replace(old, new))
+        assert bench._source_digest(str(tmp_path)) != d0
