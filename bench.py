@@ -58,8 +58,6 @@ def max_over_ranks(value, dist=None, device="cpu"):
 
 METRIC = "time to RMSD<=1 HU vs x* (s)"
 UNIT = "s"
-# outer iterations to RMSD <= 1 HU measured by the GPU arm (config.iters_to_tol), keyed by (workload, M, alpha, x0)
-REFERENCE_ITERS_TO_TOL = {("fan2d_512", 20, 1.999, "fbp"): 6, ("fan2d_512", 20, 1.999, "zeros"): 14}
 
 
 def parse():
@@ -168,58 +166,66 @@ def make_problem(args, rank: int):
     return cfg, alpha, M, n_iter, data
 
 
-def cpu_oracle_time_to_tol(cfg, data, alpha, M, iters_to_tol, budget_s=20.0, x0="fbp"):
-    """Time the FP64 oracle (as it stands) on a bounded sample and scale it to a time-to-tol.
+def oracle_xstar(cfg):
+    """The oracle's own x* of a workload (oracle/xstar.py; stored with its recipe), or None."""
+    from oracle import xstar as oxstar
 
-    Sample: the oracle's D_L (full A'WA1) and as many subiterations of Algorithm 1 as fit in
-    ``budget_s`` seconds; the time per outer iteration is the mean subiteration time x M.
-    """
+    p = oxstar.path_for(cfg.name, cfg.seed)
+    if not os.path.exists(p):
+        return None, None
+    rec = {}
+    try:
+        rec = json.load(open(p[:-4] + ".json"))
+    except (OSError, ValueError):
+        pass
+    return np.load(p).astype(np.float64), rec
+
+
+def oracle_solve_to_tol(cfg, data, alpha, M, xstar, tol_hu, x0="fbp", max_iter=60, stop_after_sub=None):
+    """One whole FP64 oracle solve, timed: FBP start (or zeros), D_L, the initial gradient, then outer
+    iterations of Algorithm 1 until the RMSD to ``xstar`` over the FOV is <= tol_hu (checked after each
+    outer iteration, as the GPU solver does).  stop_after_sub: end after that many subiterations (a
+    bounded warm-up).  Returns the wall times and the iteration count."""
     from oracle import solver as osolver
     from oracle.projector import FanProjector, num_threads
 
     g = cfg.geom
-    prob = osolver.PWLSProblem(FanProjector(g), data.y.astype(np.float32).astype(np.float64),
-                               data.w.astype(np.float32).astype(np.float64), cfg.beta_per_mm, cfg.delta,
-                               cfg.potential)
-    t_fbp = 0.0
-    xinit = np.zeros((g.ny, g.nx))
-    if x0 == "fbp":
-        from oracle.fbp import fbp_fan_arc
-
-        t0 = time.perf_counter()
-        xinit = fbp_fan_arc(g, data.y.astype(np.float32).astype(np.float64), "hann")
-        t_fbp = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    DL = prob.D_L()
-    t_dl = time.perf_counter() - t0
-    subs = []
-    last = [time.perf_counter()]
 
     class Stop(Exception):
         pass
 
-    def cb(t, x):
-        now = time.perf_counter()
-        subs.append(now - last[0])
-        last[0] = now
-        if sum(subs) > budget_s or len(subs) >= M:
+    t_start = time.perf_counter()
+    prob = osolver.PWLSProblem(FanProjector(g), data.y.astype(np.float32).astype(np.float64),
+                               data.w.astype(np.float32).astype(np.float64), cfg.beta_per_mm, cfg.delta,
+                               cfg.potential)
+    xinit = np.zeros((g.ny, g.nx))
+    if x0 == "fbp":
+        from oracle.fbp import fbp_fan_arc
+
+        xinit = fbp_fan_arc(g, prob.y, "hann")
+    t_fbp = time.perf_counter() - t_start
+    DL = prob.D_L()
+    t_dl = time.perf_counter() - t_start - t_fbp
+    mask = osolver.fov_mask(g)
+    out = {"iters_to_tol": None, "rmsd_trace_hu": []}
+
+    def cb(k, x):
+        r = osolver.rmsd_hu(x, xstar, mask, cfg.hu_per_unit)
+        out["rmsd_trace_hu"].append(round(r, 4))
+        if r <= tol_hu:
+            out["iters_to_tol"] = k
+            raise Stop()
+
+    def sub_cb(t, x):
+        if stop_after_sub is not None and t >= stop_after_sub:
             raise Stop()
 
     try:
-        last[0] = time.perf_counter()
-        osolver.relaxed_os_lalm(prob, xinit, M, alpha, 1, D_L=DL, sub_callback=cb)
+        osolver.relaxed_os_lalm(prob, xinit, M, alpha, max_iter, D_L=DL, callback=cb, sub_callback=sub_cb)
     except Stop:
         pass
-    # the first interval also holds the initialisation (one subset gradient)
-    t_sub = statistics.mean(subs[1:]) if len(subs) > 1 else subs[0]
-    t_init = max(subs[0] - t_sub, 0.0)
-    value = t_fbp + t_dl + t_init + iters_to_tol * M * t_sub
-    return {
-        "value": value, "unit": UNIT, "cores": num_threads(), "kind": "oracle",
-        "sample": (f"FP64 oracle on the same workload: FBP ({t_fbp:.2f} s) + D_L ({t_dl:.2f} s) + init ({t_init:.2f} s) + "
-                   f"{len(subs)} of {M} subiterations ({t_sub:.3f} s each) timed, scaled to "
-                   f"{iters_to_tol} outer iterations (the GPU's iteration count to the tolerance)"),
-    }
+    out.update({"seconds": time.perf_counter() - t_start, "fbp_s": t_fbp, "dl_s": t_dl, "cores": num_threads()})
+    return out
 
 
 BATCH_SIZES = (256, 384, 512)
@@ -342,8 +348,8 @@ def _helix_views(job):
 
 def helix_alu_roofline(ct, G, g, M, x, peaks, clock_mhz):
     """Subset forward / back projection of a helical scan: device time (CUDA events on the launching
-    stream) against the FP32 FMA peak.  Algorithmic FLOPs = 2 per nonzero a_ij of the subset's rows,
-    counted exactly on the host for a sample of the subset's views and scaled."""
+    stream) against the FP32 FMA peak.  Algorithmic FLOPs = FLOP_PER_AIJ_3D per nonzero a_ij of the
+    subset's rows, counted exactly on the host for a sample of the subset's views and scaled."""
     import torch
 
     views = list(range(M - 1, g.na, M))
@@ -367,17 +373,15 @@ def helix_alu_roofline(ct, G, g, M, x, peaks, clock_mhz):
     bp_s = timed(lambda: ct.ct_back(G, out, xb, views=views))
     sample = views[:: max(1, nv // 8)]
     nnz = sum(helix_nnz_view(g, v) for v in sample) * nv / len(sample)
-    flops = 2.0 * nnz
-    sm = 152
-    mhz = clock_mhz or 2070.0
-    peak = sm * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 FLOP x clock
+    flops = FLOP_PER_AIJ_3D * nnz
+    peak, peak_src = fp32_peak_tflops(clock_mhz)
     k = {"fp": {"kernel": "fp_helix_kernel", "ms": fp_s * 1e3, "tflops": flops / fp_s / 1e12},
          "bp": {"kernel": "bp_helix_kernel", "ms": bp_s * 1e3, "tflops": flops / bp_s / 1e12}}
     dom = "bp" if bp_s >= fp_s else "fp"
     return {"bound": "alu", "kernel": k[dom]["kernel"] + f" ({nv} views)", "achieved": k[dom]["tflops"],
             "peak": peak, "unit": "TFLOP/s", "frac": k[dom]["tflops"] / peak, "traffic": None,
-            "peak_source": f"152 SMs x 128 FP32 lanes x 2 FLOP x {mhz:.0f} MHz (median SM clock under load)",
-            "nnz_per_launch": nnz, "views_per_launch": nv, "kernels": k}
+            "peak_source": peak_src + " (derived from unit counts and the sampled clock)",
+            "nnz_per_launch": nnz, "flop_per_aij": FLOP_PER_AIJ_3D, "views_per_launch": nv, "kernels": k}
 
 
 def helix_nnz_view(g, v):
@@ -669,29 +673,37 @@ def run_warmstart(args):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores.  Each timed step is one whole
+    oracle solve to RMSD <= tol vs the oracle's own x* (FBP, D_L, initialisation, outer iterations with the
+    RMSD checked after each); warm-up steps run the same solve for one subiteration."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     cfg, alpha, M, n_iter, data = make_problem(args, 0)
-    # The oracle follows the GPU solver's iterates (parity <= 0.1 HU), so it needs the same number of
-    # outer iterations to reach 1 HU: REFERENCE_ITERS_TO_TOL, measured by this script's GPU arm
-    # (config.iters_to_tol) on the seed-0 workload.
-    iters = int(os.environ.get("CT_REFERENCE_ITERS", REFERENCE_ITERS_TO_TOL.get((cfg.name, M, alpha, args.x0), n_iter)))
-    per_step = []
-    cb = None
-    for _ in range(args.warmup + args.steps):
-        cb = cpu_oracle_time_to_tol(cfg, data, alpha, M, iters, budget_s=max(5.0, 60.0 / (args.warmup + args.steps)),
-                                    x0=args.x0)
-        per_step.append(cb["value"])
-    vals = per_step[args.warmup:]
-    v = statistics.mean(vals)
-    cb["value"] = v
+    xstar, rec = oracle_xstar(cfg) if args.views is None else (None, None)
+    if xstar is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle x* stored for workload {cfg.name} "
+                          "(oracle/xstar.py writes one)"}), flush=True)
+        return 0
+    for _ in range(args.warmup):
+        oracle_solve_to_tol(cfg, data, alpha, M, xstar, args.tol_hu, x0=args.x0, stop_after_sub=1)
+    runs = [oracle_solve_to_tol(cfg, data, alpha, M, xstar, args.tol_hu, x0=args.x0, max_iter=n_iter)
+            for _ in range(args.steps)]
+    reached = all(r["iters_to_tol"] is not None for r in runs)
+    step_s = [r["seconds"] for r in runs]
+    v = statistics.mean(step_s) if reached else None
+    last = runs[-1]
+    sample = (f"{args.steps} whole FP64 oracle solves (one per step): FBP {last['fbp_s']:.2f} s, D_L {last['dl_s']:.2f} s, "
+              f"then {last['iters_to_tol']} outer iterations of M = {M} to RMSD <= {args.tol_hu} HU of the "
+              f"oracle's x* ({rec.get('recipe', '?')}; KKT RMS {rec.get('kkt_rms_hu', float('nan')):.2e} HU)")
+    cb = {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle", "sample": sample}
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_s) * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": cfg.name, "alpha": alpha, "M": M, "n_iter": n_iter, "x0": args.x0,
-                   "iters_assumed": iters},
+                   "iters_to_tol": [r["iters_to_tol"] for r in runs], "rmsd_trace_hu": last["rmsd_trace_hu"],
+                   "warmup": "one subiteration of the same solve per warm-up step"},
         "cpu_baseline": cb,
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -818,7 +830,7 @@ def main():
            "h2d_bytes_per_step": 2 * y_h.numel() * 4,
            "d2h_bytes_per_step": x_h.numel() * 4}
 
-    roof = kernel_roofline(ct, G, g, M, y, w, xstar, matrix_bytes)
+    roof = kernel_roofline(ct, G, g, M, y, w, xstar, matrix_bytes, clock_info.get("sm_mhz"))
     # setup: D_L weights and back-projection, initial FP (+ packing [x | x^T] for the resident rows) and BP,
     # the FBP's filter and back-projection; then 3 launches per subiteration and the RMSD per iteration
     launches = 4 + (1 if matrix_bytes else 0) + (2 if fbp0 else 0) + n_iter * (3 * M + 1)
@@ -853,7 +865,20 @@ def main():
         "source_digest": _source_digest(),
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_oracle_time_to_tol(cfg, data, alpha, M, iters_to_tol or n_iter, x0=args.x0)
+        xs_o, rec = oracle_xstar(cfg) if args.views is None else (None, None)
+        if xs_o is not None:
+            # the oracle's own solve, once, to the same tolerance of its own x*
+            r = oracle_solve_to_tol(cfg, data, alpha, M, xs_o, args.tol_hu, x0=args.x0, max_iter=n_iter)
+            line["cpu_baseline"] = {
+                "value": r["seconds"] if r["iters_to_tol"] else None, "unit": UNIT, "cores": r["cores"],
+                "kind": "oracle",
+                "sample": (f"one whole FP64 oracle solve: FBP {r['fbp_s']:.2f} s, D_L {r['dl_s']:.2f} s, then "
+                           f"{r['iters_to_tol']} outer iterations of M = {M} to RMSD <= {args.tol_hu} HU of the "
+                           f"oracle's x* ({rec.get('recipe', '?')})"),
+                "rmsd_trace_hu": r["rmsd_trace_hu"]}
+            # the two x* (GPU: M = 1 iterations; oracle: its stored recipe) of the same problem
+            line["config"]["xstar_gpu_vs_oracle_rmsd_hu"] = float(
+                np.sqrt(np.mean(((xstar.cpu().numpy() - xs_o)[fov_mask_np(g)]) ** 2)) * hu)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -897,6 +922,13 @@ def run_study(args, ct, G, g, y, w, xstar, common, hu, kkt, cfg):
             "majorizers": majorizers}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def fov_mask_np(g):
+    """Pixel centres inside the field-of-view disk (the RMSD region)."""
+    xc = (np.arange(g.nx) - (g.nx - 1) / 2.0 + g.offset_x) * g.dx
+    yc = (np.arange(g.ny) - (g.ny - 1) / 2.0 + g.offset_y) * g.dy
+    return (xc[None, :] ** 2 + yc[:, None] ** 2) <= g.fov_radius() ** 2
 
 
 def kkt_rms_hu(ct, G, g, y, w, x, beta, delta, potential, hu):
@@ -950,9 +982,49 @@ def _source_digest(csrc=None):
     return h.hexdigest()[:16]
 
 
-def kernel_roofline(ct, G, g, M, y, w, x, matrix_bytes):
+# Algorithmic FP32 work of the projector pair, per nonzero a_ij: a footprint evaluation per (pixel, view)
+# (four corner fan angles, their sort, the amplitude) spread over the ~3.3 cells it covers, plus each
+# cell's trapezoid integral and multiply-add: about 15 operations in 2-D (1.3e10 for the 8.5e8 a_ij of
+# the 512x512, 984-view scan), about 8.3 in 3-D (the transaxial footprint is shared by a column's
+# voxels: 1e12 for the 1.2e11 a_ij of the 512x512x64 helical scan).
+FLOP_PER_AIJ_2D = 1.3e10 / 8.5e8
+FLOP_PER_AIJ_3D = 1.0e12 / 1.2e11
+
+
+def fp32_peak_tflops(clock_mhz):
+    """FP32 FMA peak: SMs (from the device) x 128 lanes x 2 FLOP x the SM clock (median under load)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = clock_mhz or 2070.0
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, f"{sms} SMs x 128 FP32 lanes x 2 FLOP x {mhz:.0f} MHz"
+
+
+def fan_cells_view(g, v):
+    """Nonzero a_ij of view v of the 2-D fan-beam SF matrix: for every pixel, the detector cells its
+    footprint [t0, t3] (corner fan angles) overlaps, clipped to the detector."""
+    b = g.betas()[v]
+    cb, sb = math.cos(b), math.sin(b)
+    xc = (np.arange(g.nx) - (g.nx - 1) / 2.0 + g.offset_x) * g.dx
+    yc = (np.arange(g.ny) - (g.ny - 1) / 2.0 + g.offset_y) * g.dy
+    X, Y = np.meshgrid(xc, yc)
+    taus = []
+    for sx in (-0.5, 0.5):
+        for sy in (-0.5, 0.5):
+            px, py = X + sx * g.dx + g.dso * cb, Y + sy * g.dy + g.dso * sb
+            taus.append(np.arctan2(-px * sb + py * cb, px * cb + py * sb) * g.dsd / g.ds + (g.ns - 1) / 2.0 - g.offset_s)
+    t0, t3 = np.minimum.reduce(taus), np.maximum.reduce(taus)
+    s_lo = np.maximum(np.floor(t0 - 0.5) + 1, 0)
+    s_hi = np.minimum(np.ceil(t3 + 0.5) - 1, g.ns - 1)
+    return float(np.maximum(s_hi - s_lo + 1, 0).sum())
+
+
+def kernel_roofline(ct, G, g, M, y, w, x, matrix_bytes, clock_mhz=None):
     """Average device time of one subset forward and back projection (CUDA events on the launching
-    stream) and their algorithmic HBM bytes; the slower of the two is reported as the dominant kernel."""
+    stream).  The bound of the projectors is the FP32 ALUs: achieved = FLOP_PER_AIJ_2D x the launch's
+    nonzero a_ij (counted on the host) / time, against the FP32 FMA peak at the sampled clock.  Beside it,
+    the HBM fraction of the compulsory bytes (image, residual rows) and, with the resident matrix, of the
+    stored bytes the kernels stream; the slower kernel is reported as the dominant one."""
     import torch
 
     views = list(range(M - 1, g.na, M))
@@ -985,26 +1057,33 @@ def kernel_roofline(ct, G, g, M, y, w, x, matrix_bytes):
     except OSError:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"
     npix = g.nx * g.ny
     ntile_px = ((g.nx + 15) // 16) * ((g.ny + 15) // 16) * 256
+    nnz = sum(fan_cells_view(g, v) for v in views)
+    flops = FLOP_PER_AIJ_2D * nnz
+    peak, peak_src = fp32_peak_tflops(clock_mhz)
+    # compulsory bytes: FP reads the image once and writes the subset's rays; BP reads the rays, writes the image
+    fp_min = 4 * npix + 4 * nv * g.ns
+    bp_min = 4 * nv * g.ns + 4 * npix
+    stored = {}
     if matrix_bytes:
         R = g.na * g.ns
         # the rows' entries (6 B each: a_ij + 16-bit offset) and chunk bases (4 B per 32 entries)
         entry_bytes = matrix_bytes - 8 * (R + 1) - 4 * (R + 2) - 24 * g.na * ntile_px
-        # FP: the subset's (pixel, a_ij) rows + row pointers, x once, y written
-        # the subset's share of the entries, 12 B per ray (row and chunk pointers), image, output
-        fp_bytes = entry_bytes * nv / g.na + 12 * nv * g.ns + 4 * npix + 4 * nv * g.ns
-        # BP: one stored footprint (24 B) per (view, pixel slot), the residual rows, x written
-        bp_bytes = 24 * ntile_px * nv + 4 * nv * g.ns + 4 * npix
-    else:
-        fp_bytes = 4 * npix + 4 * nv * g.ns
-        bp_bytes = 4 * nv * g.ns + 4 * npix
-    kernels = {
-        "fp": {"kernel": "fp_csr_kernel" if matrix_bytes else "fp_bundle_kernel", "ms": fp_s * 1e3,
-               "algorithmic_bytes": fp_bytes, "gbs": fp_bytes / fp_s / 1e9},
-        "bp": {"kernel": "bp_records_kernel" if matrix_bytes else "bp_fan2d_kernel<on the fly>",
-               "ms": bp_s * 1e3, "algorithmic_bytes": bp_bytes, "gbs": bp_bytes / bp_s / 1e9},
-    }
+        # FP: the subset's share of the entries, 12 B per ray (row and chunk pointers), image, output
+        stored["fp"] = entry_bytes * nv / g.na + 12 * nv * g.ns + 4 * npix + 4 * nv * g.ns
+        # BP: one stored record (24 B) per (view, pixel slot), the residual rows, x written
+        stored["bp"] = 24 * ntile_px * nv + 4 * nv * g.ns + 4 * npix
+    kernels = {}
+    for key, t, name, cmin in (("fp", fp_s, "fp_csr_kernel" if matrix_bytes else "fp_bundle_kernel", fp_min),
+                               ("bp", bp_s, "bp_records_kernel" if matrix_bytes else "bp_fan2d_kernel", bp_min)):
+        k = {"kernel": name, "ms": t * 1e3, "tflops": flops / t / 1e12, "alu_frac": flops / t / 1e12 / peak,
+             "compulsory_bytes": cmin, "compulsory_gbs": cmin / t / 1e9, "compulsory_frac": cmin / t / 1e9 / hbm_peak}
+        if key in stored:
+            k.update({"stored_bytes": stored[key], "stored_gbs": stored[key] / t / 1e9,
+                      "stored_frac": stored[key] / t / 1e9 / hbm_peak})
+        kernels[key] = k
     dom = "bp" if bp_s >= fp_s else "fp"
     traffic = None
     try:
@@ -1015,9 +1094,14 @@ def kernel_roofline(ct, G, g, M, y, w, x, matrix_bytes):
         pass
     k = kernels[dom]
     return {
-        "bound": "hbm", "kernel": k["kernel"] + f" ({nv} views)", "achieved": k["gbs"], "peak": hbm_peak,
-        "unit": "GB/s", "frac": k["gbs"] / hbm_peak, "traffic": traffic,
-        "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s",
+        "bound": "alu", "kernel": k["kernel"] + f" ({nv} views)", "achieved": k["tflops"], "peak": peak,
+        "unit": "TFLOP/s", "frac": k["tflops"] / peak, "traffic": traffic,
+        "peak_source": peak_src + " (derived from unit counts and the sampled clock)",
+        "flop_per_launch": flops, "nnz_per_launch": nnz, "flop_per_aij": FLOP_PER_AIJ_2D,
+        "hbm_compulsory": {"bytes": k["compulsory_bytes"], "achieved": k["compulsory_gbs"], "peak": hbm_peak,
+                           "unit": "GB/s", "frac": k["compulsory_frac"], "peak_source": hbm_src},
+        "hbm_stored": ({"bytes": k["stored_bytes"], "achieved": k["stored_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                        "frac": k["stored_frac"], "peak_source": hbm_src} if "stored_bytes" in k else None),
         "views_per_launch": nv, "kernels": kernels,
     }
 

@@ -178,8 +178,8 @@ ct_status ct_back(const ct_geom *g, const float *y, float *x, const int *views, 
  * CT_ECUDA. */
 ct_status ct_sqs_diag(const ct_geom *g, const float *w, float *d_l, void *stream);
 
-/* Same result as ct_sqs_diag, without using or allocating any device memory
- * beyond its arguments: for callers that cannot allocate once running (a
+/* Same result as ct_sqs_diag, without allocating any device memory (nor
+ * using the geometry's workspace): for callers that cannot allocate once running (a
  * process whose device memory is reserved up front by its own pool, or a
  * latency-critical loop that must not enter cudaMalloc/cudaFree, which can
  * block and synchronise the device).  The paper has no counterpart; it is an
@@ -187,8 +187,13 @@ ct_status ct_sqs_diag(const ct_geom *g, const float *w, float *d_l, void *stream
  * device array inside the library (held by every GPU that loads it until the
  * process exits), so na * ns must be <= 1,048,576 (CT_EINVAL otherwise).  The
  * first call on a device looks up that array's address with the device
- * current; make it before any stream capture.  All calls share the array:
- * calls that overlap on the GPU race.  The geometry's device must be
+ * current; make it before any stream capture.  Under CUDA's lazy module
+ * loading that first call also loads the array onto the device, so it needs
+ * 4 MiB of device memory outside any pool the caller reserved.  The address
+ * is cached for the life of the device's primary context (a cudaDeviceReset
+ * invalidates it).  Uses the geometry's kept ray sums A 1 when it has them,
+ * else one forward projection of w over all views.  All calls share the
+ * array: calls that overlap on the GPU race.  The geometry's device must be
  * current.  Errors: CT_EINVAL, CT_ECUDA. */
 ct_status ct_sqs_diag_noalloc(const ct_geom *g, const float *w, float *d_l, void *stream);
 
@@ -306,6 +311,18 @@ ct_status ct_relaxed_oslalm_solve(const ct_geom *g, const float *y, const float 
 ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms, const float *const *y, const float *const *w,
                                           const ct_solve_params *params, float *const *x_inout, int nslices,
                                           ct_solve_report *reports, void *stream);
+
+/* Failure-detection hook of the batched solve's persistent launch (no
+ * counterpart in the paper; the batched solver's grid barrier is this
+ * library's).  Every grid-barrier wait of later batched launches polls at
+ * most max_polls times (about 100 ns apart; 0 restores the built-in limit
+ * of 2^24 polls), and with missing > 0 the barrier waits for that many
+ * participants beyond the grid, which never arrive: every wait then runs out,
+ * each CTA records the failure and returns, and the call returns CT_ETIMEOUT
+ * with the GPU context intact.  Process-wide; set it only while no batched
+ * solve runs.  (0, 0) is normal operation.  Errors: CT_EINVAL (max_polls < 0,
+ * missing outside [0, 1024]). */
+ct_status ct_debug_barrier(long long max_polls, int missing);
 
 /* Message describing the last failure on this thread ("" if none). */
 const char *ct_last_error(void);

@@ -16,6 +16,7 @@
 // gives up, the kernel records an error status and every CTA returns.
 // Setup (D_L, initial gradient, optional FBP) uses the single-slice kernels.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <vector>
 
@@ -27,6 +28,11 @@ namespace {
 constexpr int kMaxSlices = 1024;
 constexpr int kThreads = 256;
 constexpr long long kMaxSpins = 1ll << 24;  // x ~100 ns sleep: ~2 s per barrier at most
+
+// Failure-detection hook (ct_debug_barrier): the poll limit of every barrier wait, and a number of
+// participants the barrier waits for beyond the grid, which never arrive (0 in normal use).
+std::atomic<long long> g_barrier_polls{kMaxSpins};
+std::atomic<int> g_barrier_missing{0};
 
 struct BatchSlice {
     FanDev G;
@@ -47,8 +53,9 @@ struct BatchCtl {
     unsigned int count;
     unsigned int gen;
     int error;
-    int pad;
+    int missing;             // participants beyond the grid that the barrier waits for (failure tests)
     unsigned long long t_start;
+    long long max_polls;     // poll limit of one barrier wait
 };
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -70,8 +77,9 @@ __device__ bool grid_barrier(BatchCtl *ctl)
         const unsigned int g0 = *vgen;
         __threadfence();
         const unsigned int arrived = atomicAdd(&ctl->count, 1u) + 1u;
+        const long long max_polls = ctl->max_polls;
         int ok = 1;
-        if (arrived == gridDim.x) {
+        if (arrived == gridDim.x + (unsigned int)ctl->missing) {
             atomicExch(&ctl->count, 0u);
             __threadfence();
             atomicAdd(&ctl->gen, 1u);
@@ -79,7 +87,7 @@ __device__ bool grid_barrier(BatchCtl *ctl)
             long long spins = 0;
             while (*vgen == g0) {
                 if (*verr) { ok = 0; break; }
-                if (++spins > kMaxSpins) {
+                if (++spins > max_polls) {
                     atomicExch(&ctl->error, 1);
                     ok = 0;
                     break;
@@ -487,6 +495,10 @@ ct_status persistent_batch(const ct_geom *const *geoms, const float *const *y, c
     BatchSlice *dsl = (BatchSlice *)(arena + desc_off);
     BatchCtl *ctl = (BatchCtl *)(arena + desc_off + al256(sizeof(BatchSlice) * nslices));
     CT_CUDA_TRY(cudaMemcpyAsync(dsl, hs.data(), sizeof(BatchSlice) * nslices, cudaMemcpyHostToDevice, ws), "upload");
+    BatchCtl hc0{};
+    hc0.max_polls = g_barrier_polls.load();
+    hc0.missing = g_barrier_missing.load();
+    CT_CUDA_TRY(cudaMemcpyAsync(ctl, &hc0, sizeof(hc0), cudaMemcpyHostToDevice, ws), "upload");
 
     // persistent grid: every CTA co-resident (cooperative launch)
     int nsm = 0, per_sm = 0;
@@ -602,6 +614,17 @@ void fill_solo_report(ct_solve_report *r, const ct_solve_params *p, const ct_sol
 }
 
 }  // namespace
+
+extern "C" ct_status ct_debug_barrier(long long max_polls, int missing)
+{
+    if (max_polls < 0 || missing < 0 || missing > 1024) {
+        set_error("ct_debug_barrier: need max_polls >= 0 and 0 <= missing <= 1024");
+        return CT_EINVAL;
+    }
+    g_barrier_polls.store(max_polls > 0 ? max_polls : kMaxSpins);
+    g_barrier_missing.store(missing);
+    return CT_OK;
+}
 
 extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms, const float *const *y,
                                                      const float *const *w, const ct_solve_params *params,

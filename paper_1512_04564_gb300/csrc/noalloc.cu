@@ -6,17 +6,24 @@
 // latency-critical reconstruction loop that must not enter cudaMalloc /
 // cudaFree, which can block and synchronise the whole device.  For them,
 // ct_sqs_diag_noalloc computes D_L = A'(w (A 1)) with its intermediate
-// sinogram w (A 1) in a file-scope device array that the library's module
-// carries (every GPU that loads the library holds it until the process
-// exits), instead of in the geometry's workspace.  It calls no cudaMalloc,
-// cudaFree or allocating library routine.
+// sinogram w (A 1) in a file-scope device array of this compile unit's
+// module, instead of in the geometry's workspace.  It calls no cudaMalloc,
+// cudaFree or allocating library routine.  When the geometry already keeps
+// its ray sums A 1 (from an earlier ct_sqs_diag or ct_geom_precompute), the
+// weights are one elementwise product; otherwise one forward projection of
+// the weights over all views writes them.
 //
 // The array's device address is looked up once per device, with that device
 // current, by the first call made on that device; make that first call
-// before any stream capture.  All calls share the array: calls that overlap
-// on the GPU (different streams, or host threads racing on one device) race
-// on it.  Every element the back-projection reads is written by the forward
-// pass of the same call, so nothing needs clearing between calls.
+// before any stream capture.  Under CUDA's lazy module loading that lookup
+// is also what loads the module on the device, so the first call on each
+// device needs 4 MiB of device memory outside any pool the caller reserved;
+// from then on the device holds the array until the process exits.  The
+// cached address is valid for the life of the device's primary context (a
+// cudaDeviceReset invalidates it).  All calls share the array: calls that
+// overlap on the GPU (different streams, or host threads racing on one
+// device) race on it.  Every element the back-projection reads is written
+// by the same call, so nothing needs clearing between calls.
 #include <mutex>
 
 #include "ct_internal.cuh"
@@ -68,9 +75,13 @@ extern "C" ct_status ct_sqs_diag_noalloc(const ct_geom *g, const float *w, float
         scratch = g_scratch_ptr[dev];
     }
     cudaStream_t s = (cudaStream_t)stream;
-    // q = w (A 1) over all views into the static scratch, then D_L = A' q
-    CT_CUDA_TRY(launch_fp(g->fan, FP_ONES_W, nullptr, g->d_views_all, g->fan.na, scratch, nullptr, w, s),
-                "ct_sqs_diag_noalloc forward");
+    // q = w (A 1) over all views into the static scratch (from the kept ray sums if the geometry has
+    // them; computing and keeping them would allocate), then D_L = A' q
+    if (g->d_a1)
+        CT_CUDA_TRY(launch_weighted_ray_sums(g, w, scratch, s), "ct_sqs_diag_noalloc weights");
+    else
+        CT_CUDA_TRY(launch_fp(g->fan, FP_ONES_W, nullptr, g->d_views_all, g->fan.na, scratch, nullptr, w, s),
+                    "ct_sqs_diag_noalloc forward");
     CT_CUDA_TRY(launch_bp(g->fan, BP_PLAIN, scratch, g->d_views_all, g->fan.na, d_l, 1.0f, 0, nullptr, s),
                 "ct_sqs_diag_noalloc back");
     return CT_OK;

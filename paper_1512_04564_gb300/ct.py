@@ -94,6 +94,7 @@ def _load():
         "ct_relaxed_oslalm_solve_batched": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                             ctypes.POINTER(ct_solve_params), ctypes.POINTER(vp), cint,
                                             ctypes.POINTER(ct_solve_report), vp],
+        "ct_debug_barrier": [ctypes.c_longlong, cint],
         "ct_gemm_bf16": [vp, vp, vp, cint, cint, cint, vp, vp],
         "ct_conv3x3_bf16": [vp, cint, cint, vp, cint, vp, vp, vp, cint, cint, cint, cint, vp, vp],
         "ct_conv3x3_bf16_dgrad": [vp, cint, vp, vp, cint, cint, vp, cint, vp, vp, cint, cint, cint, vp, vp],
@@ -129,7 +130,7 @@ _lib = _load()
 EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_geom_precompute", "ct_geom_autotune", "ct_forward",
             "ct_pack_image", "ct_forward_packed", "ct_back", "ct_sqs_diag",
             "ct_sqs_diag_noalloc", "ct_fbp", "ct_reg_gradient", "ct_kappa", "ct_relaxed_oslalm_solve",
-            "ct_relaxed_oslalm_solve_batched", "ct_last_error", "ct_version", "ct_gemm_bf16", "ct_conv3x3_bf16",
+            "ct_relaxed_oslalm_solve_batched", "ct_debug_barrier", "ct_last_error", "ct_version", "ct_gemm_bf16", "ct_conv3x3_bf16",
             "ct_conv3x3_bf16_dgrad", "ct_conv3x3_wgrad_workspace", "ct_conv3x3_bf16_wgrad", "ct_unet_create",
             "ct_unet_destroy", "ct_unet_num_params", "ct_unet_get_params", "ct_unet_set_params", "ct_unet_forward",
             "ct_unet_backward", "ct_unet_adam", "ct_unet_status")
@@ -412,6 +413,12 @@ def ct_relaxed_oslalm_solve_batched(geoms, ys, ws, xs, params: list[dict], strea
                                                 ctypes.cast(xp, ctypes.POINTER(ctypes.c_void_p)), n, R,
                                                 _stream(stream)))
     return [_report_dict(R[i], reps[i][1], reps[i][2], params[i].get("x_ref") is not None) for i in range(n)]
+
+
+def ct_debug_barrier(max_polls: int = 0, missing: int = 0) -> None:
+    """Failure-detection hook of the batched persistent launch: the poll limit of every grid-barrier wait
+    (0: the built-in limit) and a number of barrier participants that never arrive (0: normal operation)."""
+    _check(_lib.ct_debug_barrier(int(max_polls), int(missing)))
 
 
 def version() -> int:

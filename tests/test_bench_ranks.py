@@ -70,17 +70,20 @@ def test_reference_arm_other_ranks_exit_without_work(rank):
 
 
 def test_reference_arm_line_contract(monkeypatch, capsys):
-    """Rank 0 prints one JSON line with the contract's keys (the oracle timing itself is replaced by a
-    stub here: it takes tens of seconds of CPU work)."""
+    """Rank 0 prints one JSON line with the contract's keys; each timed step is one whole oracle solve to
+    the tolerance and each warm-up step a one-subiteration solve (the oracle solve itself is replaced by
+    a stub here: it takes tens of seconds of CPU work)."""
     import bench
 
     calls = []
 
-    def fake(cfg, data, alpha, M, iters, budget_s=20.0, x0="fbp"):
-        calls.append(iters)
-        return {"value": 1.5, "unit": "s", "cores": 1, "kind": "oracle", "sample": "stub"}
+    def fake(cfg, data, alpha, M, xstar, tol_hu, x0="fbp", max_iter=60, stop_after_sub=None):
+        calls.append(stop_after_sub)
+        return {"seconds": 1.5, "fbp_s": 0.1, "dl_s": 0.2, "cores": 1, "iters_to_tol": 6,
+                "rmsd_trace_hu": [3.0, 0.9]}
 
-    monkeypatch.setattr(bench, "cpu_oracle_time_to_tol", fake)
+    monkeypatch.setattr(bench, "oracle_solve_to_tol", fake)
+    monkeypatch.setattr(bench, "oracle_xstar", lambda cfg: (object(), {"recipe": "stub", "kkt_rms_hu": 0.0}))
     monkeypatch.setattr(bench, "make_problem", lambda args, rank: (type("C", (), {"name": "fan2d_512"})(), 1.999,
                                                                      20, 30, None))
     monkeypatch.setenv("RANK", "0")
@@ -90,9 +93,23 @@ def test_reference_arm_line_contract(monkeypatch, capsys):
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] == 1.5 and line["unit"] == "s"
     assert line["higher_is_better"] is False and line["steps"] == 2 and line["warmup"] == 3
+    assert line["ms_per_step"] == 1500.0
     assert line["e2e"] == {"value": 1.5, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert line["cpu_baseline"]["kind"] == "oracle"
-    assert calls == [bench.REFERENCE_ITERS_TO_TOL[("fan2d_512", 20, 1.999, "fbp")]] * 5
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == 1.5
+    assert calls == [1, 1, 1, None, None]
+
+
+def test_reference_arm_without_stored_xstar(monkeypatch, capsys):
+    import bench
+
+    monkeypatch.setattr(bench, "oracle_xstar", lambda cfg: (None, None))
+    monkeypatch.setattr(bench, "make_problem", lambda args, rank: (type("C", (), {"name": "fan2d_x"})(), 1.999,
+                                                                     20, 30, None))
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference"])
+    assert bench.run_reference(bench.parse()) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and "unavailable" in line
 
 
 def test_kernel_digest_ignores_comments_only(tmp_path):

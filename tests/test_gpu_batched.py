@@ -164,3 +164,33 @@ def test_autotune_choice_keeps_parity():
     ref = FanProjector(g).forward(x.cpu().numpy().astype(np.float64))
     den = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
     assert np.max(np.abs(yy.cpu().numpy() - ref) / den) <= 3e-5
+
+
+def test_grid_barrier_wait_runs_out_and_context_survives():
+    """Failure detection of the persistent launch: with a barrier participant that never arrives and a
+    short poll limit, every grid-barrier wait gives up, the call returns CT_ETIMEOUT, and the next
+    call on the same context (hook reset) solves normally and matches a solve made before the failure."""
+    from paper_1512_04564_gb300 import ct
+
+    g, y, w = _problem(*CASES[0][:5])
+    G = ct.Geometry.from_fan(g)
+    yd, wd = torch.from_numpy(y).cuda(), torch.from_numpy(w).cuda()
+    p = dict(M=5, n_iter=2, alpha=1.999, beta=BETA, delta=DELTA)
+    x_ok = torch.zeros(g.ny, g.nx, device="cuda")
+    ct.ct_relaxed_oslalm_solve_batched([G], [yd], [wd], [x_ok], [p])
+    try:
+        ct.ct_debug_barrier(max_polls=2000, missing=1)
+        x_bad = torch.zeros(g.ny, g.nx, device="cuda")
+        with pytest.raises(ct.CTError) as e:
+            ct.ct_relaxed_oslalm_solve_batched([G], [yd], [wd], [x_bad], [p])
+        assert e.value.status == ct.CT_ETIMEOUT
+        assert "barrier" in str(e.value)
+    finally:
+        ct.ct_debug_barrier(0, 0)
+    x2 = torch.zeros(g.ny, g.nx, device="cuda")
+    ct.ct_relaxed_oslalm_solve_batched([G], [yd], [wd], [x2], [p])
+    torch.cuda.synchronize()
+    assert _hu_rmsd(x2.cpu().numpy(), x_ok.cpu().numpy(), g) <= 1e-6
+    with pytest.raises(ct.CTError) as e:
+        ct.ct_debug_barrier(-1, 0)
+    assert e.value.status == ct.CT_EINVAL

@@ -1,0 +1,107 @@
+"""Relaxed OS-LALM on the clinical-scale 2-D workload against the FP64 oracle.
+
+Workload: 512 x 512 pixels of 0.98 mm, 984 views x 888 cells of 1.0239 mm,
+the seeded chest-like phantom, W = counts, hyperbola potential (Sec. III,
+Eq. (ct_problem); Algorithm 1 of Sec. III-A).
+
+* The configuration the benchmark times: M = 20, alpha = 1.999, FBP start
+  (each side computes its own FBP of y), continuation in rho.  After each of
+  the first three outer iterations the GPU iterate is within 0.1 HU (RMSD
+  over the field of view) of the oracle's, on both projector paths: the
+  resident matrix (paired rows into the packed image [x | x^T], half-tile
+  cell-weight records) and the footprints evaluated on the fly.
+* The workload's named subset count, M = 41: the oracle's PWLS cost rises
+  from the second outer iteration on -- the ordered-subsets instability of
+  too many subsets (Sec. IV: relaxed OS-LALM is more sensitive to gradient
+  approximation errors when using too many subsets) -- and the GPU path
+  follows the oracle within 0.1 HU over the first two iterations.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import solver as osolver
+from oracle.fbp import fbp_fan_arc
+from oracle.projector import FanProjector
+
+pytestmark = pytest.mark.gpu
+
+TOL_HU = 0.1
+
+
+@pytest.fixture(scope="module")
+def problem():
+    c = synth.fan2d_512()
+    g = c.geom
+    d = synth.make_scan(c)
+    y32, w32 = d.y.astype(np.float32), d.w.astype(np.float32)
+    prob = osolver.PWLSProblem(FanProjector(g), y32.astype(np.float64), w32.astype(np.float64), c.beta_per_mm,
+                               c.delta, c.potential)
+    x0 = fbp_fan_arc(g, y32.astype(np.float64), "hann")
+    return {"c": c, "g": g, "y": y32, "w": w32, "prob": prob, "x0": x0, "DL": prob.D_L(),
+            "mask": osolver.fov_mask(g)}
+
+
+def _oracle_iterates(P, M, alpha, n_iter, cost=False):
+    xs, costs = [], []
+
+    def cb(k, x):
+        xs.append(x.copy())
+        if cost:
+            costs.append(P["prob"].cost(x))
+
+    osolver.relaxed_os_lalm(P["prob"], P["x0"], M, alpha, n_iter, D_L=P["DL"], callback=cb)
+    return xs, costs
+
+
+def _gpu_iterate(ct, G, P, M, alpha, n_iter):
+    c = P["c"]
+    x = torch.zeros(P["g"].ny, P["g"].nx, device="cuda")
+    ct.ct_relaxed_oslalm_solve(G, torch.from_numpy(P["y"]).cuda(), torch.from_numpy(P["w"]).cuda(), x, M=M,
+                               n_iter=n_iter, alpha=alpha, beta=c.beta_per_mm, delta=c.delta, potential=c.potential,
+                               init_fbp=True)
+    torch.cuda.synchronize()
+    return x.cpu().numpy().astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def geoms(problem):
+    from paper_1512_04564_gb300 import ct
+
+    fly = ct.Geometry.from_fan(problem["g"])
+    res = ct.Geometry.from_fan(problem["g"])
+    assert ct.ct_geom_precompute(res) > 0
+    return {"on_the_fly": fly, "resident_matrix": res}
+
+
+@pytest.fixture(scope="module")
+def oracle_m20(problem):
+    return _oracle_iterates(problem, 20, 1.999, 3)[0]
+
+
+@pytest.mark.parametrize("path", ["resident_matrix", "on_the_fly"])
+def test_timed_configuration_matches_oracle(problem, geoms, oracle_m20, path):
+    from paper_1512_04564_gb300 import ct
+
+    c = problem["c"]
+    for k, xo in enumerate(oracle_m20, start=1):
+        xg = _gpu_iterate(ct, geoms[path], problem, 20, 1.999, k)
+        d = osolver.rmsd_hu(xg, xo, problem["mask"], c.hu_per_unit)
+        assert d <= TOL_HU, (path, k, d)
+
+
+def test_named_subset_count_diverges_in_the_oracle(problem, geoms):
+    from paper_1512_04564_gb300 import ct
+
+    c = problem["c"]
+    xs, costs = _oracle_iterates(problem, 41, 1.999, 4, cost=True)
+    # the cost rises from the second outer iteration on, and by iteration 4 is several times its minimum
+    assert costs[1] > costs[0] and costs[2] > costs[1] and costs[3] > costs[2], costs
+    assert costs[3] > 3.0 * min(costs), costs
+    # the GPU path follows the oracle's iterates while they are still near the start
+    for k in (1, 2):
+        xg = _gpu_iterate(ct, geoms["resident_matrix"], problem, 41, 1.999, k)
+        d = osolver.rmsd_hu(xg, xs[k - 1], problem["mask"], c.hu_per_unit)
+        assert d <= TOL_HU, (k, d)

@@ -4,7 +4,11 @@ ct_sqs_diag_noalloc serves callers that cannot allocate device memory once
 running (a pool-reserved serving process, a latency-critical loop that must
 not enter cudaMalloc/cudaFree).  Its scratch is a fixed device array shared by
 all calls, so two calls in a row with different weights must each match the
-workspace-based entry point.  This file is collected last on purpose.
+workspace-based entry point, and so must a call on a smaller geometry right
+after one on a larger one (a stale tail of the larger sinogram, or a wrong row
+stride, would show).  The file sorts last so that a run stopping at its first
+failure has run every other GPU test first; no other test depends on the
+array, and these tests pass alone in a fresh process as well.
 """
 
 import numpy as np
@@ -42,6 +46,28 @@ def test_noalloc_matches_sqs_diag_on_consecutive_calls(gname, resident):
         ct.ct_sqs_diag_noalloc(G, w, out)
         torch.cuda.synchronize()
         assert _rel_err(out.cpu().numpy().astype(np.float64), ref.cpu().numpy().astype(np.float64)) <= 1e-5, call
+
+
+@pytest.mark.parametrize("resident", [False, True])
+def test_noalloc_larger_then_smaller_geometry(resident):
+    from paper_1512_04564_gb300 import ct
+
+    rng = np.random.default_rng(8)
+    for g in (synth.fan2d_128().geom, SMALL):  # 180 x 256 cells, then 45 x 61 with a different row length
+        G = ct.Geometry.from_fan(g)
+        if resident:
+            ct.ct_geom_precompute(G)
+        w = torch.from_numpy((rng.random((g.na, g.ns)) * 1e4 + 1.0).astype(np.float32)).cuda()
+        out = torch.full((g.ny, g.nx), float("nan"), device="cuda")
+        ct.ct_sqs_diag_noalloc(G, w, out)  # before ct_sqs_diag: no ray sums kept yet (forward pass)
+        ref = torch.empty(g.ny, g.nx, device="cuda")
+        ct.ct_sqs_diag(G, w, ref)
+        out2 = torch.full((g.ny, g.nx), float("nan"), device="cuda")
+        ct.ct_sqs_diag_noalloc(G, w, out2)  # after it: from the kept ray sums
+        torch.cuda.synchronize()
+        r = ref.cpu().numpy().astype(np.float64)
+        assert _rel_err(out.cpu().numpy().astype(np.float64), r) <= 1e-5
+        assert _rel_err(out2.cpu().numpy().astype(np.float64), r) <= 1e-5
 
 
 def test_noalloc_rejects_oversized_sinogram():
