@@ -30,11 +30,10 @@ struct FanDev {
     float x_edge0, y_edge0;   // x of the left edge of column 0, y of the lower edge of row 0 (mm)
     float cxo, cyo;           // (nx-1)/2 - offset_x, (ny-1)/2 - offset_y (pixel index of the origin)
     int max_span;             // upper bound on the detector cells one pixel footprint overlaps
-    const float4 *anchor;     // [na][nay*nax]: view-frame position of the anchor tile's centre relative
-                              // to the source, (t_par - dso, t_perp) (t_par kept as dso + a small
-                              // float, so the kernels see it with the small float's rounding), and
-                              // its detector coordinate u = gamma/dgamma + (ns-1)/2 - offset_s split
-                              // into hi + lo floats (FP64-derived)
+    const float4 *anchor;     // [na][nay*nax][3]: the Anchor of each (view, 8x8 tile), FP64-derived: view-frame
+                              // position of the tile centre relative to the source (t_par - dso, t_perp), its
+                              // detector coordinate u = gamma/dgamma + (ns-1)/2 - offset_s as n + af + alo,
+                              // and the derivatives of u and of e per pixel step (see point_u)
     const float2 *view_cs;    // [na]: (cos beta, sin beta)
     const float *view_beta;   // [na]: beta in [0, 2 pi)
     // resident system matrix (ct_geom_precompute); null when footprints are computed on the fly
@@ -142,73 +141,74 @@ ct_status cuda_fail(cudaError_t e, const char *what);
 
 // ---------------------------------------------------------------- device arithmetic
 
-// arctan by its Gregory (Taylor) series, for |z| <= 0.25 (truncation < |z|^15/15).
-__device__ __forceinline__ float atan_series(float z)
-{
-    const float z2 = z * z;
-    float p = fmaf(z2, -1.0f / 13.0f, 1.0f / 11.0f);
-    p = fmaf(z2, p, -1.0f / 9.0f);
-    p = fmaf(z2, p, 1.0f / 7.0f);
-    p = fmaf(z2, p, -1.0f / 5.0f);
-    p = fmaf(z2, p, 1.0f / 3.0f);
-    return fmaf(-z * z2, p, z);
-}
-
-// arctan for the pixel-corner offsets, |z| <= 0.02 (truncation < |z|^7/7 < 2e-13).
-__device__ __forceinline__ float atan_tiny(float z)
-{
-    const float z2 = z * z;
-    return fmaf(z * z2, fmaf(z2, 0.2f, -1.0f / 3.0f), z);
-}
-
-// Separable footprint of one pixel in one view: a unit-height trapezoid with
-// sorted vertices t0..t3 in detector-cell units relative to cell n (cell s
-// covers [s - n - 1/2, s - n + 1/2]), times the amplitude amp (chord through
-// the pixel along the ray through its centre).
-struct Footprint {
-    float t0, t1, t2, t3;
-    float amp;
-    float w1, w2, w3;  // t1 - t0, t2 - t1, t3 - t2
-    float i2w1, i2w3;  // 1/(2 w1) and 1/(2 w3), 0 for a vertical edge
+// FP64-derived reference point of one (view, 8x8 pixel tile): the tile centre's view-frame position
+// and detector coordinate, and the first-order change of the detector coordinate per pixel step.
+struct Anchor {
+    float ax, ay;              // (t_par - dso, t_perp) of the tile centre relative to the source (mm)
+    float af, alo;             // its detector coordinate u_A = n + af + alo (af on the exact grid, see point_u)
+    float kxh, kxl, kyh, kyl;  // du / d(pixel step along x), du / d(pixel step along y) at u_A: hi + lo
+    float mx, my;              // (a . d) / |a|^2 per pixel step along x and y (a: the centre, d: the step)
     int n;
 };
 
-// cb, sb: view direction; A: the pixel's tile anchor for this view; (ox, oy):
-// pixel centre minus tile centre (mm, image axes).
-__device__ __forceinline__ Footprint sf_footprint(const FanDev &G, float cb, float sb, float4 A, float ox, float oy)
+__device__ __forceinline__ Anchor load_anchor(const FanDev &G, int v, int atile)
 {
-    // pixel centre relative to the anchor, in the view frame (small vector: accurate in FP32)
-    const float dpar = fmaf(ox, cb, oy * sb);
-    const float dperp = fmaf(oy, cb, -ox * sb);
-    const float cpar = G.dso + (A.x + dpar);
-    const float cperp = A.y + dperp;
-    // fan angle of the centre relative to the anchor's: atan(cross(A, c) / dot(A, c))
-    // (the anchor's t_par = dso + A.x stays an unevaluated sum: its rounding would dominate the error)
-    const float crs = fmaf(G.dso, dperp, fmaf(A.x, dperp, -A.y * dpar));
-    const float dt = fmaf(G.dso, G.dso + fmaf(2.0f, A.x, dpar), fmaf(A.x, A.x + dpar, A.y * cperp));
-    const float du = atan_series(crs / dt) * G.inv_dg;
-    const float nf = floorf(A.z + du);
-    const float f = (A.z - nf) + (A.w + du);  // centre's detector coordinate relative to cell nf
-    // corners: angle relative to the centre, atan(cross(c, o) / (|c|^2 + c.o))
-    const float r2 = fmaf(cpar, cpar, cperp * cperp);
-    const float ir2 = __frcp_rn(r2);
-    const float xpar = G.hx * cb, xperp = -G.hx * sb;  // +half pixel along x, view frame
-    const float ypar = G.hy * sb, yperp = G.hy * cb;   // +half pixel along y
-    const float cx = fmaf(cpar, xperp, -cperp * xpar), cy = fmaf(cpar, yperp, -cperp * ypar);
-    const float ex = fmaf(cpar, xpar, cperp * xperp) * ir2, ey = fmaf(cpar, ypar, cperp * yperp) * ir2;
+    const float4 *p = G.anchor + 3 * ((size_t)v * (G.nax * G.nay) + atile);
+    const float4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2);
+    Anchor A;
+    A.ax = q0.x; A.ay = q0.y; A.af = q0.z; A.alo = q0.w;
+    A.kxh = q1.x; A.kxl = q1.y; A.kyh = q1.z; A.kyl = q1.w;
+    A.mx = q2.x; A.my = q2.y; A.n = __float_as_int(q2.z);
+    return A;
+}
+
+// Detector coordinate of the point (px, py) pixel steps from the anchor tile's centre (px, py multiples
+// of 1/2, |px|, |py| <= kAnchor / 2), returned as A.n + S + L.  The exact value is
+//     u = u_A + atan(N / (1 + e)) / dgamma,
+// N / dgamma = lin = kx px + ky py (the linear term, in cells), e = mx px + my py, so
+//     u - u_A = lin - [lin e / (1 + e) + (z - atan z) / dgamma],   z = lin dgamma / (1 + e),
+// with z - atan z = z^3/3 - z^5/5 + z^7/7 - ... (|z| <= ~0.1: the next term is below 3e-10 rad).
+// The host rounds af and kxh, kyh onto a grid of 2^-p cells chosen so that S = af + kxh px + kyh py is
+// exact in FP32 for every such point (and so are sums and differences of S values of one tile); the
+// remainders kxl, kyl, alo and the nonlinear correction, all small, form L.  A footprint vertex is then
+// (S - base) + L relative to an integer base cell: one FP32 rounding at the vertex's distance from it.
+__device__ __forceinline__ void point_u(const FanDev &G, const Anchor &A, float px, float py, float &S, float &L)
+{
+    S = fmaf(A.kxh, px, fmaf(A.kyh, py, A.af));
+    const float lo = fmaf(A.kxl, px, A.kyl * py);
+    const float lin = (S - A.af) + lo;
+    const float e = fmaf(A.mx, px, A.my * py);
+    const float lr = lin * __fdividef(1.0f, 1.0f + e);
+    const float z = lr * G.dgamma;
+    const float z2 = z * z;
+    const float c3 = lr * z2 * fmaf(z2, fmaf(z2, 1.0f / 7.0f, -0.2f), 1.0f / 3.0f);
+    L = (A.alo + lo) - fmaf(lr, e, c3);
+}
+
+// Separable footprint of one pixel in one view: a unit-height trapezoid with
+// sorted vertices t0..t3 in detector-cell units relative to cell n (cell n + j
+// covers [j - 1/2, j + 1/2]), times the amplitude amp (chord through the
+// pixel along the ray through its centre).
+struct Footprint {
+    float t0, t1, t2, t3;
+    float amp;
+    float w1, w3;      // t1 - t0, t3 - t2
+    float i2w1, i2w3;  // 1/(2 w1) and 1/(2 w3), 0 for a vertical edge
+    float m;           // (t1 + t2) / 2: integrals left of it are taken from t0, right of it from t3
+    float area;        // w1/2 + (t2 - t1) + w3/2
+    int n;
+};
+
+// Footprint from its four corner coordinates (S_k, L_k) (corners (-,-), (+,-), (-,+), (+,+) of the pixel),
+// amplitude and the anchor's base cell.
+__device__ __forceinline__ Footprint footprint_from_corners(const float (&S)[4], const float (&L)[4], float amp, int n_a)
+{
+    const float fl = floorf(0.5f * (S[0] + S[3]));
     float t[4];
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const float sx = (k & 1) ? 1.0f : -1.0f;
-        const float sy = (k & 2) ? 1.0f : -1.0f;
-        const float e = fmaf(sx, ex, sy * ey);                 // (c.o)/|c|^2, |e| < 0.01
-        const float inv = fmaf(e, e - 1.0f, 1.0f);              // 1/(1+e) to O(e^3)
-        const float z = fmaf(sx, cx, sy * cy) * ir2 * fmaf(-e * e, e, inv);
-        t[k] = fmaf(atan_tiny(z), G.inv_dg, f);
-    }
-    // sort the four vertices
-    float a0 = fminf(t[0], t[1]), a1 = fmaxf(t[0], t[1]);
-    float b0 = fminf(t[2], t[3]), b1 = fmaxf(t[2], t[3]);
+    for (int k = 0; k < 4; k++) t[k] = (S[k] - fl) + L[k];
+    const float a0 = fminf(t[0], t[1]), a1 = fmaxf(t[0], t[1]);
+    const float b0 = fminf(t[2], t[3]), b1 = fmaxf(t[2], t[3]);
     Footprint F;
     F.t0 = fminf(a0, b0);
     F.t3 = fmaxf(a1, b1);
@@ -216,81 +216,135 @@ __device__ __forceinline__ Footprint sf_footprint(const FanDev &G, float cb, flo
     F.t1 = fminf(m0, m1);
     F.t2 = fmaxf(m0, m1);
     F.w1 = F.t1 - F.t0;
-    F.w2 = F.t2 - F.t1;
     F.w3 = F.t3 - F.t2;
     F.i2w1 = F.w1 > 0.0f ? __fdividef(0.5f, F.w1) : 0.0f;
     F.i2w3 = F.w3 > 0.0f ? __fdividef(0.5f, F.w3) : 0.0f;
-    // amplitude: chord through the pixel along the centre ray = |c| / max(|c_x|/dx, |c_y|/dy)
-    const float imx = fabsf(fmaf(cpar, cb, -cperp * sb)) * G.inv_dx;
-    const float imy = fabsf(fmaf(cpar, sb, cperp * cb)) * G.inv_dy;
-    F.amp = __fdividef(r2 * rsqrtf(r2), fmaxf(imx, imy));
-    F.n = (int)nf;
+    F.m = 0.5f * (F.t1 + F.t2);
+    F.area = fmaf(0.5f, F.w1 + F.w3, F.t2 - F.t1);
+    F.amp = amp;
+    F.n = n_a + (int)fl;
     return F;
 }
 
-// Integral of the unit trapezoid over (-inf, u], branch-free: rising ramp
-// a^2/(2 w1) with a = clamp(u - t0, 0, w1), flat part clamp(u - t1, 0, w2),
-// falling ramp w3/2 - b^2/(2 w3) with b = clamp(t3 - u, 0, w3).  For u <= t2
-// the falling term is the rounding residue of w3/2 - w3^2/(2 w3), the same
-// constant for every such u, so it cancels in cell differences.
-__device__ __forceinline__ float trap_cdf(const Footprint &F, float u)
+// Chord through a pixel along the ray through its centre, |c| / max(|c_x| / dx, |c_y| / dy), c the
+// centre relative to the source (view frame: cpar, cperp).
+__device__ __forceinline__ float pixel_amplitude(const FanDev &G, float cb, float sb, float cpar, float cperp)
 {
-    const float a = fminf(fmaxf(u - F.t0, 0.0f), F.w1);
-    const float b = fminf(fmaxf(F.t3 - u, 0.0f), F.w3);
-    const float flat = fminf(fmaxf(u - F.t1, 0.0f), F.w2);
-    return fmaf(a * a, F.i2w1, flat) + fmaf(-b * b, F.i2w3, 0.5f * F.w3);
+    const float r2 = fmaf(cpar, cpar, cperp * cperp);
+    const float imx = fabsf(fmaf(cpar, cb, -cperp * sb)) * G.inv_dx;
+    const float imy = fabsf(fmaf(cpar, sb, cperp * cb)) * G.inv_dy;
+    return __fdividef(r2 * rsqrtf(r2), fmaxf(imx, imy));
 }
 
-// Area of the unit trapezoid.
-__device__ __forceinline__ float trap_area(const Footprint &F)
+// Footprint of the pixel whose centre is (px, py) pixel steps from the anchor tile's centre, in the view
+// with direction (cb, sb).
+__device__ __forceinline__ Footprint sf_footprint(const FanDev &G, float cb, float sb, const Anchor &A, float px, float py)
 {
-    return fmaf(0.5f, F.w1 + F.w3, F.w2);
+    float S[4], L[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) point_u(G, A, px + ((k & 1) ? 0.5f : -0.5f), py + ((k & 2) ? 0.5f : -0.5f), S[k], L[k]);
+    const float ox = px * G.dx, oy = py * G.dy;
+    const float cpar = G.dso + (A.ax + fmaf(ox, cb, oy * sb)), cperp = A.ay + fmaf(oy, cb, -ox * sb);
+    return footprint_from_corners(S, L, pixel_amplitude(G, cb, sb, cpar, cperp), A.n);
 }
 
-// sum_s a_s r_s over the cells of one footprint (row = detector row of one view),
-// by summation by parts over the cell edges: the trapezoid's integral is 0 at the
-// first cell's lower edge and its area at the last cell's upper edge, so only the
-// interior edges need the CDF.  Cells outside [0, ns) read as 0.
-__device__ __forceinline__ float footprint_dot(const Footprint &F, const float *__restrict__ row, int ns)
+// Signed tail of the unit trapezoid at u: left of the plateau's midpoint m, its integral over (-inf, u]
+// (rising ramp a^2/(2 w1), a = clamp(u - t0, 0, w1), plus the plateau part); right of m, minus its
+// integral over [u, inf) (the mirror image, from t3).  Both are small near the ends of the footprint,
+// so a cell's weight (a difference of tails, plus the area for the cell holding m) keeps its relative
+// precision however thin the sliver of footprint it takes.
+__device__ __forceinline__ float trap_tail(const Footprint &F, float u)
 {
-    const int j0 = (int)floorf(F.t0 - 0.5f) + 1;  // first cell, relative to n
-    const int jl = (int)ceilf(F.t3 + 0.5f) - 1;   // last cell
+    const bool left = u <= F.m;
+    const float x = left ? u - F.t0 : F.t3 - u;
+    const float y = left ? u - F.t1 : F.t2 - u;
+    const float w = left ? F.w1 : F.w3;
+    const float iw = left ? F.i2w1 : F.i2w3;
+    const float a = fminf(fmaxf(x, 0.0f), w);
+    const float h = fmaf(a * a, iw, fmaxf(y, 0.0f));
+    return left ? h : -h;
+}
+
+// First and last cell (relative to n) the footprint overlaps, and the cell holding m.
+__device__ __forceinline__ int foot_first(const Footprint &F) { return (int)floorf(F.t0 - 0.5f) + 1; }
+__device__ __forceinline__ int foot_last(const Footprint &F) { return (int)ceilf(F.t3 + 0.5f) - 1; }
+__device__ __forceinline__ int foot_mid(const Footprint &F) { return (int)floorf(F.m + 0.5f); }
+
+// Unit-amplitude integral of the footprint over relative cell j, given the tails at its lower and upper
+// edges: hi - lo, plus the area for the cell holding m.
+__device__ __forceinline__ float cell_integral(const Footprint &F, int j, float h_lo, float h_hi)
+{
+    return (h_hi - h_lo) + (j == foot_mid(F) ? F.area : 0.0f);
+}
+
+// Unit-amplitude integrals of the footprint over its cells j0 = foot_first(F), j0 + 1, ... (at most maxc):
+// emit(i, value) for cell j0 + i.  Returns the number of cells.
+template <class Emit>
+__device__ __forceinline__ int foot_cells(const Footprint &F, int maxc, Emit &&emit)
+{
+    const int j0 = foot_first(F);
+    const int cnt = max(min(foot_last(F) + 1 - j0, maxc), 0);
+    const int jm = foot_mid(F);
+    float hp = 0.0f;  // the tail is 0 at the first cell's lower edge
+    for (int i = 0; i < cnt; i++) {
+        const float hn = trap_tail(F, (float)(j0 + i) + 0.5f);
+        emit(i, (hn - hp) + (j0 + i == jm ? F.area : 0.0f));
+        hp = hn;
+    }
+    return cnt;
+}
+
+// sum_s a_s r_s over the cells of one footprint (row = detector row of one view), by summation by parts
+// over the cell edges: the tail is 0 at the first cell's lower edge and the last cell's upper edge, so
+// only interior edges are evaluated, plus the area times the residual of the cell holding m.  Cells
+// outside [0, ns) read as 0.  COHERENT loads bypass L1 (rows rewritten by other CTAs of a persistent
+// kernel).
+template <bool COHERENT>
+__device__ __forceinline__ float footprint_dot_t(const Footprint &F, const float *row, int ns)
+{
+    const int j0 = foot_first(F), jl = foot_last(F);
     int s = F.n + j0;
-    float rp = ((unsigned)s < (unsigned)ns) ? __ldg(&row[s]) : 0.0f;
+    auto ld = [&](int c) { return ((unsigned)c < (unsigned)ns) ? (COHERENT ? __ldcg(&row[c]) : __ldg(&row[c])) : 0.0f; };
+    float rp = ld(s);
     float acc = 0.0f;
     for (int j = j0; j < jl; j++) {
         s++;
-        const float rn = ((unsigned)s < (unsigned)ns) ? __ldg(&row[s]) : 0.0f;
-        acc = fmaf(trap_cdf(F, (float)j + 0.5f), rp - rn, acc);
+        const float rn = ld(s);
+        acc = fmaf(trap_tail(F, (float)j + 0.5f), rp - rn, acc);
         rp = rn;
     }
-    return F.amp * fmaf(trap_area(F), rp, acc);
+    return F.amp * fmaf(F.area, ld(F.n + foot_mid(F)), acc);
 }
 
-// Anchor of pixel (ix, iy) in view v, and the pixel centre's offset from the
-// anchor tile's centre (mm, image axes).  Small anchor tiles keep the offsets,
-// and with them the FP32 error of the footprint's position, small.
-__device__ __forceinline__ float4 pixel_anchor(const FanDev &G, int v, int ix, int iy, float &ox, float &oy)
+__device__ __forceinline__ float footprint_dot(const Footprint &F, const float *__restrict__ row, int ns)
+{
+    return footprint_dot_t<false>(F, row, ns);
+}
+
+// Anchor of pixel (ix, iy) in view v, and the pixel centre's offset from the anchor tile's centre in
+// pixel steps (px, py: half-integers).  Small anchor tiles keep the offsets, and with them the FP32
+// corrections of the footprint's position, small.
+__device__ __forceinline__ Anchor pixel_anchor(const FanDev &G, int v, int ix, int iy, float &px, float &py)
 {
     const int ax = ix / kAnchor, ay = iy / kAnchor;
-    ox = ((float)(ix - ax * kAnchor) - kAnchorHalf) * G.dx;
-    oy = ((float)(iy - ay * kAnchor) - kAnchorHalf) * G.dy;
-    return __ldg(&G.anchor[(size_t)v * (G.nax * G.nay) + ay * G.nax + ax]);
+    px = (float)(ix - ax * kAnchor) - kAnchorHalf;
+    py = (float)(iy - ay * kAnchor) - kAnchorHalf;
+    return load_anchor(G, v, ay * G.nax + ax);
 }
 
 // Footprint of pixel (ix, iy) in view v (loads its anchor).
 __device__ __forceinline__ Footprint pixel_footprint(const FanDev &G, int v, float cb, float sb, int ix, int iy)
 {
-    float ox, oy;
-    const float4 A = pixel_anchor(G, v, ix, iy, ox, oy);
-    return sf_footprint(G, cb, sb, A, ox, oy);
+    float px, py;
+    const Anchor A = pixel_anchor(G, v, ix, iy, px, py);
+    return sf_footprint(G, cb, sb, A, px, py);
 }
 
 // Weight a_ij of pixel footprint F in detector cell s.
 __device__ __forceinline__ float cell_weight(const Footprint &F, int s)
 {
-    const float j = (float)(s - F.n);
-    return F.amp * (trap_cdf(F, j + 0.5f) - trap_cdf(F, j - 0.5f));
+    const int j = s - F.n;
+    return F.amp * cell_integral(F, j, trap_tail(F, (float)j - 0.5f), trap_tail(F, (float)j + 0.5f));
 }
 
 constexpr float kRangePad = 0.02f;  // pixels of padding on a wedge's row/column range
@@ -348,22 +402,6 @@ __device__ __forceinline__ void ray_visit(const FanDev &G, int v, int s, int seg
             for (int ix = ix0; ix <= ix1; ix++) visit(ix, iy);
         }
     }
-}
-
-// Footprint rebuilt from its stored form (vertices; amplitude and base cell):
-// the same values sf_footprint returns.
-__device__ __forceinline__ Footprint footprint_from(float4 t, float2 an)
-{
-    Footprint F;
-    F.t0 = t.x; F.t1 = t.y; F.t2 = t.z; F.t3 = t.w;
-    F.w1 = F.t1 - F.t0;
-    F.w2 = F.t2 - F.t1;
-    F.w3 = F.t3 - F.t2;
-    F.i2w1 = F.w1 > 0.0f ? __fdividef(0.5f, F.w1) : 0.0f;
-    F.i2w3 = F.w3 > 0.0f ? __fdividef(0.5f, F.w3) : 0.0f;
-    F.amp = an.x;
-    F.n = __float_as_int(an.y);
-    return F;
 }
 
 // One ray of the resident matrix, warp-cooperative (all 32 lanes call it with the same range):
@@ -589,18 +627,7 @@ __device__ __forceinline__ void reg_terms(const FanDev &G, const float *__restri
 // other CTAs of a persistent kernel); same arithmetic.
 __device__ __forceinline__ float footprint_dot_coherent(const Footprint &F, const float *row, int ns)
 {
-    const int j0 = (int)floorf(F.t0 - 0.5f) + 1;
-    const int jl = (int)ceilf(F.t3 + 0.5f) - 1;
-    int s = F.n + j0;
-    float rp = ((unsigned)s < (unsigned)ns) ? __ldcg(&row[s]) : 0.0f;
-    float acc = 0.0f;
-    for (int j = j0; j < jl; j++) {
-        s++;
-        const float rn = ((unsigned)s < (unsigned)ns) ? __ldcg(&row[s]) : 0.0f;
-        acc = fmaf(trap_cdf(F, (float)j + 0.5f), rp - rn, acc);
-        rp = rn;
-    }
-    return F.amp * fmaf(trap_area(F), rp, acc);
+    return footprint_dot_t<true>(F, row, ns);
 }
 
 }  // namespace ct

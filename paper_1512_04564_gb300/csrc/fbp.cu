@@ -58,9 +58,9 @@ __global__ void __launch_bounds__(kFiltThreads) fbp_filter_kernel(FanDev G, cons
 }
 
 // Pixel-driven distance-weighted back-projection with linear interpolation.  The
-// fan angle of the pixel centre is its anchor's FP64-derived detector coordinate
-// plus the small angle between anchor and pixel (the footprint code's series),
-// instead of a full atan2 per (pixel, view).
+// detector coordinate of the pixel centre is its anchor's FP64-derived one plus
+// the offset point_u gives (the footprint code's), instead of a full atan2 per
+// (pixel, view).
 __global__ void __launch_bounds__(256) fbp_backproject_kernel(FanDev G, const float *__restrict__ q,
                                                               float *__restrict__ x, float dbeta)
 {
@@ -69,16 +69,15 @@ __global__ void __launch_bounds__(256) fbp_backproject_kernel(FanDev G, const fl
     float acc = 0.0f;
     for (int v = 0; v < G.na; v++) {
         const float2 cs = __ldg(&G.view_cs[v]);
-        float ox, oy;
-        const float4 A = pixel_anchor(G, v, ix, iy, ox, oy);
-        const float dpar = fmaf(ox, cs.x, oy * cs.y), dperp = fmaf(oy, cs.x, -ox * cs.y);
-        const float cpar = G.dso + (A.x + dpar), cperp = A.y + dperp;
-        const float crs = fmaf(G.dso, dperp, fmaf(A.x, dperp, -A.y * dpar));
-        const float dt = fmaf(G.dso, G.dso + fmaf(2.0f, A.x, dpar), fmaf(A.x, A.x + dpar, A.y * cperp));
-        const float du = atan_series(__fdividef(crs, dt)) * G.inv_dg;
-        const float fl = floorf(A.z + du);
-        const int i0 = (int)fl;
-        const float f = (A.z - fl) + (A.w + du);
+        float px, py;
+        const Anchor A = pixel_anchor(G, v, ix, iy, px, py);
+        float S, L;
+        point_u(G, A, px, py, S, L);
+        const float ox = px * G.dx, oy = py * G.dy;
+        const float cpar = G.dso + (A.ax + fmaf(ox, cs.x, oy * cs.y)), cperp = A.ay + fmaf(oy, cs.x, -ox * cs.y);
+        const float fl = floorf(S + L);
+        const int i0 = A.n + (int)fl;
+        const float f = (S - fl) + L;
         const float *row = q + (size_t)v * G.ns;
         const float v0 = ((unsigned)i0 < (unsigned)G.ns) ? __ldg(&row[i0]) : 0.0f;
         const float v1 = ((unsigned)(i0 + 1) < (unsigned)G.ns) ? __ldg(&row[i0 + 1]) : 0.0f;

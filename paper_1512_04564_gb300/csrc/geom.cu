@@ -217,26 +217,71 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     const int na = d->na, ntiles = F.nax * F.nay;  // anchor tiles
     std::vector<float2> cs(na);
     std::vector<float> bet(na);
-    std::vector<float4> anc((size_t)na * ntiles);
+    std::vector<float4> anc((size_t)na * ntiles * 3);
     const double c0 = (d->ns - 1) / 2.0 - d->offset_s;
-    for (int v = 0; v < na; v++) {
+    const double inv_dg = 1.0 / dg;
+    // Anchor tables (FP64): u at each 8x8 tile centre and its derivatives per pixel step.  For a tile
+    // centre a (relative to the source, view frame) and a step d = R(beta) (px dx, py dy), the fan angle
+    // changes by atan(N / (1 + e)), N = cross(a, d) / |a|^2, e = a.d / |a|^2, both linear in (px, py).
+    auto view_angle = [&](int v) {
         double deg = std::fmod(d->orbit_start_deg + (double)v * d->orbit_deg / na, 360.0);
         if (deg < 0) deg += 360.0;
-        const double b = deg * M_PI / 180.0;
+        return deg * M_PI / 180.0;
+    };
+    struct TileGeo { double tpar, tperp, u, kx, ky, mx, my; };
+    auto tile_geo = [&](double cb, double sb, int tx, int ty) {
+        const double X = (tx * kAnchor + (double)kAnchorHalf - cxo) * d->dx;
+        const double Y = (ty * kAnchor + (double)kAnchorHalf - cyo) * d->dy;
+        TileGeo t;
+        t.tpar = d->dso + X * cb + Y * sb;
+        t.tperp = -X * sb + Y * cb;
+        const double a2 = t.tpar * t.tpar + t.tperp * t.tperp;
+        t.u = std::atan2(t.tperp, t.tpar) * inv_dg + c0;
+        // a step along x: d = dx (cb, -sb) in the view frame; along y: d = dy (sb, cb)
+        t.kx = (t.tpar * (-d->dx * sb) - t.tperp * (d->dx * cb)) / a2 * inv_dg;
+        t.ky = (t.tpar * (d->dy * cb) - t.tperp * (d->dy * sb)) / a2 * inv_dg;
+        t.mx = (t.tpar * (d->dx * cb) + t.tperp * (-d->dx * sb)) / a2;
+        t.my = (t.tpar * (d->dy * sb) + t.tperp * (d->dy * cb)) / a2;
+        return t;
+    };
+    // the grid: S = af + kxh px + kyh py over all tiles and points (|px|, |py| <= kAnchor / 2) stays below
+    // 2^(24 - p) in magnitude, so FP32 holds every such S (a multiple of 2^-p) exactly
+    double kmax = 0.0;
+    for (int v = 0; v < na; v++) {
+        const double b = view_angle(v), cb = std::cos(b), sb = std::sin(b);
+        for (int ty = 0; ty < F.nay; ty++)
+            for (int tx = 0; tx < F.nax; tx++) {
+                const TileGeo t = tile_geo(cb, sb, tx, ty);
+                kmax = std::fmax(kmax, std::fabs(t.kx) + std::fabs(t.ky));
+            }
+    }
+    const double s_bound = 2.0 + kAnchor * kmax;  // af <= 1, plus twice the largest |kx px + ky py|
+    const int p = 23 - (int)std::ceil(std::log2(s_bound));
+    if (p < 8) {
+        set_error("detector cells too fine for the pixels: a tile's footprint spans %.0f cells", s_bound);
+        free_geom(g);
+        return CT_ENOTSUP;
+    }
+    const double qk = std::ldexp(1.0, p - 1), qa = std::ldexp(1.0, p);
+    for (int v = 0; v < na; v++) {
+        const double b = view_angle(v);
         const double cb = std::cos(b), sb = std::sin(b);
         cs[v] = make_float2((float)cb, (float)sb);
         bet[v] = (float)b;
         for (int ty = 0; ty < F.nay; ty++)
             for (int tx = 0; tx < F.nax; tx++) {
-                const double X = (tx * kAnchor + (double)kAnchorHalf - cxo) * d->dx;
-                const double Y = (ty * kAnchor + (double)kAnchorHalf - cyo) * d->dy;
-                const double tpar = d->dso + X * cb + Y * sb;
-                const double tperp = -X * sb + Y * cb;
-                const double u = std::atan2(tperp, tpar) / dg + c0;
-                const float uhi = (float)u;
+                const TileGeo t = tile_geo(cb, sb, tx, ty);
+                const double kxh = std::nearbyint(t.kx * qk) / qk, kyh = std::nearbyint(t.ky * qk) / qk;
+                const double n = std::floor(t.u), fr = t.u - n;
+                const double af = std::nearbyint(fr * qa) / qa;
+                float4 *q = &anc[((size_t)v * ntiles + ty * F.nax + tx) * 3];
                 // t_par as dso (the kernels' float) + a small float
-                anc[(size_t)v * ntiles + ty * F.nax + tx] =
-                    make_float4((float)(tpar - (double)F.dso), (float)tperp, uhi, (float)(u - (double)uhi));
+                q[0] = make_float4((float)(t.tpar - (double)F.dso), (float)t.tperp, (float)af, (float)(fr - af));
+                q[1] = make_float4((float)kxh, (float)(t.kx - kxh), (float)kyh, (float)(t.ky - kyh));
+                const int ni = (int)n;
+                float nf;
+                std::memcpy(&nf, &ni, sizeof nf);  // the base cell, as the bits of an int
+                q[2] = make_float4((float)t.mx, (float)t.my, nf, 0.0f);
             }
     }
     std::vector<int> ident(na);

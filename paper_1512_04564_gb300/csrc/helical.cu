@@ -117,14 +117,14 @@ struct ColumnAxial {
 // H - L = (L (d+ + d-) + 2 d+ d-) / (2L + d+ + d-), d+- = L_max,min - L; eps
 // receives (L_max - L_min) / (L_max + L_min).
 template <bool TT>
-__device__ __forceinline__ ColumnAxial column_axial(const HelixDev &H, float4 A, float4 X, float cb, float sb,
+__device__ __forceinline__ ColumnAxial column_axial(const HelixDev &H, const Anchor &A, float4 X, float cb, float sb,
                                                     float ox, float oy, float pdx, float pdy, float &eps)
 {
     const float dpar = fmaf(ox, cb, oy * sb), dperp = fmaf(oy, cb, -ox * sb);
-    const float cpar = H.dso + (A.x + dpar), cperp = A.y + dperp;  // A.x: the anchor's t_par - dso
+    const float cpar = H.dso + (A.ax + dpar), cperp = A.ay + dperp;  // A.ax: the anchor's t_par - dso
     const float L = sqrtf(fmaf(cpar, cpar, cperp * cperp));
     const float LA = X.x * H.kA;
-    const float num = fmaf(2.0f, fmaf(H.dso, dpar, fmaf(A.x, dpar, A.y * dperp)), fmaf(dpar, dpar, dperp * dperp));
+    const float num = fmaf(2.0f, fmaf(H.dso, dpar, fmaf(A.ax, dpar, A.ay * dperp)), fmaf(dpar, dpar, dperp * dperp));
     float dL = __fdividef(num, L + LA);
     float Lc = L;
     eps = 0.0f;
@@ -299,19 +299,13 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
         if (lane < n) {  // column role: footprint weights and axial parameters of one column
             const int bc = s_lo[c] + (t - s_pre[c]);
             const int ix = M.col ? c : bc, iy = M.col ? bc : c;
-            float ox, oy;
-            const float4 A = pixel_anchor(G, v, ix, iy, ox, oy);
+            float px, py;
+            const Anchor A = pixel_anchor(G, v, ix, iy, px, py);
+            const float ox = px * G.dx, oy = py * G.dy;
             const size_t ai = (size_t)v * (G.nax * G.nay) + (iy / kAnchor) * G.nax + ix / kAnchor;
-            const Footprint F = sf_footprint(G, cs.x, cs.y, A, ox, oy);
-            const int j0 = (int)floorf(F.t0 - 0.5f) + 1;
-            cnt = max(min((int)ceilf(F.t3 + 0.5f) - j0, kHxMaxSpan), 0);
-            float Fp = trap_cdf(F, (float)j0 - 0.5f);
-            for (int i = 0; i < cnt; i++) {
-                const float Fn = trap_cdf(F, (float)(j0 + i) + 0.5f);
-                sw[lane][i] = (Fn - Fp) * F.amp;
-                Fp = Fn;
-            }
-            cf = F.n + j0 - s0;
+            const Footprint F = sf_footprint(G, cs.x, cs.y, A, px, py);
+            cnt = foot_cells(F, kHxMaxSpan, [&](int i, float a) { sw[lane][i] = a * F.amp; });
+            cf = F.n + foot_first(F) - s0;
             // axial parameters; the lowest and highest row boundaries give the voxel range
             const float4 X = __ldg(&H.tile_ax[ai]);
             float eps;
@@ -581,8 +575,9 @@ __global__ void __launch_bounds__(kHxBpCols) bp_helix_kernel(FanDev G, HelixDev 
     const int ixc = min(ix, G.nx - 1), iyc = min(iy, G.ny - 1);
     const int atile = (iyc / kAnchor) * G.nax + ixc / kAnchor;
     const int ntiles = G.nax * G.nay;
-    const float ox = ((float)(ixc - (ixc / kAnchor) * kAnchor) - kAnchorHalf) * G.dx;
-    const float oy = ((float)(iyc - (iyc / kAnchor) * kAnchor) - kAnchorHalf) * G.dy;
+    const float px = (float)(ixc - (ixc / kAnchor) * kAnchor) - kAnchorHalf;
+    const float py = (float)(iyc - (iyc / kAnchor) * kAnchor) - kAnchorHalf;
+    const float ox = px * G.dx, oy = py * G.dy;
     float *qb = s_qb + tid;
     float *wq = s_w + tid;
     float rho = 1.0f;
@@ -595,7 +590,7 @@ __global__ void __launch_bounds__(kHxBpCols) bp_helix_kernel(FanDev G, HelixDev 
         for (int k = 0; k < nviews; k++) {
             const int v = __ldg(&views[k]);
             const float2 cs = __ldg(&G.view_cs[v]);
-            const float4 A = __ldg(&G.anchor[(size_t)v * ntiles + atile]);
+            const Anchor A = load_anchor(G, v, atile);
             const float2 zb = __ldg(&H.view_zb[v]);
             float eps;
             const ColumnAxial Cx = column_axial<TT>(H, A, __ldg(&H.tile_ax[(size_t)v * ntiles + atile]), cs.x, cs.y,
@@ -612,17 +607,12 @@ __global__ void __launch_bounds__(kHxBpCols) bp_helix_kernel(FanDev G, HelixDev 
             const int t_lo = (int)fmaxf(floorf(uA - hwA + 0.499f), 0.0f);
             const int t_hi = (int)fminf(floorf(uB + hwB + 0.501f), (float)(nt - 1));
             if (t_lo > t_hi) continue;  // the chunk's shadow misses the detector in this view
-            const Footprint F = sf_footprint(G, cs.x, cs.y, A, ox, oy);
-            const int j0 = (int)floorf(F.t0 - 0.5f) + 1;
-            const int cnt = max(min((int)ceilf(F.t3 + 0.5f) - j0, kHxMaxSpan), 0);
-            const int sfirst = F.n + j0;
-            float Fp = trap_cdf(F, (float)j0 - 0.5f);
-            for (int i = 0; i < cnt; i++) {
-                const float Fn = trap_cdf(F, (float)(j0 + i) + 0.5f);
+            const Footprint F = sf_footprint(G, cs.x, cs.y, A, px, py);
+            const int sfirst = F.n + foot_first(F);
+            const int cnt = foot_cells(F, kHxMaxSpan, [&](int i, float a) {
                 const int s = sfirst + i;
-                wq[i * kHxBpCols] = ((unsigned)s < (unsigned)G.ns) ? (Fn - Fp) * F.amp : 0.0f;
-                Fp = Fn;
-            }
+                wq[i * kHxBpCols] = ((unsigned)s < (unsigned)G.ns) ? a * F.amp : 0.0f;
+            });
             const int i0 = max(-sfirst, 0);
             const int i1 = min(cnt, G.ns - sfirst);
             // running sums of q_t = c_t sum_s w_s y[t][s] over rows t_lo..t_hi

@@ -191,16 +191,9 @@ __global__ void __launch_bounds__(kBundleWarps * 32, 5) fp_bundle_kernel(FanDev 
             const float xv = (MODE == FP_ONES_W) ? 1.0f : __ldg(&x[(size_t)iy * G.nx + ix]);
             if (xv != 0.0f) {
                 const Footprint F = pixel_footprint(G, v, cs.x, cs.y, ix, iy);
-                const int j0 = (int)floorf(F.t0 - 0.5f) + 1;
-                cnt = max(min((int)ceilf(F.t3 + 0.5f) - j0, kMaxSpan), 0);
                 const float xa = xv * F.amp;
-                float Fp = trap_cdf(F, (float)j0 - 0.5f);
-                for (int i = 0; i < cnt; i++) {
-                    const float Fn = trap_cdf(F, (float)(j0 + i) + 0.5f);
-                    sw[lane][i] = (Fn - Fp) * xa;
-                    Fp = Fn;
-                }
-                cf = F.n + j0 - s0;
+                cnt = foot_cells(F, kMaxSpan, [&](int i, float a) { sw[lane][i] = a * xa; });
+                cf = F.n + foot_first(F) - s0;
             }
         }
         scf[lane] = cf;

@@ -2,9 +2,10 @@
 relaxed OS-LALM) against the FP64 oracle, through the C ABI.
 
 Tolerances follow the 2-D path's: per ray / per voxel |gpu - oracle| <= 1e-5 x
-max(|oracle|, 1e-3 max|oracle|) for volumes shaped like the workloads, 3e-5 for
-uniform-random volumes whose signal reaches the border (the FP32 resolution of
-a sliver-thin transaxial footprint overlap); <A x, y> vs <x, A'y> from the GPU
+max(|oracle|, 1e-3 max|oracle|), for volumes shaped like the workloads and for
+uniform-random volumes whose signal reaches the border (sliver-thin transaxial
+footprint overlaps; the transaxial footprint is the 2-D one, whose vertices
+are placed to about 1e-7 cells); <A x, y> vs <x, A'y> from the GPU
 outputs to 1e-5; the solver within 0.1 HU RMSD after a fixed iteration count.
 The axial footprint adds no tighter limit: its row boundaries are placed to
 about 4e-6 of a voxel (FP32 coordinates up to ~100 voxels), which moves at
@@ -23,7 +24,7 @@ from oracle.helical import HelicalProjector
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
-TOL_BORDER = 3e-5
+TOL_BORDER = TOL
 MU_W = 0.02
 HU = 1000.0 / MU_W
 
@@ -84,7 +85,9 @@ def test_forward_parity(ct, case, kind):
     y = torch.empty(g.na, g.nt, g.ns, device="cuda")
     ct.ct_forward(G, dev(x), y)
     ref = HelicalProjector(g).forward(x.astype(np.float64))
-    assert rel_err(y.cpu().numpy(), ref) <= (TOL if kind == "phantom" else TOL_BORDER)
+    e = rel_err(y.cpu().numpy(), ref)
+    print(f"helical forward {case} {kind}: worst per-ray error {e:.2e}")
+    assert e <= (TOL if kind == "phantom" else TOL_BORDER)
 
 
 @pytest.mark.parametrize("case", list(CASES))

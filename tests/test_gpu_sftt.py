@@ -3,8 +3,8 @@
 The kernels run the rectangle model's arithmetic at the ramps' centre and add
 the ramp corrections at the row boundaries the ramps straddle; the oracle
 integrates each voxel's trapezoid over each row directly.  Same tolerances as
-the rectangle model (per ray / per voxel 1e-5 of max(|value|, 1e-3 max),
-3e-5 for uniform-random volumes reaching the border), on the same four
+the rectangle model (per ray / per voxel 1e-5 of max(|value|, 1e-3 max), also
+for uniform-random volumes reaching the border), on the same four
 geometries, plus adjointness, view subsets, D_L, the solver (<= 0.1 HU after
 3 iterations of M = 8) and sampled rays and voxels of one subset of the
 full 512 x 512 x 64, 2952-view scan.
