@@ -315,13 +315,10 @@ __global__ void __launch_bounds__(kThreads, 5) batched_kernel(const BatchSlice *
                             an = __ldcs(&B.G.foot_an[i]);
                         }
                         const float *row = B.resid + (size_t)k * B.G.ns;
-                        if (__float_as_int(b.y) == kWideRecord) {  // wider than a record: on the fly
-                            const int v = B.perm[v0 + k];
-                            const float2 cs = __ldg(&B.G.view_cs[v]);
-                            acc += footprint_dot_coherent(pixel_footprint(B.G, v, cs.x, cs.y, ixc, iyc), row, B.G.ns);
-                        } else {
+                        if (__float_as_int(b.y) == kWideRecord)  // wider than a record: the overflow weights
+                            acc += wide_record_dot<true>(B.G.foot_ovf, w, row, B.G.ns);
+                        else
                             acc += record_dot<true>(w, b, row, B.G.ns);
-                        }
                     }
                 } else {
                     for (int k = 0; k < nv; k++) {

@@ -39,7 +39,9 @@ struct FanDev {
     // resident system matrix (ct_geom_precompute); null when footprints are computed on the fly
     const float4 *foot_t;     // [na][ntiles][256]: a_ij of the pixel's first four cells n0 .. n0+3
     const float2 *foot_an;    // [na][ntiles][256]: a_ij of cell n0+4, and n0 as int bits (kWideRecord:
-                              // the footprint covers more than kRecordCells cells; evaluate it on the fly)
+                              // the footprint covers more than kRecordCells cells; foot_t then holds, as int
+                              // bits, the offset of its weights in foot_ovf, their count and n0)
+    const float *foot_ovf;    // weights of the wide footprints (~1% of the records at 512 x 512)
     const long long *row_ptr; // [na*ns + 1]: start of each ray's entry pairs (ray-major; the entries in march
                               // order, two per pair, a ray with an odd count padded by a zero entry)
     const float2 *row_w;      // [pairs]: a_ij of the pair's two entries
@@ -123,6 +125,7 @@ struct ct_geom {
     int *d_row_base = nullptr;
     float4 *d_foot_t = nullptr;
     float2 *d_foot_an = nullptr;
+    float *d_foot_ovf = nullptr;
     float *d_xpack = nullptr;     // FanDev::xpack
     unsigned long long matrix_bytes = 0;
     int device = 0;
@@ -533,6 +536,20 @@ ct_status stage_views(const ct_geom *g, const int *views, int nviews, const int 
 
 constexpr int kRecordCells = 5;          // cells per stored (view, pixel) record
 constexpr int kWideRecord = -(1 << 30);  // base-cell code of a footprint wider than kRecordCells cells
+
+// sum_k a_k row[n0 + k] over the weights of a wide footprint kept in the overflow array.
+template <bool COHERENT = false>
+__device__ __forceinline__ float wide_record_dot(const float *__restrict__ ovf, float4 w, const float *row, int ns)
+{
+    const int off = __float_as_int(w.x), cnt = __float_as_int(w.y), n0 = __float_as_int(w.z);
+    float acc = 0.0f;
+#pragma unroll 1  // rare and short: unrolled, it costs the record loop around it its registers
+    for (int k = 0; k < cnt; k++) {
+        const int c = n0 + k;
+        if ((unsigned)c < (unsigned)ns) acc = fmaf(__ldg(&ovf[off + k]), COHERENT ? __ldcg(&row[c]) : __ldg(&row[c]), acc);
+    }
+    return acc;
+}
 
 // sum_k a_k row[n0 + k] over one stored record (cells outside [0, ns) read as 0).  COHERENT loads
 // bypass L1 (rows rewritten by other CTAs of a persistent kernel).

@@ -85,6 +85,7 @@ static void free_geom(ct_geom *g)
     cudaFree(g->d_row_base);
     cudaFree(g->d_foot_t);
     cudaFree(g->d_foot_an);
+    cudaFree(g->d_foot_ovf);
     cudaFree(g->d_xpack);
     cudaFree(g->d_view_zb);
     cudaFree(g->d_row_c);

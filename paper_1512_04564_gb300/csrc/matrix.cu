@@ -79,7 +79,14 @@ __global__ void __launch_bounds__(256) matrix_fill_kernel(FanDev G, const long l
     }
 }
 
-__global__ void __launch_bounds__(256) matrix_foot_kernel(FanDev G, float4 *__restrict__ ft, float2 *__restrict__ fan)
+// Per-(view, pixel) records of cell weights.  COUNT: only add the cells of the footprints wider than a
+// record to *ovf_used.  Otherwise also write those footprints' weights to ovf (slots taken with an
+// atomic counter; a record keeps its slot's offset, so the values a kernel reads do not depend on the
+// order slots were taken in).
+template <bool COUNT>
+__global__ void __launch_bounds__(256) matrix_foot_kernel(FanDev G, float4 *__restrict__ ft, float2 *__restrict__ fan,
+                                                          float *__restrict__ ovf, unsigned long long *ovf_used,
+                                                          unsigned long long ovf_cap)
 {
     const int ntiles = G.ntx * G.nty;
     const int v = blockIdx.x / ntiles, tile = blockIdx.x - v * ntiles;
@@ -91,15 +98,23 @@ __global__ void __launch_bounds__(256) matrix_foot_kernel(FanDev G, float4 *__re
     const Footprint F = pixel_footprint(G, v, cs.x, cs.y, ix, iy);
     const size_t i = ((size_t)v * (G.ntx * G.nty) + tile) * (kTile * kTile) + threadIdx.x;
     // the footprint's cells, as cell_weight evaluates them (the same a_ij as the ray-major rows)
-    const int j0 = (int)floorf(F.t0 - 0.5f) + 1, jl = (int)ceilf(F.t3 + 0.5f) - 1;
-    float w[kRecordCells] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-    int code = kWideRecord;
-    if (jl - j0 + 1 <= kRecordCells) {
-        for (int k = 0; k <= jl - j0; k++) w[k] = cell_weight(F, F.n + j0 + k);
-        code = F.n + j0;
+    const int j0 = foot_first(F), jl = foot_last(F);
+    const int cnt = jl - j0 + 1;
+    if (cnt > kRecordCells) {
+        const unsigned long long off = atomicAdd(ovf_used, (unsigned long long)cnt);
+        if (COUNT) return;
+        const bool fits = off + cnt <= ovf_cap;  // always, as both passes count the same footprints
+        if (fits)
+            for (int k = 0; k < cnt; k++) ovf[off + k] = cell_weight(F, F.n + j0 + k);
+        ft[i] = make_float4(__int_as_float((int)off), __int_as_float(fits ? cnt : 0), __int_as_float(F.n + j0), 0.0f);
+        fan[i] = make_float2(0.0f, __int_as_float(kWideRecord));
+        return;
     }
+    if (COUNT) return;
+    float w[kRecordCells] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    for (int k = 0; k < cnt; k++) w[k] = cell_weight(F, F.n + j0 + k);
     ft[i] = make_float4(w[0], w[1], w[2], w[3]);
-    fan[i] = make_float2(w[4], __int_as_float(code));
+    fan[i] = make_float2(w[4], __int_as_float(F.n + j0));
 }
 
 // in-place exclusive scan of blocks of 1024 values; block totals to sums
@@ -176,10 +191,12 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     float4 *ft = nullptr;
     float2 *fan = nullptr;
     float *xp = nullptr;
+    float *ovf = nullptr;
     if (2LL * G.nx * G.ny >= (1LL << 31)) return cudaErrorNotSupported;  // packed-image indices are 32-bit
     cudaError_t e = cudaMalloc(&rp, sizeof(long long) * (R + 1));
     if (e != cudaSuccess) return e;
     auto fail = [&](cudaError_t err) {
+        cudaFree(ovf);
         cudaFree(xp);
         cudaFree(rp);
         cudaFree(wts);
@@ -222,7 +239,8 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     hc[R] = (int)nchunks;
     hc[R + 1] = 0;  // the too-far flag
     if (nchunks >= (1LL << 31) - 4) return fail(cudaErrorNotSupported);
-    if ((e = cudaMalloc(&first, sizeof(int) * (size_t)(R + 2))) != cudaSuccess) return fail(e);
+    // (R + 2 entries and two spare 8-byte-aligned ints for the overflow counter)
+    if ((e = cudaMalloc(&first, sizeof(int) * (size_t)(R + 6))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&base, sizeof(int) * (size_t)(nchunks + 4))) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(first, hc.data(), sizeof(int) * (R + 2), cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e);
@@ -232,7 +250,19 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     matrix_fill_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(G, rp, first, reinterpret_cast<float *>(wts),
                                                                     reinterpret_cast<short *>(steps), base, first + R + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
-    matrix_foot_kernel<<<(unsigned)((size_t)G.ntx * G.nty * G.na), 256, 0, st>>>(G, ft, fan);
+    // records: the wide footprints' cells counted first, then their overflow array allocated and filled
+    // two spare ints of `first` at an 8-byte boundary
+    unsigned long long *used = reinterpret_cast<unsigned long long *>(first + ((R + 3) & ~1LL));
+    const unsigned nfoot = (unsigned)((size_t)G.ntx * G.nty * G.na);
+    if ((e = cudaMemsetAsync(used, 0, sizeof(unsigned long long), st)) != cudaSuccess) return fail(e);
+    matrix_foot_kernel<true><<<nfoot, 256, 0, st>>>(G, ft, fan, nullptr, used, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    unsigned long long n_ovf = 0;
+    if ((e = cudaMemcpy(&n_ovf, used, sizeof(n_ovf), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
+    if (n_ovf >= (1ull << 31)) return fail(cudaErrorNotSupported);  // offsets are 32-bit
+    if ((e = cudaMalloc(&ovf, sizeof(float) * (size_t)(n_ovf > 0 ? n_ovf : 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemsetAsync(used, 0, sizeof(unsigned long long), st)) != cudaSuccess) return fail(e);
+    matrix_foot_kernel<false><<<nfoot, 256, 0, st>>>(G, ft, fan, ovf, used, n_ovf);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
     int far = 0;
@@ -261,7 +291,7 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     // the exact size: row pointers, chunk pointers (+ flag), entries, chunk bases, records
     g->matrix_bytes = (unsigned long long)(R + 1) * 8ull + (unsigned long long)(R + 2) * 4ull +
                       (unsigned long long)nnz * 12ull + (unsigned long long)(nchunks + 4) * 4ull +
-                      (unsigned long long)G.na * ntile_px * 24ull;
+                      (unsigned long long)G.na * ntile_px * 24ull + n_ovf * 4ull;
     g->d_row_ptr = rp;
     g->d_row_w = wts;
     g->d_row_d = steps;
@@ -279,6 +309,8 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     g->fan.ray_order = g->d_ray_order;
     g->fan.foot_t = ft;
     g->fan.foot_an = fan;
+    g->d_foot_ovf = ovf;
+    g->fan.foot_ovf = ovf;
     return cudaSuccess;
 }
 

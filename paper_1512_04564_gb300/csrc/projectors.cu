@@ -25,10 +25,10 @@
 // * resident-matrix kernel (after ct_geom_precompute): one warp per ray
 //   streams the ray's stored (pixel, a_ij) entries and gathers x.
 //
-// Back-projector: one CTA per 16x16 pixel tile, two pixels per thread,
-// gathering from the cells its footprint covers: footprints evaluated on the
-// fly (each pixel relative to its 8x8 anchor tile), or the resident matrix's
-// per-(view, pixel) records of cell weights.  Fused epilogues: plain
+// Back-projector: one CTA per 16x16 pixel tile (or half tile), gathering from
+// the cells its footprint covers: footprints evaluated on the fly (corners
+// shared by neighbouring pixels, staged per view in shared memory), or the
+// resident matrix's per-(view, pixel) records of cell weights.  Fused epilogues: plain
 // x = scale A'r (+x), and the relaxed OS-LALM g/h updates of Algorithm 1/2
 // (Sec. III-A).
 #include <cstdio>
@@ -334,7 +334,8 @@ __device__ __forceinline__ void bp_epilogue(const FanDev &G, const SolveDev &S, 
 // Resident-matrix back-projection, one CTA per half tile (16 x 8 pixels, the first or last 128
 // records of a tile's block), one pixel per thread: twice the CTAs and warps of the two-pixel
 // kernel, which with 1024 tiles at 512 x 512 left the SMs 60% empty.  The next view's record is
-// loaded while the current view's is used; footprints wider than a record are evaluated on the fly.
+// loaded while the current view's is used; footprints wider than a record read their weights from the
+// overflow array.
 template <int MODE>
 __global__ void __launch_bounds__(kBpThreads, 16) bp_records_kernel(FanDev G, const float *__restrict__ sino,
                                                                   const int *__restrict__ views, int nviews,
@@ -367,13 +368,10 @@ __global__ void __launch_bounds__(kBpThreads, 16) bp_records_kernel(FanDev G, co
             an = __ldcs(&G.foot_an[i]);
         }
         const float *row = sino + (size_t)k * G.ns;
-        if (__float_as_int(b.y) == kWideRecord) {  // rare: a footprint wider than a record
-            const int v = __ldg(&views[k]);
-            const float2 cs = __ldg(&G.view_cs[v]);
-            acc += footprint_dot(pixel_footprint(G, v, cs.x, cs.y, ixc, iyc), row, G.ns);
-        } else {
+        if (__float_as_int(b.y) == kWideRecord)  // rare: a footprint wider than a record
+            acc += wide_record_dot(G.foot_ovf, w, row, G.ns);
+        else
             acc += record_dot(w, b, row, G.ns);
-        }
     }
     bp_epilogue<MODE>(G, S, xo, ix, iy, acc, rho, scale, accumulate);
     if (MODE == BP_SOLVE_UPDATE) {
@@ -391,33 +389,75 @@ __global__ void __launch_bounds__(kBpThreads, 16) bp_records_kernel(FanDev G, co
     }
 }
 
-// Back-projection with the footprints evaluated on the fly: one CTA per 16x16 tile, 128 threads, two
-// pixels per thread (rows ly and ly + 8 of the tile).
+// Back-projection with the footprints evaluated on the fly: one CTA per 16x16 tile (four 8x8 anchor
+// tiles), one pixel per thread.  A pixel corner is shared by up to four pixels, so per view the CTA
+// first computes the detector coordinates (S, L) of the 4 x 9 x 9 corners of its anchor tiles into
+// shared memory (double-buffered: the next view's corners are computed while this view's are used, one
+// barrier per view); each pixel then builds its footprint from its four corners, its amplitude from its
+// centre ray, and takes the dot product with the view's detector row.
+constexpr int kBpFlyThreads = kTile * kTile;
+constexpr int kCornerSide = kAnchor + 1;                  // corners per side of an anchor tile
+constexpr int kTileCorners = 4 * kCornerSide * kCornerSide;  // 324 per CTA
+
 template <int MODE>
-__global__ void __launch_bounds__(kBpThreads, 8) bp_fan2d_kernel(FanDev G, const float *__restrict__ sino,
-                                                              const int *__restrict__ views, int nviews,
-                                                              float *__restrict__ xo, float scale, int accumulate,
-                                                              SolveDev S)
+__global__ void __launch_bounds__(kBpFlyThreads, 4) bp_fan2d_kernel(FanDev G, const float *__restrict__ sino,
+                                                                 const int *__restrict__ views, int nviews,
+                                                                 float *__restrict__ xo, float scale, int accumulate,
+                                                                 SolveDev S)
 {
+    __shared__ float2 s_c[2][kTileCorners];  // (S, L) of corner (quadrant, cy, cx)
+    __shared__ int s_n[2][4];                // base cell of each quadrant's anchor
     const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
-    const int ix = blockIdx.x * kTile + lx, iy0 = blockIdx.y * kTile + ly, iy1 = iy0 + kTile / 2;
-    // footprints are evaluated for in-image pixels only (a partial tile's outside pixels take the
-    // edge pixel's, and their results are not stored); rows ly and ly + 8 lie in two anchor tiles
-    const int ixc = min(ix, G.nx - 1), iy0c = min(iy0, G.ny - 1), iy1c = min(iy1, G.ny - 1);
+    const int ix = blockIdx.x * kTile + lx, iy = blockIdx.y * kTile + ly;
+    const bool inside = ix < G.nx && iy < G.ny;
+    const int q = (ly >= kAnchor ? 2 : 0) + (lx >= kAnchor ? 1 : 0);
+    const int c0 = q * (kCornerSide * kCornerSide) + (ly & (kAnchor - 1)) * kCornerSide + (lx & (kAnchor - 1));
+    // pixel centre in the image frame (mm)
+    const float xc = ((float)ix - G.cxo) * G.dx, yc = ((float)iy - G.cyo) * G.dy;
     float rho = 1.0f;
     if (MODE == BP_SOLVE_UPDATE) rho = __ldcg(&S.rho_tab[__ldcg(&S.counter[0])]);
-    float acc0 = 0.0f, acc1 = 0.0f;
-    for (int k = 0; k < nviews; k++) {
+    // corner staging: corner c (and c + 256 for the first 68 threads) of view k into buffer b
+    auto stage = [&](int k, int b) {
         const int v = __ldg(&views[k]);
-        const float2 cs = __ldg(&G.view_cs[v]);
-        const Footprint F0 = pixel_footprint(G, v, cs.x, cs.y, ixc, iy0c);
-        const Footprint F1 = pixel_footprint(G, v, cs.x, cs.y, ixc, iy1c);
-        const float *row = sino + (size_t)k * G.ns;
-        acc0 += footprint_dot(F0, row, G.ns);
-        acc1 += footprint_dot(F1, row, G.ns);
+#pragma unroll
+        for (int rep = 0; rep < 2; rep++) {
+            const int c = threadIdx.x + rep * kBpFlyThreads;
+            if (c < kTileCorners) {
+                const int cq = c / (kCornerSide * kCornerSide), r = c - cq * (kCornerSide * kCornerSide);
+                const int cy = r / kCornerSide, cx = r - cy * kCornerSide;
+                const int atx = 2 * blockIdx.x + (cq & 1), aty = 2 * blockIdx.y + (cq >> 1);
+                if (atx < G.nax && aty < G.nay) {
+                    const Anchor A = load_anchor(G, v, aty * G.nax + atx);
+                    float Sv, Lv;
+                    point_u(G, A, (float)(cx - kAnchor / 2), (float)(cy - kAnchor / 2), Sv, Lv);
+                    s_c[b][c] = make_float2(Sv, Lv);
+                    if (r == 0) s_n[b][cq] = A.n;
+                }
+            }
+        }
+    };
+    float acc = 0.0f;
+    if (nviews > 0) stage(0, 0);
+    __syncthreads();
+    for (int k = 0; k < nviews; k++) {
+        const int b = k & 1;
+        if (k + 1 < nviews) stage(k + 1, b ^ 1);
+        if (inside) {
+            const int v = __ldg(&views[k]);
+            const float2 cs = __ldg(&G.view_cs[v]);
+            const float2 p0 = s_c[b][c0], p1 = s_c[b][c0 + 1];
+            const float2 p2 = s_c[b][c0 + kCornerSide], p3 = s_c[b][c0 + kCornerSide + 1];
+            const float Sk[4] = {p0.x, p1.x, p2.x, p3.x}, Lk[4] = {p0.y, p1.y, p2.y, p3.y};
+            // centre ray relative to the source (image frame): chord |c| / max(|c_x| / dx, |c_y| / dy)
+            const float cxv = fmaf(G.dso, cs.x, xc), cyv = fmaf(G.dso, cs.y, yc);
+            const float r2 = fmaf(cxv, cxv, cyv * cyv);
+            const float amp = __fdividef(r2 * rsqrtf(r2), fmaxf(fabsf(cxv) * G.inv_dx, fabsf(cyv) * G.inv_dy));
+            const Footprint F = footprint_from_corners(Sk, Lk, amp, s_n[b][q]);
+            acc += footprint_dot(F, sino + (size_t)k * G.ns, G.ns);
+        }
+        __syncthreads();
     }
-    bp_epilogue<MODE>(G, S, xo, ix, iy0, acc0, rho, scale, accumulate);
-    bp_epilogue<MODE>(G, S, xo, ix, iy1, acc1, rho, scale, accumulate);
+    if (inside) bp_epilogue<MODE>(G, S, xo, ix, iy, acc, rho, scale, accumulate);
     if (MODE == BP_SOLVE_UPDATE) {
         // the last block to finish advances the subiteration counter (rho for the next one)
         __syncthreads();
@@ -521,9 +561,9 @@ cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *v
         return cudaGetLastError();
     }
     switch (mode) {
-    case BP_PLAIN: bp_fan2d_kernel<BP_PLAIN><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
-    case BP_SOLVE_INIT: bp_fan2d_kernel<BP_SOLVE_INIT><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
-    default: bp_fan2d_kernel<BP_SOLVE_UPDATE><<<grid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+    case BP_PLAIN: bp_fan2d_kernel<BP_PLAIN><<<grid, kBpFlyThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+    case BP_SOLVE_INIT: bp_fan2d_kernel<BP_SOLVE_INIT><<<grid, kBpFlyThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+    default: bp_fan2d_kernel<BP_SOLVE_UPDATE><<<grid, kBpFlyThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
     }
     return cudaGetLastError();
 }
