@@ -170,6 +170,24 @@ __device__ __forceinline__ float ramp_correction(int K, float f, float eps, floa
     return c;
 }
 
+// ramp_correction with the voxel values around the boundary given: xm = x_{K-1}, x0 = x_K, xp = x_{K+1}.
+__device__ __forceinline__ float ramp_correction_w(int K, float f, float eps, float zb, float xm, float x0, float xp)
+{
+    float c = 0.0f;
+    const float h0 = eps * fabsf((float)K + zb);
+    if (f < h0) {
+        const float d = h0 - f;
+        c = (x0 - xm) * __fdividef(d * d, 4.0f * h0);
+    }
+    const float h1 = eps * fabsf((float)(K + 1) + zb);
+    const float g = 1.0f - f;
+    if (g < h1) {
+        const float d = h1 - g;
+        c = fmaf(xp - x0, __fdividef(d * d, 4.0f * h1), c);
+    }
+    return c;
+}
+
 // Detector-row boundary b (row coordinate b - 1/2) of a column, in voxel
 // coordinates z = K + f (voxel K spans [K, K+1], 0 <= f < 1):
 //   z = (b - 1/2 - ct0i + ofr) ia - zbi - zbf.
@@ -199,13 +217,6 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
     __shared__ int s_n[kHxWarps][32];
     __shared__ int s_part[kHxWarps];
     __shared__ float s_rc[NT];
-    __shared__ float4 s_ax[kHxWarps][32];   // staged column: ia_hi, ia_lo, a, ofr*ia - zbf
-    __shared__ int s_col[kHxWarps][32];     // staged column index iy * nx + ix
-    __shared__ int2 s_kr[kHxWarps][32];     // voxel range [kmin, kmax] its rows reach
-    __shared__ int s_k0[kHxWarps][32];      // lowest row boundary K + f
-    __shared__ float s_f0[kHxWarps][32];
-    __shared__ float2 s_eps[kHxWarps][TT ? 32 : 1];  // TT: the column's eps and its widest ramp (voxels)
-    __shared__ float s_xw[kHxWarps][64];    // z-window of the column being profiled
     extern __shared__ float4 s_dyn4[];
     float *s_p = reinterpret_cast<float *>(s_dyn4);  // [warp][32][PS] profiles; later [warp][NT][32] partial sums
     int *s_pre = reinterpret_cast<int *>(s_p + kHxWarps * 32 * PS);  // [nmax + 1] wedge columns before march index a
@@ -310,120 +321,70 @@ __global__ void __launch_bounds__(kHxWarps * 32, 5) fp_helix_kernel(FanDev G, He
             const float4 X = __ldg(&H.tile_ax[ai]);
             float eps;
             const ColumnAxial C = column_axial<TT>(H, A, X, cs.x, cs.y, ox, oy, G.dx, G.dy, eps);
-            if (TT) s_eps[warp][lane] = make_float2(eps, 0.0f);
             const float cz = fmaf(H.ofr, C.ia_hi + C.ia_lo, -zb.y);
             int K0, K1;
             float f0, f1;
             row_boundary(-0.5f - H.ct0i, C.ia_hi, C.ia_lo, zb.x, cz, nz, K0, f0);
             row_boundary((float)nt - 0.5f - H.ct0i, C.ia_hi, C.ia_lo, zb.x, cz, nz, K1, f1);
-            s_ax[warp][lane] = make_float4(C.ia_hi, C.ia_lo, C.a_hi + C.a_lo, cz);
-            s_col[warp][lane] = iy * G.nx + ix;
-            // (TT: one voxel more on each side, for the ramps at the outermost row boundaries)
-            s_kr[warp][lane] = TT ? make_int2(max(K0 - 1, 0), min(K1 + 1, nz - 1)) : make_int2(max(K0, 0), min(K1, nz - 1));
-            s_k0[warp][lane] = K0;
-            s_f0[warp][lane] = f0;
-            if (TT) {  // the widest ramp the column's row boundaries can meet (|z - z_src| is convex in K)
-                const float zbt = zb.x + zb.y;
-                s_eps[warp][lane].y = eps * fmaxf(fabsf((float)K0 + zbt), fabsf((float)(K1 + 1) + zbt));
+            // the widest ramp the column's row boundaries can meet (|z - z_src| is convex in K)
+            const float zbf = zb.x + zb.y;
+            const float hcol = TT ? eps * fmaxf(fabsf((float)K0 + zbf), fabsf((float)(K1 + 1) + zbf)) : 0.0f;
+            // the column's axial profile, its rows in order:
+            // p_r = a * sum_k x_k |[k, k+1] ∩ [z(r - 1/2), z(r + 1/2)]|, each row boundary placed exactly
+            // (row_boundary), the voxels read from the column's contiguous z-run (L1); TT adds at every
+            // row boundary the ramp corrections, + to the row below, - to the row above
+            const float4 P = make_float4(C.ia_hi, C.ia_lo, C.a_hi + C.a_lo, cz);
+            const float *xg = x + ((size_t)iy * G.nx + ix) * nz;
+            auto xv = [&](int kk) -> float {
+                if (kk < 0 || kk >= nz) return 0.0f;
+                return (MODE == FP_ONES_W) ? 1.0f : __ldg(&xg[kk]);
+            };
+            const float eps_l = eps;
+            int Kl = K0;
+            float fl = f0;
+            // voxels Kl - 1 .. Kl + 2 of the column in registers (0 outside the volume): the rows walk up
+            // the column, so a row's voxels and the ramp corrections at its upper boundary come from the
+            // window, and the one new voxel a shift by one needs is loaded a row before it is used
+            float w0 = xv(Kl - 1), w1 = xv(Kl), w2 = xv(Kl + 1), w3 = xv(Kl + 2);
+            float cl = TT ? ramp_correction_w(Kl, fl, eps_l, zbf, w0, w1, w2) : 0.0f;
+            float *pl = sp + lane * PS;
+            for (int r = 0; r < nt; r++) {
+                int Kh;
+                float fh;
+                row_boundary((float)r + 0.5f - H.ct0i, P.x, P.y, zb.x, P.w, nz, Kh, fh);
+                // this row: voxels Kl .. Kh, the first from fl, the last to fh
+                const int d = Kh - Kl;
+                const float c1 = d == 0 ? fh - fl : 1.0f - fl;
+                const float c2 = d == 1 ? fh : (d >= 2 ? 1.0f : 0.0f);
+                const float c3 = d == 2 ? fh : (d >= 3 ? 1.0f : 0.0f);
+                float rs = fmaf(w1, c1, fmaf(w2, c2, w3 * c3));
+                if (d >= 3) {  // a row spanning more than three voxels
+                    for (int kk = Kl + 3; kk < Kh; kk++) rs += xv(kk);
+                    rs = fmaf(xv(Kh), fh, rs);
+                }
+                // shift the window to Kh - 1 .. Kh + 2
+                if (d == 1) {
+                    w0 = w1; w1 = w2; w2 = w3; w3 = xv(Kh + 2);
+                } else if (d == 2) {
+                    w0 = w2; w1 = w3; w2 = xv(Kh + 1); w3 = xv(Kh + 2);
+                } else if (d != 0) {
+                    w0 = xv(Kh - 1); w1 = xv(Kh); w2 = xv(Kh + 1); w3 = xv(Kh + 2);
+                }
+                float sacc = rs;
+                if (TT) {
+                    const float ch = (fminf(fh, 1.0f - fh) < hcol) ? ramp_correction_w(Kh, fh, eps_l, zbf, w0, w1, w2) : 0.0f;
+                    sacc += ch - cl;
+                    cl = ch;
+                }
+                pl[r] = P.z * sacc;
+                Kl = Kh;
+                fl = fh;
             }
+            for (int r = nt; r < NT; r++) pl[r] = 0.0f;  // rows the float4 reads below cover
         }
         scf[lane] = cf;
         sns[lane] = cnt;
         __syncwarp();
-        // axial profiles of the staged columns: the warp loads each column's z-window
-        // (coalesced, one column ahead) into shared memory and lane r forms row r:
-        // p_r = a * sum_k x_k |[k, k+1] ∩ [z(r - 1/2), z(r + 1/2)]|
-        {
-            float xn0 = 0.0f, xn1 = 0.0f;
-            auto fetch = [&](int l, float &v0, float &v1) {
-                const int2 kr = s_kr[warp][l];
-                const float *xc = x + (size_t)s_col[warp][l] * nz;
-                const int k0 = kr.x + lane, k1 = kr.x + 32 + lane;
-                v0 = (k0 <= kr.y) ? __ldg(&xc[k0]) : 0.0f;
-                v1 = (k1 <= kr.y) ? __ldg(&xc[k1]) : 0.0f;
-            };
-            if (MODE != FP_ONES_W && n > 0) fetch(0, xn0, xn1);
-            for (int l = 0; l < n; l++) {
-                const float xc0 = xn0, xc1 = xn1;
-                if (MODE != FP_ONES_W && l + 1 < n) fetch(l + 1, xn0, xn1);
-                const float4 P = s_ax[warp][l];
-                const int2 kr = s_kr[warp][l];
-                float *pl = sp + l * PS;
-                if (MODE != FP_ONES_W) {
-                    s_xw[warp][lane] = xc0;
-                    s_xw[warp][32 + lane] = xc1;
-                }
-                __syncwarp();
-                int Kc = s_k0[warp][l];
-                float fc = s_f0[warp][l];
-                const float *xw = s_xw[warp] - kr.x;
-                // TT: x_k of this column for the ramp corrections (0 outside the volume)
-                const float *xg_l = x + (size_t)s_col[warp][l] * nz;
-                auto xv = [&](int kk) -> float {
-                    if (kk < 0 || kk >= nz) return 0.0f;
-                    if (MODE == FP_ONES_W) return 1.0f;
-                    return (kk >= kr.x && kk <= kr.y && kk - kr.x < 64) ? xw[kk] : __ldg(&xg_l[kk]);
-                };
-                const float eps_l = TT ? s_eps[warp][TT ? l : 0].x : 0.0f;
-                const float hcol = TT ? s_eps[warp][TT ? l : 0].y : 0.0f;
-                const float zbf = zb.x + zb.y;
-                float corr_c = TT ? ramp_correction(Kc, fc, eps_l, zbf, xv) : 0.0f;
-#pragma unroll
-                for (int r0 = 0; r0 < NT; r0 += 32) {
-                    const int r = r0 + lane;
-                    int Kh;
-                    float fh;
-                    row_boundary((float)r + 0.5f - H.ct0i, P.x, P.y, zb.x, P.w, nz, Kh, fh);
-                    int Kl = __shfl_up_sync(kFull, Kh, 1);
-                    float fl = __shfl_up_sync(kFull, fh, 1);
-                    if (lane == 0) {
-                        Kl = Kc;
-                        fl = fc;
-                    }
-                    Kc = __shfl_sync(kFull, Kh, 31);
-                    fc = __shfl_sync(kFull, fh, 31);
-                    float sacc = 0.0f;
-                    if (TT) {  // + the ramps at the row's upper boundary, - those at its lower one
-                        const bool near = fminf(fh, 1.0f - fh) < hcol;  // only then can a ramp straddle it
-                        const float ch = near ? ramp_correction(Kh, fh, eps_l, zbf, xv) : 0.0f;
-                        if (__any_sync(kFull, near) || corr_c != 0.0f) {
-                            float cl = __shfl_up_sync(kFull, ch, 1);
-                            if (lane == 0) cl = corr_c;
-                            corr_c = __shfl_sync(kFull, ch, 31);
-                            sacc = ch - cl;
-                        }
-                    }
-                    if (r < nt && Kh >= 0 && Kl < nz) {
-                        const int k0 = max(Kl, 0), k1 = min(Kh, nz - 1);
-                        const float g0 = Kl < 0 ? 0.0f : fl, g1 = Kh >= nz ? 1.0f : fh;
-                        float rs;
-                        if (MODE == FP_ONES_W) {
-                            rs = (float)(k1 - k0) + (g1 - g0);
-                        } else if (k1 - kr.x < 64) {
-                            if (k0 == k1) {
-                                rs = xw[k0] * (g1 - g0);
-                            } else {
-                                rs = xw[k0] * (1.0f - g0);
-                                for (int kk = k0 + 1; kk < k1; kk++) rs += xw[kk];
-                                rs = fmaf(xw[k1], g1, rs);
-                            }
-                        } else {  // a row beyond the staged 64-voxel window
-                            const float *xg = x + (size_t)s_col[warp][l] * nz;
-                            if (k0 == k1) {
-                                rs = __ldg(&xg[k0]) * (g1 - g0);
-                            } else {
-                                rs = __ldg(&xg[k0]) * (1.0f - g0);
-                                for (int kk = k0 + 1; kk < k1; kk++) rs += __ldg(&xg[kk]);
-                                rs = fmaf(__ldg(&xg[k1]), g1, rs);
-                            }
-                        }
-                        sacc += rs;
-                    }
-                    if (r < NT) pl[r] = P.z * sacc;
-                }
-                __syncwarp();
-            }
-        }
         // cell role: add weight x profile of every staged column this lane's wedge crosses
         const int lmax = __shfl_sync(kFull, ls, n - 1);
         for (int l = 0; l <= lmax; l++) {
