@@ -300,7 +300,9 @@ ct_status ct_relaxed_oslalm_solve(const ct_geom *g, const float *y, const float 
  * the same total in every report.  geoms, y, w, x_inout: host
  * arrays of nslices pointers (device data as in ct_relaxed_oslalm_solve;
  * slices may share a geometry); params: host array of nslices parameter
- * sets (stop_rmsd_hu is ignored: every slice runs n_iter iterations);
+ * sets (a slice with x_ref and stop_rmsd_hu > 0 stops at the end of the
+ * first outer iteration whose RMSD is at or below it, as in
+ * ct_relaxed_oslalm_solve; the others run n_iter iterations);
  * reports: optional host array of nslices reports, whose per-iteration times
  * come from the device clock at each slice's iteration ends.  Allocates one
  * device arena per call for the batched slices; a large slice's solve

@@ -4,7 +4,9 @@
 // solved together in ONE persistent cooperative launch.
 //
 // All slices advance in lockstep super-steps t = 0, 1, ...: slice i runs its
-// subiteration t while t < n_iter * M_i.  Each super-step has three phases,
+// subiteration t while t < n_iter * M_i, or until an outer iteration ends with
+// its RMSD to x_ref at or below its stopping tolerance (the slice then leaves
+// the launch; the launch ends when every slice has).  Each super-step has three phases,
 // separated by a grid barrier, and the work units of every active slice are
 // spread over all CTAs:
 //   A. regularizer + x-update (256-pixel chunks); also, for slices that just
@@ -44,6 +46,8 @@ struct BatchSlice {
     const float *rho;    // [T]
     double *rmsd_acc;    // [n_iter][2]: sum of squares, count (FOV)
     unsigned long long *stamp;  // [n_iter] %globaltimer at the end of each outer iteration
+    int *done_at;        // 0 while running; t + 1 once the slice stopped at super-step t (RMSD <= stop_hu)
+    float stop_hu, hu;   // stopping tolerance (HU; 0: run all iterations) and HU per unit of x
     Pot P;
     float alpha, beta, r2max;
     int M, T, n_iter, nonneg, algorithm;
@@ -182,6 +186,25 @@ __device__ void rmsd_units(const BatchSlice &B, int iter, int chunk)
     }
 }
 
+// Whether the RMSD of slice B to x_ref at the end of the outer iteration that subiteration t - 1 closed
+// is at or below the slice's stopping tolerance (its sums are complete: the atomics of phase A precede a
+// grid barrier).
+__device__ __forceinline__ bool at_tol(const BatchSlice &B, int t)
+{
+    if (!(B.stop_hu > 0.0f) || t <= 0 || t > B.T || (t % B.M) != 0) return false;
+    const int it = t / B.M - 1;
+    const double c = __ldcg(&B.rmsd_acc[2 * it + 1]);
+    return c > 0.0 && sqrt(__ldcg(&B.rmsd_acc[2 * it]) / c) * (double)B.hu <= (double)B.stop_hu;
+}
+
+// Whether slice B stopped before or at super-step t (done_at is written in phase B of the stopping
+// super-step and read after later barriers).
+__device__ __forceinline__ bool stopped(const BatchSlice &B, int t)
+{
+    const int d = __ldcg(B.done_at);
+    return d != 0 && d - 1 <= t;
+}
+
 __global__ void __launch_bounds__(kThreads, 5) batched_kernel(const BatchSlice *__restrict__ SL, int nsl, int Tmax,
                                                              BatchCtl *ctl)
 {
@@ -194,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 5) batched_kernel(const BatchSlice *
             // slices whose outer iteration ended with subiteration t-1
             auto ended = [&](int s) {
                 const BatchSlice &B = SL[s];
-                return t > 0 && t <= B.T && (t % B.M) == 0;
+                return t > 0 && t <= B.T && (t % B.M) == 0 && !stopped(B, t - 1);
             };
             if (blockIdx.x == 0 && threadIdx.x < 32) {
                 for (int s = lane; s < nsl; s += 32)
@@ -204,9 +227,10 @@ __global__ void __launch_bounds__(kThreads, 5) batched_kernel(const BatchSlice *
                 const BatchSlice &B = SL[s];
                 const int chunks = (B.G.nx * B.G.ny + kThreads - 1) / kThreads;
                 const int rm = (ended(s) && B.x_ref) ? chunks : 0;
-                const int k1 = (t < B.T) ? chunks : 0;
+                const int k1 = (t < B.T && !stopped(B, t)) ? chunks : 0;
                 return rm + k1;
             });
+            if (total == 0) break;  // every slice has stopped (all CTAs see the same state)
             for (int u = blockIdx.x; u < total; u += gridDim.x) {
                 const int s = find_slice(s_pre, nsl, u);
                 const BatchSlice &B = SL[s];
@@ -242,9 +266,13 @@ __global__ void __launch_bounds__(kThreads, 5) batched_kernel(const BatchSlice *
         if (!grid_barrier(ctl)) return;
         // ---- phase B: subset forward projection with the weighted residual (one warp per ray)
         {
+            // slices whose iteration that just ended met their tolerance stop here
+            if (blockIdx.x == 0)
+                for (int s = threadIdx.x; s < nsl; s += kThreads)
+                    if (!stopped(SL[s], t) && at_tol(SL[s], t)) *SL[s].done_at = t + 1;
             const int total = build_prefix(s_pre, nsl, [&](int s) {
                 const BatchSlice &B = SL[s];
-                if (t >= B.T) return 0;
+                if (t >= B.T || stopped(B, t) || at_tol(B, t)) return 0;
                 const int m = t % B.M;
                 const int rays = (B.sub_off[m + 1] - B.sub_off[m]) * B.G.ns;
                 return (rays + 7) / 8;
@@ -282,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 5) batched_kernel(const BatchSlice *
         {
             const int total = build_prefix(s_pre, nsl, [&](int s) {
                 const BatchSlice &B = SL[s];
-                return (t < B.T) ? B.G.ntx * B.G.nty : 0;
+                return (t < B.T && !stopped(B, t) && !at_tol(B, t)) ? B.G.ntx * B.G.nty : 0;
             });
             for (int u = blockIdx.x; u < total; u += gridDim.x) {
                 const int s = find_slice(s_pre, nsl, u);
@@ -407,7 +435,7 @@ ct_status persistent_batch(const ct_geom *const *geoms, const float *const *y, c
         off[i] = total;
         total += al256(npix * 8) + al256(npix * 4) * 3 + al256((size_t)max_sub * g->fan.ns * 4) + al256((size_t)g->fan.na * 4) +
                  al256((size_t)(p->M + 1) * 4) + al256((size_t)T * 4) + al256((size_t)p->n_iter * 16) +
-                 al256((size_t)p->n_iter * 8);
+                 al256((size_t)p->n_iter * 8) + al256(4);
     }
     const size_t desc_off = total;
     total += al256(sizeof(BatchSlice) * nslices) + al256(sizeof(BatchCtl));
@@ -457,7 +485,10 @@ ct_status persistent_batch(const ct_geom *const *geoms, const float *const *y, c
         int *sub = (int *)b; b += al256((size_t)(M + 1) * 4);
         float *rho = (float *)b; b += al256((size_t)T * 4);
         B.rmsd_acc = (double *)b; b += al256((size_t)p->n_iter * 16);
-        B.stamp = (unsigned long long *)b;
+        B.stamp = (unsigned long long *)b; b += al256((size_t)p->n_iter * 8);
+        B.done_at = (int *)b;
+        B.stop_hu = p->x_ref ? p->stop_rmsd_hu : 0.0f;
+        B.hu = p->hu_per_unit;
         B.y = y[i];
         B.w = w[i];
         B.x_ref = p->x_ref;
@@ -560,13 +591,15 @@ ct_status persistent_batch(const ct_geom *const *geoms, const float *const *y, c
             CT_CUDA_TRY(cudaMemcpy(acc.data(), hs[i].rmsd_acc, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost), "read");
             CT_CUDA_TRY(cudaMemcpy(st.data(), hs[i].stamp, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost),
                         "read");
+            int done_at = 0;
+            CT_CUDA_TRY(cudaMemcpy(&done_at, hs[i].done_at, sizeof(int), cudaMemcpyDeviceToHost), "read");
             ct_solve_report *r = &reports[i];
-            r->iters_done = n;
+            r->iters_done = done_at ? (done_at - 1) / p->M : n;
             r->seconds = ms_all * 1e-3;
             r->seconds_to_tol = -1.0;
             r->rmsd_hu_last = -1.0f;
             const float tol = p->stop_rmsd_hu > 0.0f ? p->stop_rmsd_hu : 1.0f;
-            for (int k = 0; k < n; k++) {
+            for (int k = 0; k < r->iters_done; k++) {
                 const double tk = ms_setup * 1e-3 + (double)(st[k] - hctl.t_start) * 1e-9;
                 if (r->iter_seconds) r->iter_seconds[k] = tk;
                 if (p->x_ref) {
@@ -595,7 +628,7 @@ constexpr long kSoloPixels = 384L * 384L;
 void fill_solo_report(ct_solve_report *r, const ct_solve_params *p, const ct_solve_report &got,
                       const std::vector<float> &trace, const std::vector<double> &times, double t0)
 {
-    const int n = p->n_iter;
+    const int n = got.iters_done;
     const float tol = p->stop_rmsd_hu > 0.0f ? p->stop_rmsd_hu : 1.0f;
     r->iters_done = n;
     r->seconds_to_tol = -1.0;
@@ -645,7 +678,6 @@ extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms
     double t_total = 0.0;  // device time of the slices solved so far
     for (int i : solo) {
         ct_solve_params q = params[i];
-        q.stop_rmsd_hu = 0.0f;  // every slice runs n_iter iterations
         std::vector<float> trace(q.n_iter);
         std::vector<double> times(q.n_iter);
         ct_solve_report got{};
@@ -680,7 +712,7 @@ extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms
                 ct_solve_report *r = &reports[shared[k]];
                 *r = rs[k];
                 if (r->iter_seconds)
-                    for (int it = 0; it < ps[k].n_iter; it++) r->iter_seconds[it] += t_total;
+                    for (int it = 0; it < r->iters_done; it++) r->iter_seconds[it] += t_total;
                 if (r->seconds_to_tol >= 0.0) r->seconds_to_tol += t_total;
             }
         }

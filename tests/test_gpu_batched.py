@@ -194,3 +194,44 @@ def test_grid_barrier_wait_runs_out_and_context_survives():
     with pytest.raises(ct.CTError) as e:
         ct.ct_debug_barrier(-1, 0)
     assert e.value.status == ct.CT_EINVAL
+
+
+def test_batched_slices_stop_at_their_tolerance():
+    """With x_ref and stop_rmsd_hu each slice leaves the persistent launch at the end of its first outer
+    iteration at the tolerance, as the single-slice solver stops: same iteration count, same image."""
+    from paper_1512_04564_gb300 import ct
+
+    probs, Gs = [], {}
+    for seed, nx, ns, na, dx, M, resident in CASES:
+        key = (nx, ns, na, dx)
+        g, y, w = _problem(seed, nx, ns, na, dx)
+        if key not in Gs:
+            Gs[key] = ct.Geometry.from_fan(g)
+            if resident:
+                ct.ct_geom_precompute(Gs[key])
+        probs.append((g, Gs[key], torch.from_numpy(y).cuda(), torch.from_numpy(w).cuda(), M))
+    refs, params, singles = [], [], []
+    for g, G, y, w, M in probs:
+        xr = torch.zeros(g.ny, g.nx, device="cuda")
+        ct.ct_relaxed_oslalm_solve(G, y, w, xr, M=1, n_iter=30, alpha=1.999, beta=BETA, delta=DELTA)
+        # a tolerance each slice first meets at iteration 3: between its single-slice RMSD after iterations
+        # 2 and 3 (far from both, so both solvers stop at the same iteration)
+        x0 = torch.zeros(g.ny, g.nx, device="cuda")
+        tr = ct.ct_relaxed_oslalm_solve(G, y, w, x0, M=M, n_iter=12, alpha=1.999, beta=BETA, delta=DELTA, x_ref=xr,
+                                        hu_per_unit=HU)["rmsd_trace_hu"]
+        assert tr[0] > tr[1] > tr[2] + 0.1, tr[:3]
+        tol = 0.5 * (tr[1] + tr[2])
+        p = dict(M=M, n_iter=12, alpha=1.999, beta=BETA, delta=DELTA, x_ref=xr, hu_per_unit=HU, stop_rmsd_hu=tol)
+        xs = torch.zeros(g.ny, g.nx, device="cuda")
+        singles.append((xs, ct.ct_relaxed_oslalm_solve(G, y, w, xs, **p)))
+        params.append(p)
+    xb = [torch.zeros(g.ny, g.nx, device="cuda") for g, *_ in probs]
+    reps = ct.ct_relaxed_oslalm_solve_batched([p[1] for p in probs], [p[2] for p in probs], [p[3] for p in probs],
+                                              xb, params)
+    torch.cuda.synchronize()
+    for i, (g, *_rest) in enumerate(probs):
+        xs, rs = singles[i]
+        assert rs["iters_done"] == 3
+        assert reps[i]["iters_done"] == 3, (i, reps[i]["iters_done"])
+        assert reps[i]["rmsd_trace_hu"][-1] <= params[i]["stop_rmsd_hu"] and reps[i]["seconds_to_tol"] > 0
+        assert _hu_rmsd(xb[i].cpu().numpy(), xs.cpu().numpy(), g) <= 0.01, i

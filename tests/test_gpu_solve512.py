@@ -17,6 +17,8 @@ Eq. (ct_problem); Algorithm 1 of Sec. III-A).
   follows the oracle within 0.1 HU over the first two iterations.
 """
 
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -105,3 +107,25 @@ def test_named_subset_count_diverges_in_the_oracle(problem, geoms):
         xg = _gpu_iterate(ct, geoms["resident_matrix"], problem, 41, 1.999, k)
         d = osolver.rmsd_hu(xg, xs[k - 1], problem["mask"], c.hu_per_unit)
         assert d <= TOL_HU, (k, d)
+
+
+def test_converged_solution_matches_the_oracles_xstar(problem, geoms):
+    """x* of the workload: the GPU's (2000 iterations of relaxed LALM with one subset, the benchmark's
+    reference) against the oracle's own, stored by oracle/xstar.py (FBP, 20 iterations of M = 20, 400 of
+    M = 1, KKT residual RMS 3e-6 HU).  The PWLS minimizer is unique, so both must agree."""
+    from oracle import xstar as oxstar
+    from paper_1512_04564_gb300 import ct
+
+    c = problem["c"]
+    p = oxstar.path_for(c.name, c.seed)
+    if not os.path.exists(p):
+        pytest.skip("no stored oracle x*")
+    xo = np.load(p).astype(np.float64)
+    x = torch.zeros(problem["g"].ny, problem["g"].nx, device="cuda")
+    ct.ct_relaxed_oslalm_solve(geoms["resident_matrix"], torch.from_numpy(problem["y"]).cuda(),
+                               torch.from_numpy(problem["w"]).cuda(), x, M=1, n_iter=2000, alpha=1.999,
+                               beta=c.beta_per_mm, delta=c.delta, potential=c.potential)
+    torch.cuda.synchronize()
+    d = osolver.rmsd_hu(x.cpu().numpy().astype(np.float64), xo, problem["mask"], c.hu_per_unit)
+    print(f"x*: GPU vs oracle RMSD {d:.4f} HU")
+    assert d <= TOL_HU, d
