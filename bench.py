@@ -314,15 +314,23 @@ def batch_result(args, n_iter=100):
         b_tol.append(max(ttol) if all(t > 0 for t in ttol) else None)
         b_all.append(reps[0]["seconds"])
     # loop of single-slice solves (same parameters, CUDA-graph solver), each stopping at the tolerance
-    l_tol = []
+    l_tol, l_small = [], []
+    solo = [i for i, (g, _, _, _) in enumerate(slices) if g.nx * g.ny >= 384 * 384]
     for _ in range(steps):
-        tot, ok = 0.0, True
+        tot, small, ok = 0.0, 0.0, True
         for i in range(n):
             x = torch.zeros_like(xst[i])
             r = ct.ct_relaxed_oslalm_solve(G_l[i], ys[i], ws[i], x, **params[i])
             ok = ok and r["seconds_to_tol"] > 0
-            tot += r["seconds_to_tol"] if r["seconds_to_tol"] > 0 else r["seconds"]
+            ti = r["seconds_to_tol"] if r["seconds_to_tol"] > 0 else r["seconds"]
+            tot += ti
+            if i not in solo:
+                small += ti
         l_tol.append(tot if ok else None)
+        l_small.append(small)
+    # the batched call's parts: the large slices alone first, then one persistent launch for the rest
+    solo_end = max((reps[i]["seconds_to_tol"] for i in solo), default=0.0)
+    shared_end = max((reps[i]["seconds_to_tol"] for i in range(n) if i not in solo), default=0.0)
     reached = sum(1 for r in reps if r["seconds_to_tol"] > 0)
     short = [{"slice": i, "image": slices[i][0].nx, "bins": slices[i][0].ns, "views": slices[i][0].na, "M": Ms[i],
               "min_rmsd_hu": round(min(r["rmsd_trace_hu"]), 3), "last_rmsd_hu": round(r["rmsd_trace_hu"][-1], 3),
@@ -345,6 +353,10 @@ def batch_result(args, n_iter=100):
         "batched_seconds_to_all_at_tol": bt, "loop_seconds_to_all_at_tol": lt,
         "batched_over_loop": (bt / lt) if bt and lt else None,
         "batched_seconds_full_call": statistics.mean(b_all),
+        "parts": {"large_slices": len(solo), "batched_large_alone_s": solo_end,
+                  "batched_persistent_launch_s": shared_end - solo_end,
+                  "loop_small_slices_s": statistics.mean(l_small),
+                  "loop_large_slices_s": (statistics.mean(l_tol) - statistics.mean(l_small)) if lt else None},
         "geometries": len(geoms), "resident_matrix_bytes": mat_bytes, "geometry_setup_s": round(t_geo, 3),
         "autotuned": tuned, "xstar_seconds": round(t_xstar, 2), "steps": steps,
     }

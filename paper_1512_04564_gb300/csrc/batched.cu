@@ -186,6 +186,35 @@ __device__ void rmsd_units(const BatchSlice &B, int iter, int chunk)
     }
 }
 
+// The on-the-fly projector paths of a slice without a resident matrix, out of line: inlined, their
+// footprint arithmetic would cost the resident-matrix paths of the same phases their registers.
+// Lane `lane` of a warp's share of ray (v, sc): sum over the wedge pixels it visits of a_ij x_j.
+__device__ __noinline__ float fly_ray_part(const BatchSlice &B, int v, int sc, int lane)
+{
+    const float2 cs = __ldg(&B.G.view_cs[v]);
+    float acc = 0.0f;
+    ray_visit(B.G, v, sc, lane, 32, [&](int ix, int iy) {
+        const float xv = __ldcg(&B.x_new[(size_t)iy * B.G.nx + ix]);
+        if (xv == 0.0f) return;
+        const Footprint F = pixel_footprint(B.G, v, cs.x, cs.y, ix, iy);
+        acc = fmaf(cell_weight(F, sc), xv, acc);
+    });
+    return acc;
+}
+
+// sum over the subset's views v0 .. v0 + nv - 1 of pixel (ix, iy)'s footprint against the residual rows.
+__device__ __noinline__ float fly_pixel_back(const BatchSlice &B, int v0, int nv, int ix, int iy)
+{
+    float acc = 0.0f;
+    for (int k = 0; k < nv; k++) {
+        const int v = B.perm[v0 + k];
+        const float2 cs = __ldg(&B.G.view_cs[v]);
+        const Footprint F = pixel_footprint(B.G, v, cs.x, cs.y, ix, iy);
+        acc += footprint_dot_coherent(F, B.resid + (size_t)k * B.G.ns, B.G.ns);
+    }
+    return acc;
+}
+
 // Whether the RMSD of slice B to x_ref at the end of the outer iteration that subiteration t - 1 closed
 // is at or below the slice's stopping tolerance (its sums are complete: the atomics of phase A precede a
 // grid barrier).
@@ -292,13 +321,7 @@ __global__ void __launch_bounds__(kThreads, 5) batched_kernel(const BatchSlice *
                     acc = csr_ray_dot<false, true>(B.G, B.G.row_ptr[ri], B.G.row_ptr[ri + 1], B.G.row_first[ri],
                                                    B.x_new, lane);
                 } else {
-                    const float2 cs = __ldg(&B.G.view_cs[v]);
-                    ray_visit(B.G, v, sc, lane, 32, [&](int ix, int iy) {
-                        const float xv = __ldcg(&B.x_new[(size_t)iy * B.G.nx + ix]);
-                        if (xv == 0.0f) return;
-                        const Footprint F = pixel_footprint(B.G, v, cs.x, cs.y, ix, iy);
-                        acc = fmaf(cell_weight(F, sc), xv, acc);
-                    });
+                    acc = fly_ray_part(B, v, sc, lane);
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -349,12 +372,7 @@ __global__ void __launch_bounds__(kThreads, 5) batched_kernel(const BatchSlice *
                             acc += record_dot<true>(w, b, row, B.G.ns);
                     }
                 } else {
-                    for (int k = 0; k < nv; k++) {
-                        const int v = B.perm[v0 + k];
-                        const float2 cs = __ldg(&B.G.view_cs[v]);
-                        const Footprint F = pixel_footprint(B.G, v, cs.x, cs.y, ixc, iyc);
-                        acc += footprint_dot_coherent(F, B.resid + (size_t)k * B.G.ns, B.G.ns);
-                    }
+                    acc = fly_pixel_back(B, v0, nv, ixc, iyc);
                 }
                 if (ix >= B.G.nx || iy >= B.G.ny) continue;
                 const size_t j = (size_t)iy * B.G.nx + ix;

@@ -11,7 +11,9 @@
 //     tensor-memory accumulator and commits them to the slice's mbarrier;
 //   * the epilogue reads the accumulator rows (warp w owns rows 32w..32w+31)
 //     16 columns at a time and hands them to the loader's store().
-// Every mbarrier wait is bounded (error flag, no hang).
+// Every mbarrier wait is bounded (error flag, no hang); after a wait gives up no
+// more MMAs are issued, and the tensor memory is freed only once a final commit
+// shows the MMAs already issued complete (that wait bounded too).
 #pragma once
 
 #include "tc.cuh"
@@ -24,7 +26,8 @@ struct GemmSmem {
     static constexpr int kA = 128 * kStageK * 2;
     static constexpr int kB = NT * kStageK * 2;
     static constexpr int kStage = kA + kB;
-    static constexpr int kBytes = ST * kStage + 64 + 1024;  // + barriers, TMEM slot, alignment slack
+    static constexpr int kBytes = ST * kStage + 64 + 1024;  // + barriers, TMEM slot, abort flag, drain barrier,
+                                                            // alignment slack
 };
 
 // Pipeline depth: two stages, so that four CTAs (16 warps) share an SM; three or four stages (two CTAs
@@ -42,12 +45,14 @@ __global__ void __launch_bounds__(128) gemm_kernel(Ld L, int k_steps, int *err)
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + ST * S::kStage);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + ST);
     int *sabort = reinterpret_cast<int *>(bar + ST + 1);
+    uint64_t *drain = bar + ST + 2;  // completion of every MMA issued (the give-up path)
     const int tid = threadIdx.x, warp = tid >> 5;
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * NT;
     const uint32_t sbase = smem_u32(base);
     if (warp == 0) tmem_alloc(tslot, NT);
     if (tid == 0) {
         for (int b = 0; b < ST; b++) mbar_init(&bar[b], 1);
+        mbar_init(drain, 1);
         *sabort = 0;
         fence_mbar_init();
     }
@@ -89,7 +94,15 @@ __global__ void __launch_bounds__(128) gemm_kernel(Ld L, int k_steps, int *err)
     }
     // the last slice's MMAs complete the accumulator (tcgen05 MMAs complete in order)
     const int last = k_steps - 1;
-    const bool ok = mbar_wait(&bar[last % ST], (last / ST) & 1, err) && !*sabort;
+    if (!*sabort && !mbar_wait(&bar[last % ST], (last / ST) & 1, err)) *sabort = 1;
+    __syncthreads();
+    const bool ok = !*sabort;
+    if (!ok) {
+        // a wait gave up: before the tensor memory is freed, wait (bounded again) for every MMA thread 0
+        // issued, tracked by one more commit; the accumulator is not read
+        if (tid == 0) mma_commit(drain);
+        mbar_wait(drain, 0, err);
+    }
     fence_after_sync();
     if (ok) {
         const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
