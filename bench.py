@@ -511,10 +511,12 @@ def run_helix(args):
     # the named subset count, and fewer subsets (a lower ordered-subsets limit cycle)
     Ms = [args.M] if args.M else [cfg.M, cfg.M // 2, cfg.M // 4]
 
+    fbp0 = args.x0 == "fbp"  # the rebinned slice-by-slice FBP (timed inside the solve), or zeros
+
     def solve(M):
         x = torch.zeros(shape, device="cuda")
         return ct.ct_relaxed_oslalm_solve(G, y, w, x, M=M, n_iter=n_iter, alpha=alpha, x_ref=xstar, hu_per_unit=hu,
-                                          **common)
+                                          init_fbp=fbp0, **common)
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     runs = {}
@@ -551,7 +553,7 @@ def run_helix(args):
                    "detector": [g.nt, g.ns], "views": g.na, "turns": g.orbit_deg / 360.0, "pitch": g.pitch,
                    "axial": args.axial,
                    "alpha": alpha, "n_iter": n_iter, "n_iter_named": cfg.n_iter, "M_named": cfg.M, "M_best": best,
-                   "x0": "zeros",
+                   "x0": "rebinned FBP" if fbp0 else "zeros",
                    "beta_water_units": cfg.beta, "xstar": f"40 its M={m_warm} + {args.xstar_iters_helix} its M=1",
                    "xstar_kkt_rms_hu": kkt, "l2": "flushed (256 MB write) between steps",
                    "data_generation_s": round(t_data, 2)},

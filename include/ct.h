@@ -206,8 +206,16 @@ enum { CT_FBP_RAMP = 0, CT_FBP_HANN = 1 };
  * (window CT_FBP_RAMP, or CT_FBP_HANN for its Hann-apodised version),
  * distance-weighted back-projection with linear interpolation.  y: device
  * [na][ns] line integrals; x: device [ny][nx] output (same units per mm).
- * Uses the geometry's sinogram workspace.  Errors: CT_EINVAL, CT_ENOTSUP
- * (orbit other than 360 degrees, or ns > 19,000), CT_ECUDA. */
+ * A helical geometry (no helical FBP is given in the paper; a reading):
+ * y is [na][nt][ns], x the [nz][ny][nx] volume, and each slice is the
+ * fan-beam FBP of its single-slice rebinning: the turn of views whose
+ * source heights are centred on the slice, from each view the detector row
+ * where the slice's height at the isocentre projects (linear between rows,
+ * times the cosine of that row's cone angle); the scan must span at least
+ * one turn with a whole number of views per turn.  Uses the geometry's
+ * sinogram workspace.  Errors: CT_EINVAL, CT_ENOTSUP (a 2-D orbit other than
+ * 360 degrees, a helical scan without whole turns, or ns > 19,000),
+ * CT_ECUDA. */
 ct_status ct_fbp(const ct_geom *g, const float *y, float *x, int window, void *stream);
 
 enum { CT_POT_HYPERBOLA = 0, CT_POT_FAIR = 1, CT_POT_QUADRATIC = 2 };
@@ -280,7 +288,9 @@ typedef struct {
  *   h+ = alpha (D_L x+ - zeta) + (1-alpha) h; rho <- rho_{k}(alpha).
  * y, w: device [na][ns] sinogram and weights (w >= 0).  x_inout: device
  * [ny][nx], the initial image on entry (or the FBP of y when init_fbp = 1,
- * which needs a 360-degree scan) and the result on return.  The solve
+ * which needs a 360-degree scan; for a helical geometry the rebinned
+ * slice-by-slice FBP of ct_fbp, which needs whole turns) and the result on
+ * return.  The solve
  * runs on `stream` as CUDA-graph replays of one outer iteration and
  * synchronises the stream before returning.  Errors: CT_EINVAL, CT_ENOMEM,
  * CT_ECUDA. */

@@ -312,7 +312,8 @@ def ct_sqs_diag_noalloc(geom: Geometry, w: torch.Tensor, d_l: torch.Tensor, stre
 
 
 def ct_fbp(geom: Geometry, y: torch.Tensor, x: torch.Tensor, window: str = "hann", stream=None) -> torch.Tensor:
-    """Full-scan equiangular fan-beam FBP (initial image of Algorithm 1)."""
+    """Full-scan equiangular fan-beam FBP (initial image of Algorithm 1); for a helical geometry, per slice the
+    fan-beam FBP of its single-slice rebinning."""
     win = {"ramp": CT_FBP_RAMP, "hann": CT_FBP_HANN}[window] if isinstance(window, str) else int(window)
     _check(_lib.ct_fbp(geom.handle, _ptr(y, "y", geom.na * geom.view_len), _ptr(x, "x", geom.nvox), win,
                        _stream(stream)))

@@ -241,7 +241,10 @@ def test_unsupported_calls_on_helical_geometry(ct):
     with pytest.raises(ct.CTError) as e:
         ct.ct_geom_precompute(G)
     assert e.value.status == ct.CT_ENOTSUP
-    y = torch.zeros(g.na, g.nt, g.ns, device="cuda")
+    # the helical start image needs whole turns: less than one turn is refused
+    g2 = g.with_(orbit_deg=300.0)
+    G2 = ct.Geometry.from_helix(g2)
+    y = torch.zeros(g2.na, g2.nt, g2.ns, device="cuda")
     with pytest.raises(ct.CTError) as e:
-        ct.ct_fbp(G, y, torch.zeros(g.nz, g.ny, g.nx, device="cuda"))
+        ct.ct_fbp(G2, y, torch.zeros(g2.nz, g2.ny, g2.nx, device="cuda"))
     assert e.value.status == ct.CT_ENOTSUP
