@@ -265,6 +265,17 @@ typedef struct {
     float dl_scale;     /* D_L <- dl_scale * diag(A'WA1) (supplement's majorizer study); 0 reads as 1 */
     const float *kappa; /* optional device image of the regularizer's voxel weights kappa_n (Eq. (def_reg),
                            e.g. from ct_kappa; same layout as x_inout), NULL for kappa = 1 */
+    /* Checkpoint and resume.  The solver state after outer iteration k is (x, g, h, k): D_L is recomputed
+       from w, rho depends only on the subiteration count k M (Eq. (dec_rho)), and the next subset is 0.
+       g_state, h_state: optional device images (layout of x_inout); when given, the solve writes its final
+       g and h (Algorithm 2: h holds zeta) into them.  start_iter > 0 resumes after that many outer
+       iterations: g and h are read from g_state and h_state (both required; init_fbp must be 0) instead
+       of the initial gradient step, x_inout holds the iterate, and rho continues at subiteration
+       start_iter M.  A run split this way gives the same x, g and h, bit for bit, as one uninterrupted
+       run on the same GPU. */
+    int start_iter;
+    float *g_state;
+    float *h_state;
 } ct_solve_params;
 
 /* Report filled by ct_relaxed_oslalm_solve.  The two array pointers are

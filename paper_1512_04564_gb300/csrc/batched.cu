@@ -429,6 +429,7 @@ ct_status validate_slice(int i, const ct_geom *g, const float *y, const float *w
         if (sf != CT_OK) return sf;
     }
     if ((long)p->n_iter * p->M > 50000000L) { set_error("slice %d: n_iter * M too large", i); return CT_EINVAL; }
+    if (p->start_iter != 0) { set_error("slice %d: batched solves do not resume (start_iter)", i); return CT_ENOTSUP; }
     return CT_OK;
 }
 

@@ -189,6 +189,14 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
         ct_status sf = validate_fbp(g, CT_FBP_HANN);
         if (sf != CT_OK) return sf;
     }
+    if (p->start_iter < 0 || (long)p->start_iter * p->M > 200000000L) {
+        set_error("start_iter=%d out of range", p->start_iter);
+        return CT_EINVAL;
+    }
+    if (p->start_iter > 0 && (!p->g_state || !p->h_state || p->init_fbp)) {
+        set_error("resuming (start_iter > 0) needs g_state and h_state and init_fbp = 0");
+        return CT_EINVAL;
+    }
 
     const int M = p->M;
     // interleaved subsets, stored contiguously: perm = [S_0 | S_1 | ... | S_{M-1}]
@@ -205,8 +213,10 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
     for (int m = 0; m < M; m++) max_sub = cnt[m] > max_sub ? cnt[m] : max_sub;
     const long T = (long)p->n_iter * M;
     std::vector<float> rho((size_t)(T > 0 ? T : 1));
+    // rho of the subiterations this call runs: a resumed solve continues the sequence after start_iter * M
+    const long t0 = (long)p->start_iter * M;
     for (long t = 0; t < T; t++)
-        rho[t] = (float)(p->continuation ? rho_continuation(t, p->alpha) : (double)p->rho_fixed);
+        rho[t] = (float)(p->continuation ? rho_continuation(t0 + t, p->alpha) : (double)p->rho_fixed);
 
     Workspace W;
     ct_status st = ensure_workspace(g, max_sub, (int)(T > 0 ? T : 1), p->n_iter, p->kappa != nullptr, W);
@@ -297,9 +307,22 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
     CT_CUDA_TRY(launch_weighted_ray_sums(g, w, g->d_sino_ws, ws), "D_L weights");
     CT_CUDA_TRY(step_bp(g, BP_PLAIN, g->d_sino_ws, g->d_views_all, na, W.d_l, nullptr, ws,
                         p->dl_scale > 0.0f ? p->dl_scale : 1.0f), "D_L back");
-    // rho = 1, zeta = g = M grad L_M(x), h = D_L x - zeta  (last subset)
-    CT_CUDA_TRY(step_fp(g, FP_RESID, S.x, W.perm + off[M - 1], cnt[M - 1], W.resid, y, w, ws), "init forward");
-    CT_CUDA_TRY(step_bp(g, BP_SOLVE_INIT, W.resid, W.perm + off[M - 1], cnt[M - 1], nullptr, &S, ws), "init back");
+    if (p->start_iter > 0) {
+        // resume: g and h from the checkpoint
+        const size_t nvox = (size_t)G.nx * G.ny * (g->helical ? g->hx.nz : 1);
+        if (g->helical) {
+            CT_CUDA_TRY(launch_to_columns(g, p->g_state, W.g, ws), "g layout");
+            CT_CUDA_TRY(launch_to_columns(g, p->h_state, W.h, ws), "h layout");
+        } else {
+            CT_CUDA_TRY(cudaMemcpyAsync(W.g, p->g_state, sizeof(float) * nvox, cudaMemcpyDeviceToDevice, ws), "g");
+            CT_CUDA_TRY(cudaMemcpyAsync(W.h, p->h_state, sizeof(float) * nvox, cudaMemcpyDeviceToDevice, ws), "h");
+        }
+    } else {
+        // rho = 1, zeta = g = M grad L_M(x), h = D_L x - zeta  (last subset)
+        CT_CUDA_TRY(step_fp(g, FP_RESID, S.x, W.perm + off[M - 1], cnt[M - 1], W.resid, y, w, ws), "init forward");
+        CT_CUDA_TRY(step_bp(g, BP_SOLVE_INIT, W.resid, W.perm + off[M - 1], cnt[M - 1], nullptr, &S, ws),
+                    "init back");
+    }
 
     const float tol = p->stop_rmsd_hu > 0.0f ? p->stop_rmsd_hu : 1.0f;
     int done = 0;
@@ -315,6 +338,17 @@ extern "C" ct_status ct_relaxed_oslalm_solve(const ct_geom *gc, const float *y, 
         }
     }
     if (g->helical) CT_CUDA_TRY(launch_to_slices(g, W.x_col, x, 1.0f, 0, ws), "x layout");
+    // checkpoint: the final g and h (x is the caller's x_inout)
+    for (int q = 0; q < 2; q++) {
+        float *dst = q == 0 ? p->g_state : p->h_state;
+        const float *src = q == 0 ? W.g : W.h;
+        if (!dst) continue;
+        if (g->helical)
+            CT_CUDA_TRY(launch_to_slices(g, src, dst, 1.0f, 0, ws), "state layout");
+        else
+            CT_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(float) * (size_t)G.nx * G.ny, cudaMemcpyDeviceToDevice, ws),
+                        "state");
+    }
     CT_CUDA_TRY(cudaEventRecord(ev_end, ws), "event");
     CT_CUDA_TRY(cudaEventRecord(ev_in, ws), "event");
     CT_CUDA_TRY(cudaStreamWaitEvent(user, ev_in, 0), "ordering caller's stream");

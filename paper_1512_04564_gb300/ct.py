@@ -51,6 +51,7 @@ class ct_solve_params(ctypes.Structure):
         ("x_ref", ctypes.c_void_p), ("hu_per_unit", ctypes.c_float), ("fov_radius", ctypes.c_float),
         ("stop_rmsd_hu", ctypes.c_float), ("init_fbp", ctypes.c_int), ("curvature", ctypes.c_int),
         ("dl_scale", ctypes.c_float), ("kappa", ctypes.c_void_p),
+        ("start_iter", ctypes.c_int), ("g_state", ctypes.c_void_p), ("h_state", ctypes.c_void_p),
     ]
 
 
@@ -342,13 +343,19 @@ def ct_relaxed_oslalm_solve(geom: Geometry, y: torch.Tensor, w: torch.Tensor, x:
                             algorithm="proposed", nonneg=True, continuation=True, rho_fixed=0.0,
                             x_ref: torch.Tensor | None = None, hu_per_unit=1.0, fov_radius=0.0,
                             stop_rmsd_hu=0.0, init_fbp=False, curvature="huber", dl_scale=1.0,
-                            kappa: torch.Tensor | None = None, stream=None) -> dict:
-    """Relaxed OS-LALM (Algorithm 1 / 2); x is updated in place.  Returns the report as a dict."""
+                            kappa: torch.Tensor | None = None, start_iter=0, g_state: torch.Tensor | None = None,
+                            h_state: torch.Tensor | None = None, stream=None) -> dict:
+    """Relaxed OS-LALM (Algorithm 1 / 2); x is updated in place.  Returns the report as a dict.
+    g_state, h_state: optional image tensors that receive the final g and h (a checkpoint with x and the
+    iteration count); start_iter > 0 resumes from them after that many outer iterations."""
     n = geom.nvox
     p = _params(geom, M=M, n_iter=n_iter, alpha=alpha, beta=beta, delta=delta, potential=potential,
                 algorithm=algorithm, nonneg=nonneg, continuation=continuation, rho_fixed=rho_fixed, x_ref=x_ref,
                 hu_per_unit=hu_per_unit, fov_radius=fov_radius, stop_rmsd_hu=stop_rmsd_hu, init_fbp=init_fbp,
                 curvature=curvature, dl_scale=dl_scale, kappa=kappa)
+    p.start_iter = int(start_iter)
+    p.g_state = _ptr(g_state, "g_state", n)
+    p.h_state = _ptr(h_state, "h_state", n)
     r, trace, its = _report(n_iter)
     _check(_lib.ct_relaxed_oslalm_solve(geom.handle, _ptr(y, "y", geom.na * geom.view_len), _ptr(w, "w", geom.na * geom.view_len),
                                         ctypes.byref(p), _ptr(x, "x", n), ctypes.byref(r), _stream(stream)))
