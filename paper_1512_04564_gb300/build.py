@@ -19,7 +19,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "libct.so")
 SOURCES = ["geom.cu", "projectors.cu", "matrix.cu", "reg2d.cu", "solve.cu", "noalloc.cu", "fbp.cu", "batched.cu", "tune.cu",
            "helical.cu", "unet.cu", "raysum.cu"]
-HEADERS = ["ct_internal.cuh"]
+HEADERS = ["ct_internal.cuh", "tc.cuh", "tc_gemm.cuh", "tc_conv_tma.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

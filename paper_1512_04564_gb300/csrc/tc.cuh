@@ -140,5 +140,49 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// ---- TMA operand staging with the 64-byte swizzle
+//
+// A K-major operand plane of R rows x 32 BF16 (64 bytes per row), written by one tiled TMA copy with the
+// 64-byte swizzle: rows are 64 bytes apart and the pattern repeats every 8 rows (512 bytes).  The MMA reads
+// it through a descriptor with the same swizzle: K-chunk q (16 elements) of the plane starts 32 q bytes in,
+// 8-row groups are 512 bytes apart.  Planes start on 1024-byte boundaries.
+constexpr uint32_t kSw64SBO = 512;
+
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                              // leading byte offset: unused within a swizzle atom
+    d |= (uint64_t)((kSw64SBO >> 4) & 0x3FFF) << 32;    // 8-row groups
+    d |= (uint64_t)1 << 46;                              // descriptor version
+    d |= (uint64_t)4 << 61;                              // 64-byte swizzle
+    return d;
+}
+
+// Arrive on the mbarrier (count 1) and expect `bytes` more from asynchronous copies in this phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Tiled TMA loads into this CTA's shared memory, completion counted in bytes on `bar`.
+__device__ __forceinline__ void tma_load_2d(uint32_t sdst, const void *map, int c0, int c1, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(sdst),
+        "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t sdst, const void *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(sdst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
 }  // namespace tc
 }  // namespace ct

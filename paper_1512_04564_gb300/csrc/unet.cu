@@ -4,6 +4,7 @@
 // small kernels around them.  The paper has no counterpart; the C ABI is in
 // include/ct_unet.h.
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -12,6 +13,7 @@
 
 #include "../../include/ct_unet.h"
 #include "ct_internal.cuh"
+#include "tc_conv_tma.cuh"
 #include "tc_gemm.cuh"
 
 namespace ct {
@@ -507,6 +509,85 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
 
 // ---------------------------------------------------------------- convolution launchers
 
+// The driver's tensor-map encoder, through the runtime (no link against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+// Tensor maps of the TMA convolution (tc_conv_tma.cuh), when it takes this layer: a single full-resolution
+// input of a multiple of 32 channels, a multiple of 32 output channels, 128-pixel tiles that are one
+// part of a row (W a multiple of 128) or whole rows of one image (128 a multiple of W, H W of 128), and
+// 16-byte aligned tensors.  A: the input [B][H][W][Ci], box 32 channels x the tile's pixels; B: the
+// weights [N][9 Ci], box 32 K-elements x nt channels; both with the 64-byte swizzle, zeros outside.
+bool conv_tma_maps(const ConvIn &in, const bf16 *w, int B, int H, int W, int N, int nt, CUtensorMap &ma,
+                   CUtensorMap &mb)
+{
+    if (in.c2 != 0 || in.up1 || in.c1 % 32 != 0 || N % 32 != 0) return false;
+    if (!((W % 128 == 0) || (W < 128 && 128 % W == 0 && (H * W) % 128 == 0))) return false;
+    if (((uintptr_t)in.t1 & 15) || ((uintptr_t)w & 15)) return false;
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t Ci = (cuuint64_t)in.c1, Kt = 9 * Ci;
+    const cuuint64_t dimA[4] = {Ci, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strA[3] = {Ci * 2, (cuuint64_t)W * Ci * 2, (cuuint64_t)H * W * Ci * 2};
+    const cuuint32_t boxA[4] = {32, (cuuint32_t)std::min(W, 128), (cuuint32_t)(W >= 128 ? 1 : 128 / W), 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(in.t1), dimA, strA, boxA, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t dimB[2] = {Kt, (cuuint64_t)N};
+    const cuuint64_t strB[1] = {Kt * 2};
+    const cuuint32_t boxB[2] = {32, (cuuint32_t)nt};
+    return enc(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(w), dimB, strB, boxB, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NT, int ST, class L>
+cudaError_t launch_conv_tma_st(const CUtensorMap &ma, const CUtensorMap &mb, const L &epi, tc::ConvTmaGeo geo,
+                               int mtiles, int ntiles, int *err, cudaStream_t st)
+{
+    const int bytes = tc::ConvTmaSmem<NT, ST>::kBytes;
+    cudaError_t e =
+        cudaFuncSetAttribute(tc::conv_tma_kernel<NT, ST, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    tc::conv_tma_kernel<NT, ST, L><<<dim3(mtiles, ntiles), 128, bytes, st>>>(ma, mb, epi, geo, err);
+    return cudaGetLastError();
+}
+
+int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    }
+    return n;
+}
+
+// Two stages when the grid covers the SMs twice or more (several CTAs per SM overlap one another's
+// copies), four when it does not.
+template <int NT, class L>
+cudaError_t launch_conv_tma(const CUtensorMap &ma, const CUtensorMap &mb, const L &epi, tc::ConvTmaGeo geo, int mtiles,
+                            int ntiles, int *err, cudaStream_t st)
+{
+    if ((long)mtiles * ntiles >= 2L * sm_count()) return launch_conv_tma_st<NT, 2>(ma, mb, epi, geo, mtiles, ntiles, err, st);
+    return launch_conv_tma_st<NT, 4>(ma, mb, epi, geo, mtiles, ntiles, err, st);
+}
+
 template <int EPI>
 cudaError_t conv3x3_tc(const ConvIn &in, const bf16 *w, const float *bias, bf16 *out, const ConvIn &mask, bf16 *out2,
                        int B, int H, int W, int N, int *err, cudaStream_t st)
@@ -517,6 +598,16 @@ cudaError_t conv3x3_tc(const ConvIn &in, const bf16 *w, const float *bias, bf16 
     int nt = 256;
     while (nt > 32 && N % nt != 0) nt >>= 1;
     const int ntiles = (N + nt - 1) / nt;
+    CUtensorMap ma, mb;
+    if (conv_tma_maps(in, w, B, H, W, N, nt, ma, mb)) {
+        const tc::ConvTmaGeo geo{H, W, Ci, 9 * Ci / 32};
+        switch (nt) {
+        case 256: return launch_conv_tma<256>(ma, mb, ConvGemm<256, EPI>{in, w, bias, out, mask, out2, B, H, W, Ci, N}, geo, mt, ntiles, err, st);
+        case 128: return launch_conv_tma<128>(ma, mb, ConvGemm<128, EPI>{in, w, bias, out, mask, out2, B, H, W, Ci, N}, geo, mt, ntiles, err, st);
+        case 64: return launch_conv_tma<64>(ma, mb, ConvGemm<64, EPI>{in, w, bias, out, mask, out2, B, H, W, Ci, N}, geo, mt, ntiles, err, st);
+        default: return launch_conv_tma<32>(ma, mb, ConvGemm<32, EPI>{in, w, bias, out, mask, out2, B, H, W, Ci, N}, geo, mt, ntiles, err, st);
+        }
+    }
     switch (nt) {
     case 256: return launch_gemm<256>(ConvGemm<256, EPI>{in, w, bias, out, mask, out2, B, H, W, Ci, N}, mt, ntiles, ks, err, st);
     case 128: return launch_gemm<128>(ConvGemm<128, EPI>{in, w, bias, out, mask, out2, B, H, W, Ci, N}, mt, ntiles, ks, err, st);
