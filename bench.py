@@ -1124,7 +1124,6 @@ def kernel_roofline(ct, G, g, M, y, w, x, matrix_bytes, clock_mhz=None):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"
     npix = g.nx * g.ny
-    ntile_px = ((g.nx + 15) // 16) * ((g.ny + 15) // 16) * 256
     nnz = sum(fan_cells_view(g, v) for v in views)
     flops = FLOP_PER_AIJ_2D * nnz
     peak, peak_src = fp32_peak_tflops(clock_mhz)
@@ -1135,11 +1134,13 @@ def kernel_roofline(ct, G, g, M, y, w, x, matrix_bytes, clock_mhz=None):
     if matrix_bytes:
         R = g.na * g.ns
         # the rows' entries (6 B each: a_ij + 16-bit offset) and chunk bases (4 B per 32 entries)
-        entry_bytes = matrix_bytes - 8 * (R + 1) - 4 * (R + 2) - 24 * g.na * ntile_px
+        _, rec_bytes = ct.ct_geom_matrix_info(G)
+        entry_bytes = matrix_bytes - 8 * (R + 1) - 4 * (R + 3) - rec_bytes
         # FP: the subset's share of the entries, 12 B per ray (row and chunk pointers), image, output
         stored["fp"] = entry_bytes * nv / g.na + 12 * nv * g.ns + 4 * npix + 4 * nv * g.ns
-        # BP: one stored record (24 B) per (view, pixel slot), the residual rows, x written
-        stored["bp"] = 24 * ntile_px * nv + 4 * nv * g.ns + 4 * npix
+        # BP: the subset's share of the records (per view and 32 pixels: a chunk of 16-bit first cells and
+        # counts and K weights per pixel; its 4-byte word), the residual rows, x written
+        stored["bp"] = rec_bytes * nv / g.na + 4 * nv * g.ns + 4 * npix
     kernels = {}
     for key, t, name, cmin in (("fp", fp_s, "fp_csr_kernel" if matrix_bytes else "fp_bundle_kernel", fp_min),
                                ("bp", bp_s, "bp_records_kernel" if matrix_bytes else "bp_fan2d_kernel", bp_min)):

@@ -117,8 +117,9 @@ void ct_geom_destroy(ct_geom *g);
  * ray-driven forward projector, whose steep rays index a transposed copy of
  * the image (the projector packs [x | x^T] into a 2 nx ny scratch that g
  * also owns, or the solver's update kernel writes it) and (2) per-(view,
- * pixel) records of the pixel's cell weights for the voxel-driven
- * back-projector.  Afterwards ct_forward,
+ * pixel) records of the pixel's cell weights (first cell and count in 16
+ * bits, then the weights, interleaved across chunks of 32 pixels) for the
+ * voxel-driven back-projector.  Afterwards ct_forward,
  * ct_back, ct_sqs_diag and ct_relaxed_oslalm_solve stream it instead of
  * recomputing footprints; results stay within FP32 rounding of the
  * on-the-fly path.  Also computes the ray sums A 1 from it (see ct_sqs_diag).  max_bytes: refuse with CT_ENOMEM (nothing kept) when the
@@ -128,6 +129,14 @@ void ct_geom_destroy(ct_geom *g);
  * CT_ENOMEM, CT_ENOTSUP (an image too wide for the 16-bit offsets),
  * CT_ECUDA. */
 ct_status ct_geom_precompute(ct_geom *g, unsigned long long max_bytes, unsigned long long *bytes_out, void *stream);
+
+/* Sizes of the resident matrix of g (an implementation detail; the paper has
+ * no counterpart): matrix_bytes the whole (as ct_geom_precompute reports),
+ * record_bytes the back-projector's records within it (0 when it keeps
+ * none: footprints wider than 15 cells, or more than 4096 cells).  Both 0
+ * before ct_geom_precompute.  Either pointer may be NULL.  Errors: CT_EINVAL
+ * (null geometry). */
+ct_status ct_geom_matrix_info(const ct_geom *g, unsigned long long *matrix_bytes, unsigned long long *record_bytes);
 
 /* Projector autotuner (an implementation choice; the paper has no
  * counterpart).  Times, on a subset of views_per_launch evenly spread views

@@ -344,32 +344,17 @@ __global__ void __launch_bounds__(kThreads, 5) batched_kernel(const BatchSlice *
                 const int ix = tx * kTile + lx, iy = ty * kTile + ly;
                 const int m = t % B.M;
                 const int v0 = B.sub_off[m], nv = B.sub_off[m + 1] - v0;
-                const int ntiles = B.G.ntx * B.G.nty;
                 const int ixc = min(ix, B.G.nx - 1), iyc = min(iy, B.G.ny - 1);  // anchor of an in-image pixel
                 float acc = 0.0f;
-                if (B.G.foot_t) {  // stored footprints, next view's prefetched
-                    const size_t vstride = (size_t)ntiles * (kTile * kTile);
-                    const size_t base = (size_t)tile * (kTile * kTile) + threadIdx.x;
-                    float4 tn = make_float4(0.f, 0.f, 0.f, 0.f);
-                    float2 an = make_float2(0.f, 0.f);
-                    if (nv > 0) {
-                        const size_t i = (size_t)B.perm[v0] * vstride + base;
-                        tn = __ldcs(&B.G.foot_t[i]);
-                        an = __ldcs(&B.G.foot_an[i]);
-                    }
+                if (B.G.rec_data) {  // stored records (warp w: chunk w of the tile), the next view's prefetched
+                    const unsigned group = (unsigned)tile * (kTile * kTile / kRecGroup) + (threadIdx.x >> 5);
+                    RecSlot r{};
+                    if (nv > 0) r = rec_fetch(B.G, rec_word(B.G, B.perm[v0], group));
                     for (int k = 0; k < nv; k++) {
-                        const float4 w = tn;
-                        const float2 b = an;
-                        if (k + 1 < nv) {
-                            const size_t i = (size_t)B.perm[v0 + k + 1] * vstride + base;
-                            tn = __ldcs(&B.G.foot_t[i]);
-                            an = __ldcs(&B.G.foot_an[i]);
-                        }
-                        const float *row = B.resid + (size_t)k * B.G.ns;
-                        if (__float_as_int(b.y) == kWideRecord)  // wider than a record: the overflow weights
-                            acc += wide_record_dot<true>(B.G.foot_ovf, w, row, B.G.ns);
-                        else
-                            acc += record_dot<true>(w, b, row, B.G.ns);
+                        const RecSlot cur = r;
+                        if (k + 1 < nv) r = rec_fetch(B.G, rec_word(B.G, B.perm[v0 + k + 1], group));
+                        acc += rec_dot<true>(B.G, cur, B.resid + (size_t)k * B.G.ns,
+                                             [&] { return rec_word(B.G, B.perm[v0 + k], group); });
                     }
                 } else {
                     acc = fly_pixel_back(B, v0, nv, ixc, iyc);

@@ -37,11 +37,10 @@ struct FanDev {
     const float2 *view_cs;    // [na]: (cos beta, sin beta)
     const float *view_beta;   // [na]: beta in [0, 2 pi)
     // resident system matrix (ct_geom_precompute); null when footprints are computed on the fly
-    const float4 *foot_t;     // [na][ntiles][256]: a_ij of the pixel's first four cells n0 .. n0+3
-    const float2 *foot_an;    // [na][ntiles][256]: a_ij of cell n0+4, and n0 as int bits (kWideRecord:
-                              // the footprint covers more than kRecordCells cells; foot_t then holds, as int
-                              // bits, the offset of its weights in foot_ovf, their count and n0)
-    const float *foot_ovf;    // weights of the wide footprints (~1% of the records at 512 x 512)
+    // Back-projector records in chunks of 32 pixel slots (see the layout at kRecGroup); null when
+    // footprints are computed on the fly
+    const unsigned char *rec_data;
+    const unsigned int *rec_grp;  // [na][ntiles][8]: the chunk's start in 32-byte units (bits 0-27) and K (28-31)
     const long long *row_ptr; // [na*ns + 1]: start of each ray's entry pairs (ray-major; the entries in march
                               // order, two per pair, a ray with an odd count padded by a zero entry)
     const float2 *row_w;      // [pairs]: a_ij of the pair's two entries
@@ -123,9 +122,9 @@ struct ct_geom {
     int *d_row_d = nullptr;
     int *d_row_first = nullptr;
     int *d_row_base = nullptr;
-    float4 *d_foot_t = nullptr;
-    float2 *d_foot_an = nullptr;
-    float *d_foot_ovf = nullptr;
+    unsigned char *d_rec_data = nullptr;
+    unsigned int *d_rec_grp = nullptr;
+    unsigned long long rec_bytes = 0;  // the records' share of matrix_bytes
     float *d_xpack = nullptr;     // FanDev::xpack
     unsigned long long matrix_bytes = 0;
     int device = 0;
@@ -534,37 +533,68 @@ ct_status stage_views(const ct_geom *g, const int *views, int nviews, const int 
 
 // ---------------------------------------------------------------- stored cell-weight records (resident matrix)
 
-constexpr int kRecordCells = 5;          // cells per stored (view, pixel) record
-constexpr int kWideRecord = -(1 << 30);  // base-cell code of a footprint wider than kRecordCells cells
+// A record is the weights a_ij of one (view, pixel) footprint's cells, clipped to the detector: n0 the
+// first cell, cnt <= 15 cells.  The records of 32 consecutive pixel slots of a 16x16 tile (one warp of the
+// back-projectors; slots in tile order, 8 groups a tile) and one view form a chunk of 64 + 128 K bytes,
+// K the group's largest cnt:
+//   bytes 0 - 63   each slot's n0 (bits 0-11) and cnt (bits 12-15), u16
+//   bytes 64 -     weight i of slot l at float 32 i + l (i < K; zero for i >= the slot's cnt)
+// so that the warp reads weight i of all 32 slots with one coalesced 128-byte load, and every address
+// follows from the group's word (chunk start and K) alone.
+constexpr int kRecGroup = 32;
+constexpr int kRecMaxCells = 15;
+constexpr int kRecInline = 5;  // weights a lane holds in registers (a footprint covers 2 - 5 cells, rarely more)
 
-// sum_k a_k row[n0 + k] over the weights of a wide footprint kept in the overflow array.
-template <bool COHERENT = false>
-__device__ __forceinline__ float wide_record_dot(const float *__restrict__ ovf, float4 w, const float *row, int ns)
+// One slot's record of one view, its first kRecInline weights loaded.
+struct RecSlot {
+    unsigned nc;  // first cell (bits 0-11) and count (12-15)
+    float w[kRecInline];
+};
+
+__device__ __forceinline__ const float *rec_weights(const FanDev &G, unsigned word)
 {
-    const int off = __float_as_int(w.x), cnt = __float_as_int(w.y), n0 = __float_as_int(w.z);
+    return reinterpret_cast<const float *>(G.rec_data + 32 * (size_t)(word & 0x0fffffffu) + 64) + (threadIdx.x & 31);
+}
+
+// The record of this lane's slot in the chunk of group word `word` (every lane of the warp calls it: the
+// loads of weights i < K are warp-uniform).
+__device__ __forceinline__ RecSlot rec_fetch(const FanDev &G, unsigned word)
+{
+    const int K = (int)(word >> 28), lane = threadIdx.x & 31;
+    const unsigned char *c = G.rec_data + 32 * (size_t)(word & 0x0fffffffu);
+    const float *wp = reinterpret_cast<const float *>(c + 64) + lane;
+    RecSlot r;
+    r.nc = __ldcs(reinterpret_cast<const unsigned short *>(c) + lane);
+#pragma unroll
+    for (int i = 0; i < kRecInline; i++) r.w[i] = i < K ? __ldcs(wp + 32 * i) : 0.0f;
+    return r;
+}
+
+// sum_k a_k row[n0 + k] over one record; word() gives the chunk's word again for the rare records wider
+// than kRecInline cells.  COHERENT loads of the row bypass L1 (rows rewritten by other CTAs of a
+// persistent kernel).
+template <bool COHERENT = false, class Word>
+__device__ __forceinline__ float rec_dot(const FanDev &G, const RecSlot &r, const float *rows, Word word)
+{
+    const int cnt = (int)(r.nc >> 12);
+    const float *row = rows + (r.nc & 0xfffu);
     float acc = 0.0f;
-#pragma unroll 1  // rare and short: unrolled, it costs the record loop around it its registers
-    for (int k = 0; k < cnt; k++) {
-        const int c = n0 + k;
-        if ((unsigned)c < (unsigned)ns) acc = fmaf(__ldg(&ovf[off + k]), COHERENT ? __ldcg(&row[c]) : __ldg(&row[c]), acc);
+#pragma unroll
+    for (int i = 0; i < kRecInline; i++)
+        if (i < cnt) acc = fmaf(r.w[i], COHERENT ? __ldcg(&row[i]) : __ldg(&row[i]), acc);
+    if (cnt > kRecInline) {
+        const float *wp = rec_weights(G, word());
+#pragma unroll 1
+        for (int i = kRecInline; i < cnt; i++)
+            acc = fmaf(__ldcs(wp + 32 * i), COHERENT ? __ldcg(&row[i]) : __ldg(&row[i]), acc);
     }
     return acc;
 }
 
-// sum_k a_k row[n0 + k] over one stored record (cells outside [0, ns) read as 0).  COHERENT loads
-// bypass L1 (rows rewritten by other CTAs of a persistent kernel).
-template <bool COHERENT = false>
-__device__ __forceinline__ float record_dot(float4 w, float2 w4n, const float *row, int ns)
+// Word of group `group` (tile * 8 + warp of the tile) of view v.
+__device__ __forceinline__ unsigned rec_word(const FanDev &G, int v, unsigned group)
 {
-    const int n0 = __float_as_int(w4n.y);
-    const float wk[kRecordCells] = {w.x, w.y, w.z, w.w, w4n.x};
-    float acc = 0.0f;
-#pragma unroll
-    for (int k = 0; k < kRecordCells; k++) {
-        const int c = n0 + k;
-        if ((unsigned)c < (unsigned)ns) acc = fmaf(wk[k], COHERENT ? __ldcg(&row[c]) : __ldg(&row[c]), acc);
-    }
-    return acc;
+    return __ldg(&G.rec_grp[(size_t)v * ((size_t)G.ntx * G.nty * 8) + group]);
 }
 
 // ---------------------------------------------------------------- regularizer (Eq. (def_reg))

@@ -83,9 +83,8 @@ static void free_geom(ct_geom *g)
     cudaFree(g->d_row_d);
     cudaFree(g->d_row_first);
     cudaFree(g->d_row_base);
-    cudaFree(g->d_foot_t);
-    cudaFree(g->d_foot_an);
-    cudaFree(g->d_foot_ovf);
+    cudaFree(g->d_rec_data);
+    cudaFree(g->d_rec_grp);
     cudaFree(g->d_xpack);
     cudaFree(g->d_view_zb);
     cudaFree(g->d_row_c);

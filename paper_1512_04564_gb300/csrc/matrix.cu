@@ -2,7 +2,7 @@
 //
 // The SF weights a_ij (Sec. III, Eq. (ct_problem): A is the projection
 // matrix) depend on the geometry only.  For a 2-D scan the whole matrix fits
-// in HBM (about 15 GB for 512x512 pixels, 984 views x 888 cells), so it is
+// in HBM (about 8.4 GB for 512x512 pixels, 984 views x 888 cells), so it is
 // evaluated once with the same device functions the on-the-fly projectors
 // use and then streamed:
 //   * ray-major rows: for every ray, its a_ij in the order the ray kernel
@@ -13,12 +13,16 @@
 //     ray, marched row by row, indexes the transposed copy, so that the 64
 //     entries a warp gathers at once lie on a few columns of x^T instead of
 //     some twenty rows of x;
-//   * per-(view, pixel) records: the a_ij of the footprint's first five cells
-//     and the base cell, laid out tile by tile, for the voxel-driven
-//     back-projector (footprints wider than five cells, ~1% at 512x512, are
-//     marked and evaluated on the fly).
+//   * per-(view, pixel) records for the voxel-driven back-projector, in
+//     chunks of 32 pixels of a 16x16 tile: each footprint's first cell and
+//     cell count in 16 bits, then K weights per pixel interleaved across the
+//     32 (K the chunk's widest footprint), about 18 bytes per record at
+//     512x512 against 24 for five padded weights and a base cell.
+//     Geometries with footprints wider than 15 cells keep no records and
+//     back-project on the fly.
 // Building it: count each ray's nonzero weights, exclusive-scan the counts
-// into row pointers, fill the rows, store the footprints.
+// into row pointers, fill the rows; size each record chunk, exclusive-scan
+// the sizes into chunk starts, fill the chunks.
 #include <algorithm>
 #include <vector>
 
@@ -79,42 +83,43 @@ __global__ void __launch_bounds__(256) matrix_fill_kernel(FanDev G, const long l
     }
 }
 
-// Per-(view, pixel) records of cell weights.  COUNT: only add the cells of the footprints wider than a
-// record to *ovf_used.  Otherwise also write those footprints' weights to ovf (slots taken with an
-// atomic counter; a record keeps its slot's offset, so the values a kernel reads do not depend on the
-// order slots were taken in).
+// Back-projector records (layout at kRecGroup), one CTA per (view, tile): thread t = slot t, warp w the
+// chunk of group w.  A record holds the footprint's cells with a nonzero a_ij (as cell_weight evaluates
+// them: the same a_ij as the ray-major rows), clipped to the detector.  COUNT: each chunk's size
+// (32-byte units) to units[]; a footprint of more than kRecMaxCells cells sets *wide (the build then
+// keeps no records).  Otherwise units[] holds each chunk's start (exclusive scan of the sizes): write
+// the chunks and the groups' words.
 template <bool COUNT>
-__global__ void __launch_bounds__(256) matrix_foot_kernel(FanDev G, float4 *__restrict__ ft, float2 *__restrict__ fan,
-                                                          float *__restrict__ ovf, unsigned long long *ovf_used,
-                                                          unsigned long long ovf_cap)
+__global__ void __launch_bounds__(256) matrix_rec_kernel(FanDev G, long long *__restrict__ units,
+                                                         unsigned char *__restrict__ data,
+                                                         unsigned int *__restrict__ grp, int *wide)
 {
     const int ntiles = G.ntx * G.nty;
     const int v = blockIdx.x / ntiles, tile = blockIdx.x - v * ntiles;
-    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile, lane = threadIdx.x & 31;
     const int ty = tile / G.ntx, tx = tile - ty * G.ntx;
     // pixels of a partial tile beyond the image get the edge pixel's (unused) record
     const int ix = min(tx * kTile + lx, G.nx - 1), iy = min(ty * kTile + ly, G.ny - 1);
     const float2 cs = __ldg(&G.view_cs[v]);
     const Footprint F = pixel_footprint(G, v, cs.x, cs.y, ix, iy);
-    const size_t i = ((size_t)v * (G.ntx * G.nty) + tile) * (kTile * kTile) + threadIdx.x;
-    // the footprint's cells, as cell_weight evaluates them (the same a_ij as the ray-major rows)
-    const int j0 = foot_first(F), jl = foot_last(F);
-    const int cnt = jl - j0 + 1;
-    if (cnt > kRecordCells) {
-        const unsigned long long off = atomicAdd(ovf_used, (unsigned long long)cnt);
-        if (COUNT) return;
-        const bool fits = off + cnt <= ovf_cap;  // always, as both passes count the same footprints
-        if (fits)
-            for (int k = 0; k < cnt; k++) ovf[off + k] = cell_weight(F, F.n + j0 + k);
-        ft[i] = make_float4(__int_as_float((int)off), __int_as_float(fits ? cnt : 0), __int_as_float(F.n + j0), 0.0f);
-        fan[i] = make_float2(0.0f, __int_as_float(kWideRecord));
+    const int c0 = max(F.n + foot_first(F), 0), c1 = min(F.n + foot_last(F), G.ns - 1);
+    int cnt = max(c1 - c0 + 1, 0);
+    if (cnt > kRecMaxCells) {
+        if (COUNT) atomicExch(wide, 1);
+        cnt = kRecMaxCells;  // (only reached when the count pass has already rejected the build)
+    }
+    const int K = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
+    const size_t g = (size_t)blockIdx.x * (kTile * kTile / kRecGroup) + (threadIdx.x >> 5);
+    if (COUNT) {
+        if (lane == 0) units[g] = 2 + 4 * K;
         return;
     }
-    if (COUNT) return;
-    float w[kRecordCells] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-    for (int k = 0; k < cnt; k++) w[k] = cell_weight(F, F.n + j0 + k);
-    ft[i] = make_float4(w[0], w[1], w[2], w[3]);
-    fan[i] = make_float2(w[4], __int_as_float(F.n + j0));
+    const long long u = units[g];
+    unsigned char *c = data + 32 * (size_t)u;
+    reinterpret_cast<unsigned short *>(c)[lane] = (unsigned short)((cnt > 0 ? c0 : 0) | (cnt << 12));
+    float *w = reinterpret_cast<float *>(c + 64) + lane;
+    for (int i = 0; i < K; i++) w[32 * i] = i < cnt ? cell_weight(F, c0 + i) : 0.0f;
+    if (lane == 0) grp[g] = (unsigned int)u | ((unsigned int)K << 28);
 }
 
 // in-place exclusive scan of blocks of 1024 values; block totals to sums
@@ -188,23 +193,23 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     int *steps = nullptr;
     int *first = nullptr;
     int *base = nullptr;
-    float4 *ft = nullptr;
-    float2 *fan = nullptr;
+    unsigned char *rdata = nullptr;
+    unsigned int *rgrp = nullptr;
+    long long *ulen = nullptr;
     float *xp = nullptr;
-    float *ovf = nullptr;
     if (2LL * G.nx * G.ny >= (1LL << 31)) return cudaErrorNotSupported;  // packed-image indices are 32-bit
     cudaError_t e = cudaMalloc(&rp, sizeof(long long) * (R + 1));
     if (e != cudaSuccess) return e;
     auto fail = [&](cudaError_t err) {
-        cudaFree(ovf);
+        cudaFree(rdata);
+        cudaFree(ulen);
         cudaFree(xp);
         cudaFree(rp);
         cudaFree(wts);
         cudaFree(steps);
         cudaFree(first);
         cudaFree(base);
-        cudaFree(ft);
-        cudaFree(fan);
+        cudaFree(rgrp);
         return err;
     };
     if ((e = cudaMemsetAsync(rp + R, 0, sizeof(long long), st)) != cudaSuccess) return fail(e);
@@ -216,7 +221,7 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     // rows: pointers, chunk pointers, 12 bytes per pair, a base index per 32 pairs (bounded by nnz/32 + R)
     const unsigned long long bytes = (unsigned long long)(R + 1) * 8ull + (unsigned long long)R * 4ull +
                                      (unsigned long long)nnz * 12ull + ((unsigned long long)nnz / 32 + R) * 4ull +
-                                     (unsigned long long)G.na * ntile_px * 24ull;
+                                     (unsigned long long)G.na * ntile_px * 8ull;  // records: an estimate, known below
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     if ((max_bytes && bytes > max_bytes) || bytes > (unsigned long long)(0.9 * (double)free_b)) {
@@ -239,32 +244,45 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     hc[R] = (int)nchunks;
     hc[R + 1] = 0;  // the too-far flag
     if (nchunks >= (1LL << 31) - 4) return fail(cudaErrorNotSupported);
-    // (R + 2 entries and two spare 8-byte-aligned ints for the overflow counter)
-    if ((e = cudaMalloc(&first, sizeof(int) * (size_t)(R + 6))) != cudaSuccess) return fail(e);
+    // (R + 2 entries and a spare int for the records' wide flag)
+    if ((e = cudaMalloc(&first, sizeof(int) * (size_t)(R + 3))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&base, sizeof(int) * (size_t)(nchunks + 4))) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(first, hc.data(), sizeof(int) * (R + 2), cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e);
-    if ((e = cudaMalloc(&ft, sizeof(float4) * G.na * ntile_px)) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&fan, sizeof(float2) * G.na * ntile_px)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&xp, sizeof(float) * 2 * (size_t)G.nx * G.ny)) != cudaSuccess) return fail(e);
     matrix_fill_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(G, rp, first, reinterpret_cast<float *>(wts),
                                                                     reinterpret_cast<short *>(steps), base, first + R + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
-    // records: the wide footprints' cells counted first, then their overflow array allocated and filled
-    // two spare ints of `first` at an 8-byte boundary
-    unsigned long long *used = reinterpret_cast<unsigned long long *>(first + ((R + 3) & ~1LL));
+    // records: each chunk's size, their exclusive scan (the chunks' starts), then the chunks
+    int *wide = first + R + 2;
     const unsigned nfoot = (unsigned)((size_t)G.ntx * G.nty * G.na);
-    if ((e = cudaMemsetAsync(used, 0, sizeof(unsigned long long), st)) != cudaSuccess) return fail(e);
-    matrix_foot_kernel<true><<<nfoot, 256, 0, st>>>(G, ft, fan, nullptr, used, 0);
-    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
-    unsigned long long n_ovf = 0;
-    if ((e = cudaMemcpy(&n_ovf, used, sizeof(n_ovf), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
-    if (n_ovf >= (1ull << 31)) return fail(cudaErrorNotSupported);  // offsets are 32-bit
-    if ((e = cudaMalloc(&ovf, sizeof(float) * (size_t)(n_ovf > 0 ? n_ovf : 1))) != cudaSuccess) return fail(e);
-    if ((e = cudaMemsetAsync(used, 0, sizeof(unsigned long long), st)) != cudaSuccess) return fail(e);
-    matrix_foot_kernel<false><<<nfoot, 256, 0, st>>>(G, ft, fan, ovf, used, n_ovf);
-    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    const long long ng = (long long)nfoot * (kTile * kTile / kRecGroup);
+    long long units = 0;
+    int hw = 0;
+    bool keep_rec = G.ns <= 4096;  // first cells are 12-bit
+    if ((e = cudaMemsetAsync(wide, 0, sizeof(int), st)) != cudaSuccess) return fail(e);
+    if (keep_rec) {
+        if ((e = cudaMalloc(&ulen, sizeof(long long) * (size_t)(ng + 1))) != cudaSuccess) return fail(e);
+        if ((e = cudaMemsetAsync(ulen + ng, 0, sizeof(long long), st)) != cudaSuccess) return fail(e);
+        matrix_rec_kernel<true><<<nfoot, 256, 0, st>>>(G, ulen, nullptr, nullptr, wide);
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+        if ((e = exclusive_scan(ulen, ng + 1, st)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpy(&hw, wide, sizeof(hw), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpy(&units, ulen + ng, sizeof(units), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
+        // footprints wider than a record can hold, or chunk starts beyond 28 bits: back-project on the fly
+        keep_rec = !hw && units < (1LL << 28);
+    }
+    if (keep_rec) {
+        if ((e = cudaMalloc(&rdata, 32 * (size_t)(units > 0 ? units : 1))) != cudaSuccess) return fail(e);
+        if ((e = cudaMalloc(&rgrp, sizeof(unsigned int) * (size_t)ng)) != cudaSuccess) return fail(e);
+        matrix_rec_kernel<false><<<nfoot, 256, 0, st>>>(G, ulen, rdata, rgrp, wide);
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    cudaFree(ulen);
+    ulen = nullptr;
+    const unsigned long long rec_bytes =
+        rdata ? 32ull * (unsigned long long)units + 4ull * (unsigned long long)ng : 0ull;
     int far = 0;
     if ((e = cudaMemcpy(&far, first + R + 1, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
     if (far) {  // pixel-index steps beyond 16 bits (an image too wide for them): no resident matrix
@@ -288,17 +306,17 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
         if ((e = cudaMemcpy(g->d_ray_order, order.data(), sizeof(int) * nblk, cudaMemcpyHostToDevice)) != cudaSuccess)
             return fail(e);
     }
-    // the exact size: row pointers, chunk pointers (+ flag), entries, chunk bases, records
-    g->matrix_bytes = (unsigned long long)(R + 1) * 8ull + (unsigned long long)(R + 2) * 4ull +
-                      (unsigned long long)nnz * 12ull + (unsigned long long)(nchunks + 4) * 4ull +
-                      (unsigned long long)G.na * ntile_px * 24ull + n_ovf * 4ull;
+    // the exact size: row pointers, chunk pointers (+ flags), entries, chunk bases, records
+    g->matrix_bytes = (unsigned long long)(R + 1) * 8ull + (unsigned long long)(R + 3) * 4ull +
+                      (unsigned long long)nnz * 12ull + (unsigned long long)(nchunks + 4) * 4ull + rec_bytes;
+    g->rec_bytes = rec_bytes;
     g->d_row_ptr = rp;
     g->d_row_w = wts;
     g->d_row_d = steps;
     g->d_row_first = first;
     g->d_row_base = base;
-    g->d_foot_t = ft;
-    g->d_foot_an = fan;
+    g->d_rec_data = rdata;
+    g->d_rec_grp = rgrp;
     g->d_xpack = xp;
     g->fan.xpack = xp;
     g->fan.row_ptr = rp;
@@ -307,10 +325,8 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     g->fan.row_first = first;
     g->fan.row_base = base;
     g->fan.ray_order = g->d_ray_order;
-    g->fan.foot_t = ft;
-    g->fan.foot_an = fan;
-    g->d_foot_ovf = ovf;
-    g->fan.foot_ovf = ovf;
+    g->fan.rec_data = rdata;
+    g->fan.rec_grp = rgrp;
     return cudaSuccess;
 }
 
@@ -348,5 +364,15 @@ extern "C" ct_status ct_geom_precompute(ct_geom *g, unsigned long long max_bytes
         CT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream), "ray sums A 1");
     }
     if (bytes_out) *bytes_out = g->matrix_bytes;
+    return CT_OK;
+}
+
+extern "C" ct_status ct_geom_matrix_info(const ct_geom *g, unsigned long long *matrix_bytes,
+                                         unsigned long long *record_bytes)
+{
+    if (!g) { set_error("ct_geom_matrix_info: null geometry"); return CT_EINVAL; }
+    const bool built = g->d_row_ptr != nullptr;
+    if (matrix_bytes) *matrix_bytes = built ? g->matrix_bytes : 0ull;
+    if (record_bytes) *record_bytes = built ? g->rec_bytes : 0ull;
     return CT_OK;
 }

@@ -331,11 +331,11 @@ __device__ __forceinline__ void bp_epilogue(const FanDev &G, const SolveDev &S, 
     }
 }
 
-// Resident-matrix back-projection, one CTA per half tile (16 x 8 pixels, the first or last 128
-// records of a tile's block), one pixel per thread: twice the CTAs and warps of the two-pixel
-// kernel, which with 1024 tiles at 512 x 512 left the SMs 60% empty.  The next view's record is
-// loaded while the current view's is used; footprints wider than a record read their weights from the
-// overflow array.
+// Resident-matrix back-projection, one CTA per half tile (16 x 8 pixels, the first or last 128 slots of a
+// tile), one pixel per thread: twice the CTAs and warps of a full-tile CTA, which with 1024 tiles at
+// 512 x 512 left the SMs 60% empty.  Warp w reads chunk w of the half tile per view: its word (start and
+// K) two views ahead of use, its record (first cell and count, K weights in coalesced 128-byte loads)
+// one view ahead.
 template <int MODE>
 __global__ void __launch_bounds__(kBpThreads, 16) bp_records_kernel(FanDev G, const float *__restrict__ sino,
                                                                   const int *__restrict__ views, int nviews,
@@ -345,33 +345,20 @@ __global__ void __launch_bounds__(kBpThreads, 16) bp_records_kernel(FanDev G, co
     const int half = blockIdx.y & 1, ty = blockIdx.y >> 1;
     const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile + half * (kTile / 2);
     const int ix = blockIdx.x * kTile + lx, iy = ty * kTile + ly;
-    const int tile = ty * G.ntx + blockIdx.x;
-    const int ixc = min(ix, G.nx - 1), iyc = min(iy, G.ny - 1);
+    const unsigned group = (unsigned)(ty * G.ntx + blockIdx.x) * (kTile * kTile / kRecGroup) +
+                           (half * kBpThreads + threadIdx.x) / kRecGroup;
     float rho = 1.0f;
     if (MODE == BP_SOLVE_UPDATE) rho = __ldcg(&S.rho_tab[__ldcg(&S.counter[0])]);
     float acc = 0.0f;
-    const size_t vstride = (size_t)G.ntx * G.nty * (kTile * kTile);
-    const size_t base = (size_t)tile * (kTile * kTile) + half * kBpThreads + threadIdx.x;
-    float4 tn = make_float4(0.f, 0.f, 0.f, 0.f);
-    float2 an = make_float2(0.f, 0.f);
-    if (nviews > 0) {
-        const size_t i = (size_t)__ldg(&views[0]) * vstride + base;
-        tn = __ldcs(&G.foot_t[i]);
-        an = __ldcs(&G.foot_an[i]);
-    }
+    unsigned word = 0;
+    RecSlot r{};
+    if (nviews > 0) r = rec_fetch(G, rec_word(G, __ldg(&views[0]), group));
+    if (nviews > 1) word = rec_word(G, __ldg(&views[1]), group);
     for (int k = 0; k < nviews; k++) {
-        const float4 w = tn;
-        const float2 b = an;
-        if (k + 1 < nviews) {
-            const size_t i = (size_t)__ldg(&views[k + 1]) * vstride + base;
-            tn = __ldcs(&G.foot_t[i]);
-            an = __ldcs(&G.foot_an[i]);
-        }
-        const float *row = sino + (size_t)k * G.ns;
-        if (__float_as_int(b.y) == kWideRecord)  // rare: a footprint wider than a record
-            acc += wide_record_dot(G.foot_ovf, w, row, G.ns);
-        else
-            acc += record_dot(w, b, row, G.ns);
+        const RecSlot cur = r;
+        if (k + 1 < nviews) r = rec_fetch(G, word);
+        if (k + 2 < nviews) word = rec_word(G, __ldg(&views[k + 2]), group);
+        acc += rec_dot(G, cur, sino + (size_t)k * G.ns, [&] { return rec_word(G, __ldg(&views[k]), group); });
     }
     bp_epilogue<MODE>(G, S, xo, ix, iy, acc, rho, scale, accumulate);
     if (MODE == BP_SOLVE_UPDATE) {
@@ -550,7 +537,7 @@ cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *v
     dim3 grid(G.ntx, G.nty);
     SolveDev s0{};
     const SolveDev &SS = S ? *S : s0;
-    const bool stored = G.foot_t && G.bp_variant != BP_VAR_FLY;
+    const bool stored = G.rec_data && G.bp_variant != BP_VAR_FLY;
     if (stored) {
         const dim3 hgrid(G.ntx, 2 * G.nty);  // half tiles
         switch (mode) {

@@ -85,7 +85,7 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, int views_per_launch, int *fp_
     const int bps[2] = {BP_VAR_STORED, BP_VAR_FLY};
     float* xo = x;
     for (int c : bps) {
-        if (c == BP_VAR_STORED && !G.foot_t) continue;
+        if (c == BP_VAR_STORED && !G.rec_data) continue;
         FanDev T = G;
         T.bp_variant = c;
         float ms = 0.0f;

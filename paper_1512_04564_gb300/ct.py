@@ -87,6 +87,7 @@ def _load():
         "ct_sqs_diag_noalloc": [vp, vp, vp, vp],
         "ct_fbp": [vp, vp, vp, cint, vp],
         "ct_geom_precompute": [vp, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong), vp],
+        "ct_geom_matrix_info": [vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)],
         "ct_geom_autotune": [vp, cint, ip, ip, vp],
         "ct_reg_gradient": [vp, vp, vp, cfl, cfl, cint, vp, vp, vp],
         "ct_kappa": [vp, vp, vp, vp],
@@ -128,7 +129,8 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_geom_precompute", "ct_geom_autotune", "ct_forward",
+EXPORTED = ("ct_geom_create", "ct_geom_destroy", "ct_geom_precompute", "ct_geom_matrix_info", "ct_geom_autotune",
+            "ct_forward",
             "ct_pack_image", "ct_forward_packed", "ct_back", "ct_sqs_diag",
             "ct_sqs_diag_noalloc", "ct_fbp", "ct_reg_gradient", "ct_kappa", "ct_relaxed_oslalm_solve",
             "ct_relaxed_oslalm_solve_batched", "ct_debug_barrier", "ct_last_error", "ct_version", "ct_gemm_bf16", "ct_conv3x3_bf16",
@@ -255,6 +257,13 @@ def ct_geom_precompute(geom: Geometry, max_bytes: int = 0, stream=None) -> int:
     b = ctypes.c_ulonglong(0)
     _check(_lib.ct_geom_precompute(geom.handle, ctypes.c_ulonglong(int(max_bytes)), ctypes.byref(b), _stream(stream)))
     return int(b.value)
+
+
+def ct_geom_matrix_info(geom: Geometry) -> tuple[int, int]:
+    """(bytes of the resident matrix, bytes of its back-projector records)."""
+    m, r = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0)
+    _check(_lib.ct_geom_matrix_info(geom.handle, ctypes.byref(m), ctypes.byref(r)))
+    return int(m.value), int(r.value)
 
 
 FP_VARIANTS = {1: "resident rows", 2: "bundle", 3: "ray"}

@@ -344,7 +344,9 @@ def test_resident_matrix_limit_and_size(ct):
     ct.ct_forward(G, dev(phantom_image(g)), y)
     b = ct.ct_geom_precompute(G)
     ntiles = ((g.nx + 15) // 16) * ((g.ny + 15) // 16)
-    assert b > g.na * ntiles * 256 * 24
+    # the records: per view and 32 pixels at least the 16-bit first cells and counts, two weights, a word
+    m, r = ct.ct_geom_matrix_info(G)
+    assert m == b and g.na * ntiles * 8 * (64 + 256 + 4) <= r < b
     assert ct.ct_geom_precompute(G) == b  # idempotent
     y2 = torch.empty_like(y)
     ct.ct_forward(G, dev(phantom_image(g)), y2)
