@@ -20,6 +20,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "ct_internal.cuh"
@@ -647,6 +649,110 @@ void fill_solo_report(ct_solve_report *r, const ct_solve_params *p, const ct_sol
     }
 }
 
+// Large slices solved concurrently: the slices of one geometry (which owns its solver workspace) form a group;
+// up to kSoloLanes lanes, each a host thread running the single-slice graph solver on a stream of its own,
+// take the groups one after another from a queue ordered by work (pixels x views x iterations, largest
+// first) and solve a group's slices in turn.  Slices then share the GPU: a 384 x 384 slice's projector
+// launches fill about half of it, and one lane's per-iteration host step (the stopping test) leaves the
+// GPU to the others; taking groups from a queue keeps the lanes busy although slices stop after different
+// iteration counts.  Each report counts from `ev0` (recorded on the caller's
+// stream); *t_end receives the device time from ev0 to the last lane's end.
+constexpr int kSoloLanes = 4;
+
+ct_status solve_lanes(const ct_geom *const *geoms, const float *const *y, const float *const *w,
+                      const ct_solve_params *params, float *const *x_inout, const std::vector<int> &solo,
+                      ct_solve_report *reports, cudaStream_t caller, int dev, double *t_end)
+{
+    // geometries in order of first appearance, with their slices and work
+    std::vector<const ct_geom *> gkey;
+    std::vector<std::vector<int>> gsl;
+    std::vector<double> gwork;
+    for (int i : solo) {
+        size_t k = 0;
+        while (k < gkey.size() && gkey[k] != geoms[i]) k++;
+        if (k == gkey.size()) {
+            gkey.push_back(geoms[i]);
+            gsl.emplace_back();
+            gwork.push_back(0.0);
+        }
+        gsl[k].push_back(i);
+        gwork[k] += (double)geoms[i]->fan.nx * geoms[i]->fan.ny * geoms[i]->fan.na * std::max(params[i].n_iter, 1);
+    }
+    const int nl = std::min<int>(kSoloLanes, (int)gkey.size());
+    std::vector<int> queue(gkey.size());
+    for (size_t k = 0; k < queue.size(); k++) queue[k] = (int)k;
+    std::stable_sort(queue.begin(), queue.end(), [&](int a, int b) { return gwork[a] > gwork[b]; });
+    std::atomic<int> next{0};
+    cudaEvent_t ev0 = nullptr;
+    CT_CUDA_TRY(cudaEventCreate(&ev0), "event");
+    struct EvGuard {
+        cudaEvent_t e;
+        ~EvGuard() { cudaEventDestroy(e); }
+    } g0{ev0};
+    CT_CUDA_TRY(cudaEventRecord(ev0, caller), "event");
+    std::vector<ct_status> status(nl, CT_OK);
+    std::vector<std::string> message(nl);
+    std::vector<double> lane_end(nl, 0.0);
+    auto run = [&](int l) {
+        cudaStream_t ls = nullptr;
+        cudaEvent_t ev = nullptr;
+        auto fail = [&](ct_status st) {
+            status[l] = st;
+            message[l] = ct_last_error();
+        };
+        if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreate(&ev) != cudaSuccess || cudaStreamWaitEvent(ls, ev0, 0) != cudaSuccess) {
+            set_error("batched solve: setting up a lane stream failed");
+            fail(CT_ECUDA);
+        }
+        while (status[l] == CT_OK) {
+            const int gq = next.fetch_add(1);
+            if (gq >= (int)queue.size()) break;
+            for (const int i : gsl[queue[gq]]) {
+                ct_solve_params pi = params[i];
+                std::vector<float> trace(std::max(pi.n_iter, 1));
+                std::vector<double> times(std::max(pi.n_iter, 1));
+                ct_solve_report got{};
+                got.rmsd_trace_hu = trace.data();
+                got.iter_seconds = times.data();
+                float ms = 0.0f;
+                if (cudaEventRecord(ev, ls) != cudaSuccess) {
+                    set_error("batched solve: event record failed");
+                    fail(CT_ECUDA);
+                    break;
+                }
+                const ct_status st = ct_relaxed_oslalm_solve(geoms[i], y[i], w[i], &pi, x_inout[i], &got, ls);
+                if (st != CT_OK) {
+                    fail(st);
+                    break;
+                }
+                cudaEventElapsedTime(&ms, ev0, ev);  // both complete: the solve synchronised its stream
+                if (reports) fill_solo_report(&reports[i], &params[i], got, trace, times, ms * 1e-3);
+                lane_end[l] = ms * 1e-3 + got.seconds;
+            }
+        }
+        if (ev) cudaEventDestroy(ev);
+        if (ls) {
+            cudaStreamSynchronize(ls);
+            cudaStreamDestroy(ls);
+        }
+    };
+    if (nl == 1) {
+        run(0);
+    } else {
+        std::vector<std::thread> pool;
+        for (int l = 0; l < nl; l++) pool.emplace_back(run, l);
+        for (auto &t : pool) t.join();
+    }
+    for (int l = 0; l < nl; l++)
+        if (status[l] != CT_OK) {
+            set_error("%s", message[l].c_str());
+            return status[l];
+        }
+    *t_end = *std::max_element(lane_end.begin(), lane_end.end());
+    return CT_OK;
+}
+
 }  // namespace
 
 extern "C" ct_status ct_debug_barrier(long long max_polls, int missing)
@@ -675,22 +781,17 @@ extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms
         const ct_status st = validate_slice(i, geoms[i], y[i], w[i], x_inout[i], &params[i], dev);
         if (st != CT_OK) return st;
     }
+    // the large slices: the single-slice solver, concurrently over their geometries; the rest: one
+    // persistent launch after them
     std::vector<int> solo, shared;
     for (int i = 0; i < nslices; i++)
         ((long)geoms[i]->fan.nx * geoms[i]->fan.ny >= kSoloPixels ? solo : shared).push_back(i);
 
     double t_total = 0.0;  // device time of the slices solved so far
-    for (int i : solo) {
-        ct_solve_params q = params[i];
-        std::vector<float> trace(q.n_iter);
-        std::vector<double> times(q.n_iter);
-        ct_solve_report got{};
-        got.rmsd_trace_hu = trace.data();
-        got.iter_seconds = times.data();
-        const ct_status st = ct_relaxed_oslalm_solve(geoms[i], y[i], w[i], &q, x_inout[i], &got, stream);
+    if (!solo.empty()) {
+        const ct_status st = solve_lanes(geoms, y, w, params, x_inout, solo, reports, (cudaStream_t)stream, dev,
+                                         &t_total);
         if (st != CT_OK) return st;
-        if (reports) fill_solo_report(&reports[i], &params[i], got, trace, times, t_total);
-        t_total += got.seconds;
     }
     if (!shared.empty()) {
         const size_t n = shared.size();

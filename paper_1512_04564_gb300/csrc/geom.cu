@@ -1,14 +1,35 @@
 // Geometry object of the C ABI: validation, FP64-derived device tables, error state.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ct_internal.cuh"
 
 namespace ct {
+
+// f(lo, hi, worker) over [0, n) split into contiguous ranges, one per host thread (up to 16); every
+// element is computed as in a single-threaded loop, so the tables do not depend on the thread count.
+template <class F>
+static void host_parallel_for(int n, F f)
+{
+    const unsigned hc = std::thread::hardware_concurrency();
+    const int nw = std::max(1, std::min({(int)(hc ? hc : 1), 16, (n + 7) / 8}));
+    if (nw == 1) {
+        f(0, n, 0);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nw; w++) {
+        const int lo = (int)((long long)n * w / nw), hi = (int)((long long)n * (w + 1) / nw);
+        pool.emplace_back([=] { f(lo, hi, w); });
+    }
+    for (auto &t : pool) t.join();
+}
 
 namespace {
 thread_local std::string g_last_error;
@@ -246,15 +267,21 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     };
     // the grid: S = af + kxh px + kyh py over all tiles and points (|px|, |py| <= kAnchor / 2) stays below
     // 2^(24 - p) in magnitude, so FP32 holds every such S (a multiple of 2^-p) exactly
+    std::vector<double> kmax_w(16, 0.0);
+    host_parallel_for(na, [&](int v0, int v1, int w) {
+        double km = 0.0;
+        for (int v = v0; v < v1; v++) {
+            const double b = view_angle(v), cb = std::cos(b), sb = std::sin(b);
+            for (int ty = 0; ty < F.nay; ty++)
+                for (int tx = 0; tx < F.nax; tx++) {
+                    const TileGeo t = tile_geo(cb, sb, tx, ty);
+                    km = std::fmax(km, std::fabs(t.kx) + std::fabs(t.ky));
+                }
+        }
+        kmax_w[w] = km;
+    });
     double kmax = 0.0;
-    for (int v = 0; v < na; v++) {
-        const double b = view_angle(v), cb = std::cos(b), sb = std::sin(b);
-        for (int ty = 0; ty < F.nay; ty++)
-            for (int tx = 0; tx < F.nax; tx++) {
-                const TileGeo t = tile_geo(cb, sb, tx, ty);
-                kmax = std::fmax(kmax, std::fabs(t.kx) + std::fabs(t.ky));
-            }
-    }
+    for (double km : kmax_w) kmax = std::fmax(kmax, km);
     const double s_bound = 2.0 + kAnchor * kmax;  // af <= 1, plus twice the largest |kx px + ky py|
     const int p = 23 - (int)std::ceil(std::log2(s_bound));
     if (p < 8) {
@@ -263,7 +290,8 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         return CT_ENOTSUP;
     }
     const double qk = std::ldexp(1.0, p - 1), qa = std::ldexp(1.0, p);
-    for (int v = 0; v < na; v++) {
+    host_parallel_for(na, [&](int v0, int v1, int) {
+    for (int v = v0; v < v1; v++) {
         const double b = view_angle(v);
         const double cb = std::cos(b), sb = std::sin(b);
         cs[v] = make_float2((float)cb, (float)sb);
@@ -284,6 +312,7 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
                 q[2] = make_float4((float)t.mx, (float)t.my, nf, 0.0f);
             }
     }
+    });
     std::vector<int> ident(na);
     for (int v = 0; v < na; v++) ident[v] = v;
 
@@ -314,7 +343,8 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         const double mid = (d->orbit_start_deg + 0.5 * d->orbit_deg) * M_PI / 180.0;
         const double cover = d->nt * d->dt * d->dso / d->dsd;
         const double kA = d->dz * d->dsd / d->dt;
-        for (int v = 0; v < na; v++) {
+        host_parallel_for(na, [&](int v0, int v1, int) {
+        for (int v = v0; v < v1; v++) {
             const double b = (d->orbit_start_deg + (double)v * d->orbit_deg / na) * M_PI / 180.0;
             const double zsrc = d->pitch * cover * (b - mid) / (2.0 * M_PI);
             const double zb = (face0 - zsrc) / d->dz;
@@ -333,6 +363,7 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
                         make_float4(iah, (float)(ia - (double)iah), ah, (float)(a - (double)ah));
                 }
         }
+        });
         for (int t = 0; t < d->nt; t++) {
             const double vt = (t - (d->nt - 1) / 2.0 + d->offset_t) * d->dt;
             rc[t] = (float)std::sqrt(1.0 + (vt / d->dsd) * (vt / d->dsd));

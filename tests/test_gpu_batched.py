@@ -1,4 +1,5 @@
-"""Batched relaxed OS-LALM (one persistent launch) against the single-slice solver and the oracle.
+"""Batched relaxed OS-LALM against the single-slice solver and the oracle: the persistent launch of the
+small slices, and the large slices' single-slice solves on concurrent streams.
 
 A batch mixes image sizes, detector sizes, view counts and subset counts;
 some slices use the resident system matrix and some the on-the-fly
@@ -117,6 +118,38 @@ def test_large_slice_solved_alone_in_batch():
     assert r_small["iter_seconds"][-1] <= r_small["seconds"] * (1 + 1e-6)
     assert all(b > a for a, b in zip(r_big["iter_seconds"], r_big["iter_seconds"][1:]))
     assert len(r_big["rmsd_trace_hu"]) == 3 and r_big["rmsd_trace_hu"][-1] < r_big["rmsd_trace_hu"][0]
+
+
+def test_large_slices_of_several_geometries_run_concurrently():
+    """Large slices of different geometries are solved by the single-slice solver on concurrent streams
+    (one geometry's slices one after another, as they share its workspace): each result is the single
+    solve's, bit for bit, and each slice's times count from the call's start and stay within its total."""
+    from paper_1512_04564_gb300 import ct
+
+    probs = [_problem(6, 384, 400, 72, 0.5), _problem(7, 384, 320, 60, 0.55), _problem(8, 384, 400, 72, 0.5)]
+    Gs = [ct.Geometry.from_fan(probs[0][0]), ct.Geometry.from_fan(probs[1][0])]
+    G_of = [Gs[0], Gs[1], Gs[0]]  # the third slice shares the first one's geometry
+    ys = [torch.from_numpy(p[1]).cuda() for p in probs]
+    ws = [torch.from_numpy(p[2]).cuda() for p in probs]
+    params, singles = [], []
+    for i, (g, _, _) in enumerate(probs):
+        xr = torch.zeros(g.ny, g.nx, device="cuda")
+        ct.ct_relaxed_oslalm_solve(G_of[i], ys[i], ws[i], xr, M=1, n_iter=10, alpha=1.999, beta=BETA, delta=DELTA)
+        p = dict(M=6, n_iter=3, alpha=1.999, beta=BETA, delta=DELTA, x_ref=xr, hu_per_unit=HU)
+        xs = torch.zeros(g.ny, g.nx, device="cuda")
+        singles.append((xs, ct.ct_relaxed_oslalm_solve(G_of[i], ys[i], ws[i], xs, **p)))
+        params.append(p)
+    xb = [torch.zeros(p[0].ny, p[0].nx, device="cuda") for p in probs]
+    reps = ct.ct_relaxed_oslalm_solve_batched(G_of, ys, ws, xb, params)
+    torch.cuda.synchronize()
+    for i in range(3):
+        assert torch.equal(xb[i], singles[i][0]), i
+        assert reps[i]["rmsd_trace_hu"] == singles[i][1]["rmsd_trace_hu"], i
+        t = reps[i]["iter_seconds"]
+        assert len(t) == 3 and 0 < t[0] < t[1] < t[2] <= reps[i]["seconds"] * (1 + 1e-6), (i, t)
+        assert reps[i]["seconds"] == reps[0]["seconds"]
+    # the two slices of one geometry ran one after the other
+    assert reps[0]["iter_seconds"][-1] <= reps[2]["iter_seconds"][0] or reps[2]["iter_seconds"][-1] <= reps[0]["iter_seconds"][0]
 
 
 def test_batched_slice_matches_oracle():
