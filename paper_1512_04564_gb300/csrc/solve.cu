@@ -26,32 +26,40 @@ __global__ void __launch_bounds__(256) rmsd_kernel(FanDev G, const float *__rest
                                                    float r2max, double *__restrict__ partial, int *__restrict__ counter,
                                                    float *__restrict__ trace, int M, float hu)
 {
-    __shared__ double ss[256];
-    __shared__ double sc[256];
+    __shared__ double ss[8];
+    __shared__ double sc[8];
     double s = 0.0, c = 0.0;
-    const long n = (long)G.nx * G.ny;
-    for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
-        const int ix = (int)(j % G.nx), iy = (int)(j / G.nx);
-        const float X = ((float)ix - G.cxo) * G.dx, Y = ((float)iy - G.cyo) * G.dy;
-        if (fmaf(X, X, Y * Y) <= r2max) {
-            const double d = (double)x[j] - (double)xr[j];
-            s += d * d;
-            c += 1.0;
+    // rows by block, columns by thread: the pixel's position without integer division
+    for (int iy = blockIdx.x; iy < G.ny; iy += gridDim.x) {
+        const float Y = ((float)iy - G.cyo) * G.dy;
+        const size_t row = (size_t)iy * G.nx;
+        for (int ix = threadIdx.x; ix < G.nx; ix += blockDim.x) {
+            const float X = ((float)ix - G.cxo) * G.dx;
+            if (fmaf(X, X, Y * Y) <= r2max) {
+                const double d = (double)x[row + ix] - (double)xr[row + ix];
+                s += d * d;
+                c += 1.0;
+            }
         }
     }
-    ss[threadIdx.x] = s;
-    sc[threadIdx.x] = c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ss[threadIdx.x >> 5] = s;
+        sc[threadIdx.x >> 5] = c;
+    }
     __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            ss[threadIdx.x] += ss[threadIdx.x + o];
-            sc[threadIdx.x] += sc[threadIdx.x + o];
-        }
-        __syncthreads();
-    }
     if (threadIdx.x == 0) {
-        partial[2 * blockIdx.x] = ss[0];
-        partial[2 * blockIdx.x + 1] = sc[0];
+        double S0 = 0.0, C0 = 0.0;
+        for (int q = 0; q < 8; q++) {
+            S0 += ss[q];
+            C0 += sc[q];
+        }
+        partial[2 * blockIdx.x] = S0;
+        partial[2 * blockIdx.x + 1] = C0;
         __threadfence();
         const int done = atomicAdd(&counter[2], 1);
         if (done == (int)gridDim.x - 1) {
