@@ -41,6 +41,7 @@ struct FanDev {
     // footprints are computed on the fly
     const unsigned char *rec_data;
     const unsigned int *rec_grp;  // [na][ntiles][8]: the chunk's start in 32-byte units (bits 0-27) and K (28-31)
+    int bp_vs;                    // warps per record chunk of the back-projector, each on every bp_vs-th view
     const long long *row_ptr; // [na*ns + 1]: start of each ray's entry pairs (ray-major; the entries in march
                               // order, two per pair, a ray with an odd count padded by a zero entry)
     const float2 *row_w;      // [pairs]: a_ij of the pair's two entries

@@ -327,6 +327,17 @@ cudaError_t build_matrix(ct_geom *g, unsigned long long max_bytes, cudaStream_t 
     g->fan.ray_order = g->d_ray_order;
     g->fan.rec_data = rdata;
     g->fan.rec_grp = rgrp;
+    {   // view split of the back-projector: 1, 2 or 4 warps per chunk, the most that keep its CTAs of 4 warps
+        // (16 per SM) within one wave; small images then still fill the GPU (a fixed rule of the geometry and
+        // the device, so that a solve and its resumption run the same arithmetic)
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const long half_tiles = 2L * G.ntx * G.nty, slots = 16L * (nsm > 0 ? nsm : 1);
+        int vs = 1;
+        while (vs < 4 && half_tiles * vs * 2 <= slots) vs *= 2;
+        g->fan.bp_vs = vs;
+    }
     return cudaSuccess;
 }
 

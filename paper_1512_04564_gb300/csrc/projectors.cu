@@ -376,6 +376,61 @@ __global__ void __launch_bounds__(kBpThreads, 16) bp_records_kernel(FanDev G, co
     }
 }
 
+// The same with the views split (images too small for bp_records_kernel to fill the SMs: a warp walking all
+// of a launch's views one after another is bound by their latency, not the bytes): VS = 2 or 4 warps share a
+// record chunk, warp q taking views q, q + VS, ...; their sums are added in a fixed order (q = 0, 1, ...)
+// through shared memory.  A CTA of 4 warps covers 4 / VS chunks.  (Grids under one wave: more registers.)
+template <int MODE, int VS>
+__global__ void __launch_bounds__(kBpThreads, 8) bp_records_split_kernel(FanDev G, const float *__restrict__ sino,
+                                                                  const int *__restrict__ views, int nviews,
+                                                                  float *__restrict__ xo, float scale,
+                                                                  int accumulate, SolveDev S)
+{
+    constexpr int kCpc = (kBpThreads / kRecGroup) / VS;           // chunks per CTA
+    constexpr int kSubs = (kTile * kTile / kRecGroup) / kCpc;      // CTAs per tile
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = blockIdx.y % kSubs, ty = blockIdx.y / kSubs;
+    const int chunk = sub * kCpc + warp / VS, q = warp % VS;       // chunk of the tile, view phase
+    const int slot = chunk * kRecGroup + lane;
+    const int ix = blockIdx.x * kTile + (slot & (kTile - 1)), iy = ty * kTile + slot / kTile;
+    const unsigned group = (unsigned)(ty * G.ntx + blockIdx.x) * (kTile * kTile / kRecGroup) + chunk;
+    float rho = 1.0f;
+    if (MODE == BP_SOLVE_UPDATE) rho = __ldcg(&S.rho_tab[__ldcg(&S.counter[0])]);
+    float acc = 0.0f;
+    unsigned word = 0;
+    RecSlot r{};
+    if (q < nviews) r = rec_fetch(G, rec_word(G, __ldg(&views[q]), group));
+    if (q + VS < nviews) word = rec_word(G, __ldg(&views[q + VS]), group);
+    for (int k = q; k < nviews; k += VS) {
+        const RecSlot cur = r;
+        if (k + VS < nviews) r = rec_fetch(G, word);
+        if (k + 2 * VS < nviews) word = rec_word(G, __ldg(&views[k + 2 * VS]), group);
+        acc += rec_dot(G, cur, sino + (size_t)k * G.ns, [&] { return rec_word(G, __ldg(&views[k]), group); });
+    }
+    {
+        __shared__ float s_part[kBpThreads];
+        s_part[threadIdx.x] = acc;
+        __syncthreads();
+        if (q == 0)
+#pragma unroll
+            for (int p = 1; p < VS; p++) acc += s_part[threadIdx.x + 32 * p];
+    }
+    if (q == 0) bp_epilogue<MODE>(G, S, xo, ix, iy, acc, rho, scale, accumulate);
+    if (MODE == BP_SOLVE_UPDATE) {
+        // the last block to finish advances the subiteration counter (rho for the next one)
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const int done = atomicAdd(&S.counter[1], 1);
+            if (done == (int)(gridDim.x * gridDim.y) - 1) {
+                S.counter[1] = 0;
+                S.counter[0] += 1;
+                __threadfence();
+            }
+        }
+    }
+}
+
 // Back-projection with the footprints evaluated on the fly: one CTA per 16x16 tile (four 8x8 anchor
 // tiles), one pixel per thread.  A pixel corner is shared by up to four pixels, so per view the CTA
 // first computes the detector coordinates (S, L) of the 4 x 9 x 9 corners of its anchor tiles into
@@ -539,12 +594,26 @@ cudaError_t launch_bp(const FanDev &G, int mode, const float *sino, const int *v
     const SolveDev &SS = S ? *S : s0;
     const bool stored = G.rec_data && G.bp_variant != BP_VAR_FLY;
     if (stored) {
-        const dim3 hgrid(G.ntx, 2 * G.nty);  // half tiles
-        switch (mode) {
-        case BP_PLAIN: bp_records_kernel<BP_PLAIN><<<hgrid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
-        case BP_SOLVE_INIT: bp_records_kernel<BP_SOLVE_INIT><<<hgrid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
-        default: bp_records_kernel<BP_SOLVE_UPDATE><<<hgrid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+        const int vs = G.bp_vs == 4 ? 4 : (G.bp_vs == 2 ? 2 : 1);
+        const dim3 hgrid(G.ntx, 2 * vs * G.nty);  // 2 vs CTAs per tile
+#define CT_BP_REC(VS)                                                                                                     \
+        switch (mode) {                                                                                                   \
+        case BP_PLAIN: bp_records_split_kernel<BP_PLAIN, VS><<<hgrid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break; \
+        case BP_SOLVE_INIT: bp_records_split_kernel<BP_SOLVE_INIT, VS><<<hgrid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break; \
+        default: bp_records_split_kernel<BP_SOLVE_UPDATE, VS><<<hgrid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break; \
         }
+        if (vs == 1) {
+            switch (mode) {
+            case BP_PLAIN: bp_records_kernel<BP_PLAIN><<<hgrid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+            case BP_SOLVE_INIT: bp_records_kernel<BP_SOLVE_INIT><<<hgrid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+            default: bp_records_kernel<BP_SOLVE_UPDATE><<<hgrid, kBpThreads, 0, st>>>(G, sino, views, nviews, x, scale, accumulate, SS); break;
+            }
+        } else if (vs == 2) {
+            CT_BP_REC(2)
+        } else {
+            CT_BP_REC(4)
+        }
+#undef CT_BP_REC
         return cudaGetLastError();
     }
     switch (mode) {

@@ -129,7 +129,7 @@ def test_kernel_digest_ignores_comments_only(tmp_path):
     p.write_text(text.replace("fp_csr_kernel(FanDev G", "fp_csr_kernel(FanDev G /* a comment */", 1))
     assert bench._source_digest(str(tmp_path)) == d0
     for old, new in (("8 * __ldg(&G.ray_order[rank])", "8 * __ldg(&G.ray_order[rank + 0])"),  # forward
-                     ("(half * kBpThreads + threadIdx.x) / kRecGroup", "(threadIdx.x + half * kBpThreads) / kRecGroup")):  # back
+                     ("const int slot = chunk * kRecGroup + lane;", "const int slot = lane + chunk * kRecGroup;")):  # back
         assert text.count(old) == 1
         p.write_text(text.replace(old, new))
         assert bench._source_digest(str(tmp_path)) != d0
