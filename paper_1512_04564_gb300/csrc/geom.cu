@@ -32,6 +32,79 @@ static void host_parallel_for(int n, F f)
 }
 
 namespace {
+
+// Anchor tables in FP64 on the device, one thread per (view, 8x8 anchor tile): u at the tile centre and its
+// derivatives per pixel step.  For a tile centre a (relative to the source, view frame) and a step
+// d = R(beta) (px dx, py dy), the fan angle changes by atan(N / (1 + e)), N = cross(a, d) / |a|^2,
+// e = a.d / |a|^2, both linear in (px, py).  The views' cos and sin come from the host.
+struct AnchorParams {
+    int na, nax, nay;
+    double cxo, cyo, dx, dy, dso, inv_dg, c0;
+    float dso_f;  // the kernels' FP32 dso
+};
+
+struct TileGeo {
+    double tpar, tperp, u, kx, ky, mx, my;
+};
+
+__device__ TileGeo tile_geo(const AnchorParams &P, double cb, double sb, int tx, int ty)
+{
+    const double X = (tx * kAnchor + (double)kAnchorHalf - P.cxo) * P.dx;
+    const double Y = (ty * kAnchor + (double)kAnchorHalf - P.cyo) * P.dy;
+    TileGeo t;
+    t.tpar = P.dso + X * cb + Y * sb;
+    t.tperp = -X * sb + Y * cb;
+    const double a2 = t.tpar * t.tpar + t.tperp * t.tperp;
+    t.u = atan2(t.tperp, t.tpar) * P.inv_dg + P.c0;
+    // a step along x: d = dx (cb, -sb) in the view frame; along y: d = dy (sb, cb)
+    t.kx = (t.tpar * (-P.dx * sb) - t.tperp * (P.dx * cb)) / a2 * P.inv_dg;
+    t.ky = (t.tpar * (P.dy * cb) - t.tperp * (P.dy * sb)) / a2 * P.inv_dg;
+    t.mx = (t.tpar * (P.dx * cb) + t.tperp * (-P.dx * sb)) / a2;
+    t.my = (t.tpar * (P.dy * sb) + t.tperp * (P.dy * cb)) / a2;
+    return t;
+}
+
+// max over (view, tile) of |kx| + |ky| (non-negative doubles order as their bit patterns)
+__global__ void __launch_bounds__(256) anchor_kmax_kernel(AnchorParams P, const double2 *__restrict__ vcs,
+                                                          unsigned long long *kmax)
+{
+    const long long n = (long long)P.na * P.nax * P.nay;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double km = 0.0;
+    if (i < n) {
+        const int nt = P.nax * P.nay, v = (int)(i / nt), tile = (int)(i - (long long)v * nt);
+        const double2 c = vcs[v];
+        const TileGeo t = tile_geo(P, c.x, c.y, tile % P.nax, tile / P.nax);
+        km = fabs(t.kx) + fabs(t.ky);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) km = fmax(km, __shfl_xor_sync(0xffffffffu, km, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(kmax, (unsigned long long)__double_as_longlong(km));
+}
+
+// the anchors, with af and kxh, kyh rounded onto the grid of 1/qa and 1/qk cells
+__global__ void __launch_bounds__(256) anchor_fill_kernel(AnchorParams P, const double2 *__restrict__ vcs, double qk,
+                                                          double qa, float4 *__restrict__ anc)
+{
+    const long long n = (long long)P.na * P.nax * P.nay;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int nt = P.nax * P.nay, v = (int)(i / nt), tile = (int)(i - (long long)v * nt);
+    const double2 c = vcs[v];
+    const TileGeo t = tile_geo(P, c.x, c.y, tile % P.nax, tile / P.nax);
+    const double kxh = rint(t.kx * qk) / qk, kyh = rint(t.ky * qk) / qk;
+    const double nn = floor(t.u), fr = t.u - nn;
+    const double af = rint(fr * qa) / qa;
+    float4 *q = anc + 3 * i;
+    // t_par as dso (the kernels' float) + a small float
+    q[0] = make_float4((float)(t.tpar - (double)P.dso_f), (float)t.tperp, (float)af, (float)(fr - af));
+    q[1] = make_float4((float)kxh, (float)(t.kx - kxh), (float)kyh, (float)(t.ky - kyh));
+    q[2] = make_float4((float)t.mx, (float)t.my, __int_as_float((int)nn), 0.0f);  // the base cell, as int bits
+}
+
+}  // namespace
+
+namespace {
 thread_local std::string g_last_error;
 }
 
@@ -238,93 +311,74 @@ extern "C" ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     const int na = d->na, ntiles = F.nax * F.nay;  // anchor tiles
     std::vector<float2> cs(na);
     std::vector<float> bet(na);
-    std::vector<float4> anc((size_t)na * ntiles * 3);
-    const double c0 = (d->ns - 1) / 2.0 - d->offset_s;
-    const double inv_dg = 1.0 / dg;
-    // Anchor tables (FP64): u at each 8x8 tile centre and its derivatives per pixel step.  For a tile
-    // centre a (relative to the source, view frame) and a step d = R(beta) (px dx, py dy), the fan angle
-    // changes by atan(N / (1 + e)), N = cross(a, d) / |a|^2, e = a.d / |a|^2, both linear in (px, py).
-    auto view_angle = [&](int v) {
+    std::vector<double2> vcs(na);  // cos, sin of each view angle (FP64) for the anchor kernels
+    for (int v = 0; v < na; v++) {
         double deg = std::fmod(d->orbit_start_deg + (double)v * d->orbit_deg / na, 360.0);
         if (deg < 0) deg += 360.0;
-        return deg * M_PI / 180.0;
-    };
-    struct TileGeo { double tpar, tperp, u, kx, ky, mx, my; };
-    auto tile_geo = [&](double cb, double sb, int tx, int ty) {
-        const double X = (tx * kAnchor + (double)kAnchorHalf - cxo) * d->dx;
-        const double Y = (ty * kAnchor + (double)kAnchorHalf - cyo) * d->dy;
-        TileGeo t;
-        t.tpar = d->dso + X * cb + Y * sb;
-        t.tperp = -X * sb + Y * cb;
-        const double a2 = t.tpar * t.tpar + t.tperp * t.tperp;
-        t.u = std::atan2(t.tperp, t.tpar) * inv_dg + c0;
-        // a step along x: d = dx (cb, -sb) in the view frame; along y: d = dy (sb, cb)
-        t.kx = (t.tpar * (-d->dx * sb) - t.tperp * (d->dx * cb)) / a2 * inv_dg;
-        t.ky = (t.tpar * (d->dy * cb) - t.tperp * (d->dy * sb)) / a2 * inv_dg;
-        t.mx = (t.tpar * (d->dx * cb) + t.tperp * (-d->dx * sb)) / a2;
-        t.my = (t.tpar * (d->dy * sb) + t.tperp * (d->dy * cb)) / a2;
-        return t;
-    };
-    // the grid: S = af + kxh px + kyh py over all tiles and points (|px|, |py| <= kAnchor / 2) stays below
-    // 2^(24 - p) in magnitude, so FP32 holds every such S (a multiple of 2^-p) exactly
-    std::vector<double> kmax_w(16, 0.0);
-    host_parallel_for(na, [&](int v0, int v1, int w) {
-        double km = 0.0;
-        for (int v = v0; v < v1; v++) {
-            const double b = view_angle(v), cb = std::cos(b), sb = std::sin(b);
-            for (int ty = 0; ty < F.nay; ty++)
-                for (int tx = 0; tx < F.nax; tx++) {
-                    const TileGeo t = tile_geo(cb, sb, tx, ty);
-                    km = std::fmax(km, std::fabs(t.kx) + std::fabs(t.ky));
-                }
-        }
-        kmax_w[w] = km;
-    });
-    double kmax = 0.0;
-    for (double km : kmax_w) kmax = std::fmax(kmax, km);
-    const double s_bound = 2.0 + kAnchor * kmax;  // af <= 1, plus twice the largest |kx px + ky py|
-    const int p = 23 - (int)std::ceil(std::log2(s_bound));
-    if (p < 8) {
-        set_error("detector cells too fine for the pixels: a tile's footprint spans %.0f cells", s_bound);
-        free_geom(g);
-        return CT_ENOTSUP;
-    }
-    const double qk = std::ldexp(1.0, p - 1), qa = std::ldexp(1.0, p);
-    host_parallel_for(na, [&](int v0, int v1, int) {
-    for (int v = v0; v < v1; v++) {
-        const double b = view_angle(v);
-        const double cb = std::cos(b), sb = std::sin(b);
+        const double b = deg * M_PI / 180.0, cb = std::cos(b), sb = std::sin(b);
+        vcs[v] = make_double2(cb, sb);
         cs[v] = make_float2((float)cb, (float)sb);
         bet[v] = (float)b;
-        for (int ty = 0; ty < F.nay; ty++)
-            for (int tx = 0; tx < F.nax; tx++) {
-                const TileGeo t = tile_geo(cb, sb, tx, ty);
-                const double kxh = std::nearbyint(t.kx * qk) / qk, kyh = std::nearbyint(t.ky * qk) / qk;
-                const double n = std::floor(t.u), fr = t.u - n;
-                const double af = std::nearbyint(fr * qa) / qa;
-                float4 *q = &anc[((size_t)v * ntiles + ty * F.nax + tx) * 3];
-                // t_par as dso (the kernels' float) + a small float
-                q[0] = make_float4((float)(t.tpar - (double)F.dso), (float)t.tperp, (float)af, (float)(fr - af));
-                q[1] = make_float4((float)kxh, (float)(t.kx - kxh), (float)kyh, (float)(t.ky - kyh));
-                const int ni = (int)n;
-                float nf;
-                std::memcpy(&nf, &ni, sizeof nf);  // the base cell, as the bits of an int
-                q[2] = make_float4((float)t.mx, (float)t.my, nf, 0.0f);
-            }
     }
-    });
     std::vector<int> ident(na);
     for (int v = 0; v < na; v++) ident[v] = v;
-
+    AnchorParams AP;
+    AP.na = na;
+    AP.nax = F.nax;
+    AP.nay = F.nay;
+    AP.cxo = cxo;
+    AP.cyo = cyo;
+    AP.dx = d->dx;
+    AP.dy = d->dy;
+    AP.dso = d->dso;
+    AP.inv_dg = 1.0 / dg;
+    AP.c0 = (d->ns - 1) / 2.0 - d->offset_s;
+    AP.dso_f = F.dso;
+    const long long n_anchor = (long long)na * ntiles;
+    const unsigned anchor_blocks = (unsigned)((n_anchor + 255) / 256);
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_anchor, sizeof(float4) * anc.size());
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_anchor, sizeof(float4) * 3 * (size_t)n_anchor);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_view_cs, sizeof(float2) * na);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_view_beta, sizeof(float) * na);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_views_all, sizeof(int) * na);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_views_stage, sizeof(int) * na);
     const size_t rows = helical ? (size_t)d->nt : 1;
     if (e == cudaSuccess) e = cudaMalloc(&g->d_sino_ws, sizeof(float) * (size_t)na * d->ns * rows);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d_anchor, anc.data(), sizeof(float4) * anc.size(), cudaMemcpyHostToDevice);
+    // the anchor tables: the largest |du/dpx| + |du/dpy| fixes the grid of the exact FP32 linear term (S =
+    // af + kxh px + kyh py over all tiles and points |px|, |py| <= kAnchor / 2 stays below 2^(24 - p) in
+    // magnitude, so FP32 holds every such S, a multiple of 2^-p, exactly), then the tables themselves
+    double2 *d_vcs = nullptr;
+    unsigned long long *d_kmax = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&d_vcs, sizeof(double2) * na + 256);
+    if (e == cudaSuccess) {
+        d_kmax = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(d_vcs) + ((sizeof(double2) * na + 15) & ~(size_t)15));
+        e = cudaMemcpy(d_vcs, vcs.data(), sizeof(double2) * na, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemset(d_kmax, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) {
+        anchor_kmax_kernel<<<anchor_blocks, 256>>>(AP, d_vcs, d_kmax);
+        e = cudaGetLastError();
+    }
+    unsigned long long kbits = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&kbits, d_kmax, sizeof(kbits), cudaMemcpyDeviceToHost);
+    int p = 0;
+    double s_bound = 0.0;
+    if (e == cudaSuccess) {
+        double kmax;
+        std::memcpy(&kmax, &kbits, sizeof kmax);
+        s_bound = 2.0 + kAnchor * kmax;  // af <= 1, plus twice the largest |kx px + ky py|
+        p = 23 - (int)std::ceil(std::log2(s_bound));
+        if (p < 8) {
+            cudaFree(d_vcs);
+            set_error("detector cells too fine for the pixels: a tile's footprint spans %.0f cells", s_bound);
+            free_geom(g);
+            return CT_ENOTSUP;
+        }
+        anchor_fill_kernel<<<anchor_blocks, 256>>>(AP, d_vcs, std::ldexp(1.0, p - 1), std::ldexp(1.0, p), g->d_anchor);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    cudaFree(d_vcs);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_view_cs, cs.data(), sizeof(float2) * na, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_view_beta, bet.data(), sizeof(float) * na, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_views_all, ident.data(), sizeof(int) * na, cudaMemcpyHostToDevice);
