@@ -328,7 +328,9 @@ def batch_result(args, n_iter=100):
                 small += ti
         l_tol.append(tot if ok else None)
         l_small.append(small)
-    # the batched call's parts: the large slices alone first, then one persistent launch for the rest
+    # the batched call's path: slices of several geometries all run the single-slice solver on concurrent
+    # lanes; one geometry's large slices alone, then one persistent launch for the rest
+    several = len({id(G) for G in G_l}) > 1
     solo_end = max((reps[i]["seconds_to_tol"] for i in solo), default=0.0)
     shared_end = max((reps[i]["seconds_to_tol"] for i in range(n) if i not in solo), default=0.0)
     reached = sum(1 for r in reps if r["seconds_to_tol"] > 0)
@@ -353,8 +355,11 @@ def batch_result(args, n_iter=100):
         "batched_seconds_to_all_at_tol": bt, "loop_seconds_to_all_at_tol": lt,
         "batched_over_loop": (bt / lt) if bt and lt else None,
         "batched_seconds_full_call": statistics.mean(b_all),
-        "parts": {"large_slices": len(solo), "batched_large_alone_s": solo_end,
-                  "batched_persistent_launch_s": shared_end - solo_end,
+        "parts": {"path": ("every slice on concurrent lanes (several geometries)" if several else
+                           "large slices alone, then one persistent launch"),
+                  "large_slices": len(solo),
+                  "batched_large_alone_s": None if several else solo_end,
+                  "batched_persistent_launch_s": None if several else shared_end - solo_end,
                   "loop_small_slices_s": statistics.mean(l_small),
                   "loop_large_slices_s": (statistics.mean(l_tol) - statistics.mean(l_small)) if lt else None},
         "geometries": len(geoms), "resident_matrix_bytes": mat_bytes, "geometry_setup_s": round(t_geo, 3),

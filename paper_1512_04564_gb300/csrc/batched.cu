@@ -649,13 +649,13 @@ void fill_solo_report(ct_solve_report *r, const ct_solve_params *p, const ct_sol
     }
 }
 
-// Large slices solved concurrently: the slices of one geometry (which owns its solver workspace) form a group;
+// Slices solved concurrently: the slices of one geometry (which owns its solver workspace) form a group;
 // up to kSoloLanes lanes, each a host thread running the single-slice graph solver on a stream of its own,
 // take the groups one after another from a queue ordered by work (pixels x views x iterations, largest
 // first) and solve a group's slices in turn.  Slices then share the GPU: a 384 x 384 slice's projector
-// launches fill about half of it, and one lane's per-iteration host step (the stopping test) leaves the
-// GPU to the others; taking groups from a queue keeps the lanes busy although slices stop after different
-// iteration counts.  Each report counts from `ev0` (recorded on the caller's
+// launches fill about half of it, a 256 x 256 slice's less, and one lane's per-iteration host step (the
+// stopping test) leaves the GPU to the others; taking groups from a queue keeps the lanes busy although
+// slices stop after different iteration counts.  Each report counts from `ev0` (recorded on the caller's
 // stream); *t_end receives the device time from ev0 to the last lane's end.
 constexpr int kSoloLanes = 4;
 
@@ -781,11 +781,14 @@ extern "C" ct_status ct_relaxed_oslalm_solve_batched(const ct_geom *const *geoms
         const ct_status st = validate_slice(i, geoms[i], y[i], w[i], x_inout[i], &params[i], dev);
         if (st != CT_OK) return st;
     }
-    // the large slices: the single-slice solver, concurrently over their geometries; the rest: one
-    // persistent launch after them
+    // slices of two or more geometries: every slice by the single-slice solver, concurrently over the
+    // geometries (lanes); slices of one geometry (they share its workspace, so run one at a time): the large
+    // ones alone, the rest in one persistent launch after them
+    bool several = false;
+    for (int i = 1; i < nslices; i++) several = several || geoms[i] != geoms[0];
     std::vector<int> solo, shared;
     for (int i = 0; i < nslices; i++)
-        ((long)geoms[i]->fan.nx * geoms[i]->fan.ny >= kSoloPixels ? solo : shared).push_back(i);
+        ((several || (long)geoms[i]->fan.nx * geoms[i]->fan.ny >= kSoloPixels) ? solo : shared).push_back(i);
 
     double t_total = 0.0;  // device time of the slices solved so far
     if (!solo.empty()) {

@@ -1,5 +1,6 @@
-"""Batched relaxed OS-LALM against the single-slice solver and the oracle: the persistent launch of the
-small slices, and the large slices' single-slice solves on concurrent streams.
+"""Batched relaxed OS-LALM against the single-slice solver and the oracle: slices of several geometries on
+concurrent lanes of the single-slice solver, and the slices of one geometry (its large slices one after
+another, its small ones in one persistent launch).
 
 A batch mixes image sizes, detector sizes, view counts and subset counts;
 some slices use the resident system matrix and some the on-the-fly
@@ -87,37 +88,65 @@ def test_batched_matches_single_slice_solves():
         assert all(b > a for a, b in zip(reps[i]["iter_seconds"], reps[i]["iter_seconds"][1:]))
 
 
-def test_large_slice_solved_alone_in_batch():
-    """A slice of >= 384 x 384 pixels runs the single-slice solver inside the batched call."""
+def test_large_slices_of_one_geometry_solved_one_after_another():
+    """Slices of >= 384 x 384 pixels run the single-slice solver inside the batched call; slices of one
+    geometry share its workspace, so they are solved one after the other: each result is the single
+    solve's, bit for bit, and the second slice's iterations start after the first's end."""
     from paper_1512_04564_gb300 import ct
 
-    big = _problem(6, 384, 400, 72, 0.5)
-    small = _problem(*CASES[0][:5])
-    Gs = [ct.Geometry.from_fan(p[0]) for p in (big, small)]
-    ys = [torch.from_numpy(p[1]).cuda() for p in (big, small)]
-    ws = [torch.from_numpy(p[2]).cuda() for p in (big, small)]
-    refs, singles = [], []
-    for i, (g, _, _) in enumerate((big, small)):
+    probs = [_problem(6, 384, 400, 72, 0.5), _problem(10, 384, 400, 72, 0.5)]
+    G = ct.Geometry.from_fan(probs[0][0])
+    ys = [torch.from_numpy(p[1]).cuda() for p in probs]
+    ws = [torch.from_numpy(p[2]).cuda() for p in probs]
+    params, singles = [], []
+    for i, (g, _, _) in enumerate(probs):
         xr = torch.zeros(g.ny, g.nx, device="cuda")
-        ct.ct_relaxed_oslalm_solve(Gs[i], ys[i], ws[i], xr, M=1, n_iter=20, alpha=1.999, beta=BETA, delta=DELTA)
-        refs.append(xr)
+        ct.ct_relaxed_oslalm_solve(G, ys[i], ws[i], xr, M=1, n_iter=20, alpha=1.999, beta=BETA, delta=DELTA)
+        p = dict(M=6, n_iter=3, alpha=1.999, beta=BETA, delta=DELTA, x_ref=xr, hu_per_unit=HU)
         xs = torch.zeros(g.ny, g.nx, device="cuda")
-        ct.ct_relaxed_oslalm_solve(Gs[i], ys[i], ws[i], xs, M=6, n_iter=3, alpha=1.999, beta=BETA, delta=DELTA)
-        singles.append(xs)
-    params = [dict(M=6, n_iter=3, alpha=1.999, beta=BETA, delta=DELTA, x_ref=refs[i], hu_per_unit=HU)
-              for i in range(2)]
-    xb = [torch.zeros(p[0].ny, p[0].nx, device="cuda") for p in (big, small)]
-    reps = ct.ct_relaxed_oslalm_solve_batched([Gs[1], Gs[0]], [ys[1], ys[0]], [ws[1], ws[0]], [xb[1], xb[0]],
-                                              [params[1], params[0]])
-    for i, (g, _, _) in enumerate((big, small)):
-        assert _hu_rmsd(xb[i].cpu().numpy(), singles[i].cpu().numpy(), g) <= 0.01, i
-    r_small, r_big = reps
-    # the large slice is solved first, the batched rest after it; one total time for the call
-    assert r_small["seconds"] == r_big["seconds"]
-    assert r_big["iter_seconds"][-1] <= r_small["iter_seconds"][0]
-    assert r_small["iter_seconds"][-1] <= r_small["seconds"] * (1 + 1e-6)
-    assert all(b > a for a, b in zip(r_big["iter_seconds"], r_big["iter_seconds"][1:]))
-    assert len(r_big["rmsd_trace_hu"]) == 3 and r_big["rmsd_trace_hu"][-1] < r_big["rmsd_trace_hu"][0]
+        singles.append((xs, ct.ct_relaxed_oslalm_solve(G, ys[i], ws[i], xs, **p)))
+        params.append(p)
+    xb = [torch.zeros(p[0].ny, p[0].nx, device="cuda") for p in probs]
+    reps = ct.ct_relaxed_oslalm_solve_batched([G, G], ys, ws, xb, params)
+    torch.cuda.synchronize()
+    for i in range(2):
+        assert torch.equal(xb[i], singles[i][0]), i
+        assert len(reps[i]["rmsd_trace_hu"]) == 3 and reps[i]["rmsd_trace_hu"][-1] < reps[i]["rmsd_trace_hu"][0]
+        assert all(b > a for a, b in zip(reps[i]["iter_seconds"], reps[i]["iter_seconds"][1:]))
+    assert reps[0]["seconds"] == reps[1]["seconds"]
+    assert reps[0]["iter_seconds"][-1] <= reps[1]["iter_seconds"][0]
+    assert reps[1]["iter_seconds"][-1] <= reps[1]["seconds"] * (1 + 1e-6)
+
+
+def test_persistent_launch_matches_single_slice_solves():
+    """Small slices of one geometry share one persistent launch (different data and subset counts): each
+    matches its single-slice solve (RMSD <= 0.01 HU: the same arithmetic with a different summation order
+    in the projectors), the traces too."""
+    from paper_1512_04564_gb300 import ct
+
+    g0 = _problem(1, 64, 96, 90, 2.0)[0]
+    G = ct.Geometry.from_fan(g0)
+    ct.ct_geom_precompute(G)
+    probs = [_problem(seed, 64, 96, 90, 2.0) for seed in (1, 4, 9)]
+    Ms = (5, 9, 7)
+    ys = [torch.from_numpy(p[1]).cuda() for p in probs]
+    ws = [torch.from_numpy(p[2]).cuda() for p in probs]
+    params, singles = [], []
+    for i, (g, _, _) in enumerate(probs):
+        xr = torch.zeros(g.ny, g.nx, device="cuda")
+        ct.ct_relaxed_oslalm_solve(G, ys[i], ws[i], xr, M=1, n_iter=30, alpha=1.999, beta=BETA, delta=DELTA)
+        p = dict(M=Ms[i], n_iter=4, alpha=1.999, beta=BETA, delta=DELTA, x_ref=xr, hu_per_unit=HU)
+        xs = torch.zeros(g.ny, g.nx, device="cuda")
+        singles.append((xs, ct.ct_relaxed_oslalm_solve(G, ys[i], ws[i], xs, **p)))
+        params.append(p)
+    xb = [torch.zeros(g0.ny, g0.nx, device="cuda") for _ in probs]
+    reps = ct.ct_relaxed_oslalm_solve_batched([G] * 3, ys, ws, xb, params)
+    torch.cuda.synchronize()
+    for i, (g, _, _) in enumerate(probs):
+        d = _hu_rmsd(xb[i].cpu().numpy(), singles[i][0].cpu().numpy(), g)
+        assert d <= 0.01, (i, d)
+        tb, ts = reps[i]["rmsd_trace_hu"], singles[i][1]["rmsd_trace_hu"]
+        assert len(tb) == 4 and np.allclose(tb, ts, rtol=1e-3, atol=1e-2), (i, tb, ts)
 
 
 def test_large_slices_of_several_geometries_run_concurrently():
@@ -259,8 +288,15 @@ def test_batched_slices_stop_at_their_tolerance():
         singles.append((xs, ct.ct_relaxed_oslalm_solve(G, y, w, xs, **p)))
         params.append(p)
     xb = [torch.zeros(g.ny, g.nx, device="cuda") for g, *_ in probs]
-    reps = ct.ct_relaxed_oslalm_solve_batched([p[1] for p in probs], [p[2] for p in probs], [p[3] for p in probs],
-                                              xb, params)
+    # one batched call per geometry: the slices of one geometry share the persistent launch
+    reps = [None] * len(probs)
+    for G in {id(p[1]): p[1] for p in probs}.values():
+        idx = [i for i, p in enumerate(probs) if p[1] is G]
+        got = ct.ct_relaxed_oslalm_solve_batched([G] * len(idx), [probs[i][2] for i in idx],
+                                                 [probs[i][3] for i in idx], [xb[i] for i in idx],
+                                                 [params[i] for i in idx])
+        for i, r in zip(idx, got):
+            reps[i] = r
     torch.cuda.synchronize()
     for i, (g, *_rest) in enumerate(probs):
         xs, rs = singles[i]
