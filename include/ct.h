@@ -319,15 +319,18 @@ ct_status ct_relaxed_oslalm_solve(const ct_geom *g, const float *y, const float 
 
 /* Batched relaxed OS-LALM: nslices independent problems (Algorithm 1 or 2
  * each, with its own geometry, sinogram, weights and parameters).  Slices
- * of at least 384 x 384 pixels, whose own subsets fill the GPU, are solved
- * one after another by ct_relaxed_oslalm_solve; the smaller ones together
- * in one persistent cooperative launch, after per-slice setup launches
- * (D_L, initial gradient, optional FBP).  There, slice i runs n_iter_i * M_i
- * subiterations; all slices advance in lockstep super-steps, and each
- * super-step's regularizer, forward-projection and back-projection work of
- * every active slice is spread over all SMs.  Report times count from the
- * start of the call's device work (the large slices first); `seconds` is
- * the same total in every report.  geoms, y, w, x_inout: host
+ * of two or more geometries are all solved by ct_relaxed_oslalm_solve, on up
+ * to four concurrent host threads with a stream each (the slices of one
+ * geometry, which owns the solver workspace, one after another).  Slices of
+ * one geometry: those of at least 384 x 384 pixels, whose own subsets fill
+ * the GPU, one after another by ct_relaxed_oslalm_solve; the smaller ones
+ * together in one persistent cooperative launch, after per-slice setup
+ * launches (D_L, initial gradient, optional FBP).  There, slice i runs
+ * n_iter_i * M_i subiterations; all slices advance in lockstep super-steps,
+ * and each super-step's regularizer, forward-projection and back-projection
+ * work of every active slice is spread over all SMs.  Report times count from
+ * the start of the call's device work (an event on `stream`); `seconds` is the
+ * same total in every report.  geoms, y, w, x_inout: host
  * arrays of nslices pointers (device data as in ct_relaxed_oslalm_solve;
  * slices may share a geometry); params: host array of nslices parameter
  * sets (a slice with x_ref and stop_rmsd_hu > 0 stops at the end of the

@@ -1,7 +1,9 @@
 // Batched relaxed OS-LALM: many 2-D slices of uneven size, view count and
-// subset count (Algorithm 1 per slice, Sec. III-A).  Slices large enough to
-// fill the GPU alone go through the single-slice solver; the rest are
-// solved together in ONE persistent cooperative launch.
+// subset count (Algorithm 1 per slice, Sec. III-A).  Slices of several
+// geometries run the single-slice solver concurrently (solve_lanes); slices of
+// one geometry that are large enough to fill the GPU alone go through the
+// single-slice solver one after another, and the rest are solved together in
+// ONE persistent cooperative launch.
 //
 // All slices advance in lockstep super-steps t = 0, 1, ...: slice i runs its
 // subiteration t while t < n_iter * M_i, or until an outer iteration ends with
